@@ -1,0 +1,700 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY; see oracle.h).
+ *
+ * What it computes, and where each piece comes from (Quiroga, arXiv:1803.08320):
+ *   - the Kerr metric in Boyer-Lindquist coordinates with rho^2, Delta, Sigma
+ *     (Sec. 2, eq. kerr) and its ADM lapse/shift/3-metric (Sec. 2, after eq. coord);
+ *   - the geodesic equation; the paper integrates the canonical form (Sec. 2,
+ *     eq. Ham); the oracle integrates the equivalent second-order form
+ *     d2x/dl2 = -Gamma u u with Gamma built generically from analytic metric
+ *     derivatives in plain 4x4x4 loops, and keeps eq. Ham as a cross-form;
+ *   - classical RK4 (Sec. 5: "traditional fourth order Runge-Kutta"; tableau
+ *     c = (0, 1/2, 1/2, 1), b = (1, 2, 2, 1)/6, the paper does not print it);
+ *   - the per-ray horizon stop (Sec. 5), generalised to r <= (1+eps) r_+, plus
+ *     escape r >= r_esc, a non-finite check and a step cap;
+ *   - circular equatorial orbits: Schwarzschild eqs. COrbit, COrbit2,
+ *     gralorbits (Sec. 4); Kerr eqs. energia, momento (Sec. 3) and Bardeen's
+ *     closed forms; ISCO (eq. ISCO, eq. iscokerr, Bardeen-Press-Teukolsky);
+ *     angular frequency eq. omega;
+ *   - textbook additions the paper does not contain, each marked [not in paper]:
+ *     Carter constant, photon-orbit radii, the backward camera, the generic
+ *     bound-orbit solve and the SplitMix64 counter-based generator.
+ * Compile with -O2 -fno-fast-math -ffp-contract=off so that x86 and Arm hosts
+ * round identically.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define IDX2(m, n) ((m) * 4 + (n))
+#define IDX3(s, m, n) ((s) * 16 + (m) * 4 + (n))
+
+/* ------------------------------------------------------------------------ */
+/* geometry                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Outer horizon r_+ = M + sqrt(M^2 - a^2) (Sec. 3, text after eq. ISCO). */
+double orc_r_plus(double M, double a) { return M + sqrt(M * M - a * a); }
+
+/* Kerr line element in BL coordinates, Sec. 2 eq. kerr:
+ *   g_tt = -(Delta - a^2 sin^2)/rho^2, g_tphi = -2 a M r sin^2/rho^2,
+ *   g_rr = rho^2/Delta, g_thth = rho^2, g_phph = Sigma sin^2/rho^2. */
+void orc_metric(double M, double a, double r, double th, double g[16]) {
+  double s = sin(th), c = cos(th);
+  double rho2 = r * r + a * a * c * c;
+  double Delta = r * r - 2.0 * M * r + a * a;
+  double Sigma = (r * r + a * a) * (r * r + a * a) - a * a * Delta * s * s;
+  memset(g, 0, 16 * sizeof(double));
+  g[IDX2(0, 0)] = -(Delta - a * a * s * s) / rho2;
+  g[IDX2(0, 3)] = -2.0 * a * M * r * s * s / rho2;
+  g[IDX2(3, 0)] = g[IDX2(0, 3)];
+  g[IDX2(1, 1)] = rho2 / Delta;
+  g[IDX2(2, 2)] = rho2;
+  g[IDX2(3, 3)] = Sigma * s * s / rho2;
+}
+
+/* Analytic partial derivatives of the components above (only d/dr and d/dtheta
+ * are non-zero: the metric does not depend on t or phi).  Each component is a
+ * quotient N/D; the quotient rule is applied to the numerators and
+ * denominators exactly as written in eq. kerr. */
+void orc_metric_derivs(double M, double a, double r, double th, double dg[64]) {
+  double s = sin(th), c = cos(th);
+  double rho2 = r * r + a * a * c * c;
+  double Delta = r * r - 2.0 * M * r + a * a;
+  double Sigma = (r * r + a * a) * (r * r + a * a) - a * a * Delta * s * s;
+  /* derivatives of the building blocks; index 0 -> d/dr, 1 -> d/dtheta */
+  double drho2[2] = {2.0 * r, -2.0 * a * a * s * c};
+  double dDelta[2] = {2.0 * r - 2.0 * M, 0.0};
+  double dSigma[2] = {4.0 * r * (r * r + a * a) - a * a * dDelta[0] * s * s,
+                      -a * a * Delta * 2.0 * s * c};
+  double ds2[2] = {0.0, 2.0 * s * c};
+  memset(dg, 0, 64 * sizeof(double));
+  for (int k = 0; k < 2; ++k) {
+    int sidx = k + 1; /* coordinate index: r = 1, theta = 2 */
+    /* g_tt = -Ntt/rho2, Ntt = Delta - a^2 s^2 */
+    double Ntt = Delta - a * a * s * s;
+    double dNtt = dDelta[k] - a * a * ds2[k];
+    dg[IDX3(sidx, 0, 0)] = -(dNtt * rho2 - Ntt * drho2[k]) / (rho2 * rho2);
+    /* g_tphi = Ntp/rho2, Ntp = -2 a M r s^2 */
+    double Ntp = -2.0 * a * M * r * s * s;
+    double dNtp = (k == 0) ? -2.0 * a * M * s * s : -2.0 * a * M * r * ds2[1];
+    dg[IDX3(sidx, 0, 3)] = (dNtp * rho2 - Ntp * drho2[k]) / (rho2 * rho2);
+    dg[IDX3(sidx, 3, 0)] = dg[IDX3(sidx, 0, 3)];
+    /* g_rr = rho2/Delta */
+    dg[IDX3(sidx, 1, 1)] = (drho2[k] * Delta - rho2 * dDelta[k]) / (Delta * Delta);
+    /* g_thth = rho2 */
+    dg[IDX3(sidx, 2, 2)] = drho2[k];
+    /* g_phph = Npp/rho2, Npp = Sigma s^2 */
+    double Npp = Sigma * s * s;
+    double dNpp = dSigma[k] * s * s + Sigma * ds2[k];
+    dg[IDX3(sidx, 3, 3)] = (dNpp * rho2 - Npp * drho2[k]) / (rho2 * rho2);
+  }
+}
+
+/* Inverse metric: closed-form inverse of the (t, phi) block, reciprocal of the
+ * diagonal (r, theta) entries. */
+void orc_inverse_metric(double M, double a, double r, double th, double gi[16]) {
+  double g[16];
+  orc_metric(M, a, r, th, g);
+  double det = g[IDX2(0, 0)] * g[IDX2(3, 3)] - g[IDX2(0, 3)] * g[IDX2(0, 3)];
+  memset(gi, 0, 16 * sizeof(double));
+  gi[IDX2(0, 0)] = g[IDX2(3, 3)] / det;
+  gi[IDX2(0, 3)] = -g[IDX2(0, 3)] / det;
+  gi[IDX2(3, 0)] = gi[IDX2(0, 3)];
+  gi[IDX2(3, 3)] = g[IDX2(0, 0)] / det;
+  gi[IDX2(1, 1)] = 1.0 / g[IDX2(1, 1)];
+  gi[IDX2(2, 2)] = 1.0 / g[IDX2(2, 2)];
+}
+
+/* Christoffel symbols of the second kind, generic definition:
+ *   Gamma^m_{ab} = 1/2 g^{mn} (d_a g_{nb} + d_b g_{na} - d_n g_{ab}).
+ * G[m*16 + a*4 + b]. */
+void orc_christoffel(double M, double a, double r, double th, double G[64]) {
+  double gi[16], dg[64];
+  orc_inverse_metric(M, a, r, th, gi);
+  orc_metric_derivs(M, a, r, th, dg);
+  for (int m = 0; m < 4; ++m)
+    for (int al = 0; al < 4; ++al)
+      for (int be = 0; be < 4; ++be) {
+        double sum = 0.0;
+        for (int n = 0; n < 4; ++n)
+          sum += gi[IDX2(m, n)] *
+                 (dg[IDX3(al, n, be)] + dg[IDX3(be, n, al)] - dg[IDX3(n, al, be)]);
+        G[IDX3(m, al, be)] = 0.5 * sum;
+      }
+}
+
+/* ADM quantities of Kerr (Sec. 2, the comparison of eq. ADM with eq. kerr):
+ * alpha = sqrt(rho^2 Delta / Sigma), beta^phi = -2 M a r / Sigma,
+ * gamma = diag(rho^2/Delta, rho^2, Sigma sin^2/rho^2). */
+void orc_adm(double M, double a, double r, double th, double* alpha, double* beta_phi,
+             double gamma[3]) {
+  double s = sin(th), c = cos(th);
+  double rho2 = r * r + a * a * c * c;
+  double Delta = r * r - 2.0 * M * r + a * a;
+  double Sigma = (r * r + a * a) * (r * r + a * a) - a * a * Delta * s * s;
+  *alpha = sqrt(rho2 * Delta / Sigma);
+  *beta_phi = -2.0 * M * a * r / Sigma;
+  gamma[0] = rho2 / Delta;
+  gamma[1] = rho2;
+  gamma[2] = Sigma * s * s / rho2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* equations of motion                                                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double M, a;
+} orc_bh;
+
+/* dx^m/dl = u^m, du^m/dl = -Gamma^m_{ab} u^a u^b (full 4x4 double sum). */
+void orc_rhs(double M, double a, const double y[8], double f[8]) {
+  double G[64];
+  orc_christoffel(M, a, y[1], y[2], G);
+  for (int m = 0; m < 4; ++m) {
+    f[m] = y[4 + m];
+    double acc = 0.0;
+    for (int al = 0; al < 4; ++al)
+      for (int be = 0; be < 4; ++be) acc += G[IDX3(m, al, be)] * y[4 + al] * y[4 + be];
+    f[4 + m] = -acc;
+  }
+}
+
+/* Canonical equations, Sec. 2 eq. Ham with H = 1/2 g^{mn} p_m p_n:
+ *   dx^m/dl = g^{mn} p_n,  dp_m/dl = -1/2 (d_m g^{ab}) p_a p_b,
+ * where d_s g^{ab} = -g^{am} (d_s g_{mn}) g^{nb}. */
+void orc_rhs_hamiltonian(double M, double a, const double z[8], double f[8]) {
+  double gi[16], dg[64];
+  orc_inverse_metric(M, a, z[1], z[2], gi);
+  orc_metric_derivs(M, a, z[1], z[2], dg);
+  for (int m = 0; m < 4; ++m) {
+    double acc = 0.0;
+    for (int n = 0; n < 4; ++n) acc += gi[IDX2(m, n)] * z[4 + n];
+    f[m] = acc;
+  }
+  for (int s = 0; s < 4; ++s) {
+    double acc = 0.0;
+    for (int al = 0; al < 4; ++al)
+      for (int be = 0; be < 4; ++be) {
+        double dgi = 0.0;
+        for (int m = 0; m < 4; ++m)
+          for (int n = 0; n < 4; ++n) dgi -= gi[IDX2(al, m)] * dg[IDX3(s, m, n)] * gi[IDX2(n, be)];
+        acc += dgi * z[4 + al] * z[4 + be];
+      }
+    f[4 + s] = -0.5 * acc;
+  }
+}
+
+typedef void (*orc_rhs_fn)(const void* ctx, const double* y, double* f);
+
+/* One classical RK4 step of size h on a dim-dimensional system.  If
+ * stage_min is given, it receives the smallest component `watch` among the
+ * three intermediate stage states (the points where k2, k3, k4 are taken). */
+static void rk4_generic(orc_rhs_fn fn, const void* ctx, int dim, double h, double* y, int watch,
+                        double* stage_min) {
+  double k1[8], k2[8], k3[8], k4[8], tmp[8];
+  double mn = INFINITY;
+  fn(ctx, y, k1);
+  for (int i = 0; i < dim; ++i) tmp[i] = y[i] + 0.5 * h * k1[i];
+  if (stage_min && tmp[watch] < mn) mn = tmp[watch];
+  fn(ctx, tmp, k2);
+  for (int i = 0; i < dim; ++i) tmp[i] = y[i] + 0.5 * h * k2[i];
+  if (stage_min && tmp[watch] < mn) mn = tmp[watch];
+  fn(ctx, tmp, k3);
+  for (int i = 0; i < dim; ++i) tmp[i] = y[i] + h * k3[i];
+  if (stage_min && tmp[watch] < mn) mn = tmp[watch];
+  fn(ctx, tmp, k4);
+  for (int i = 0; i < dim; ++i) y[i] = y[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+  if (stage_min) *stage_min = mn;
+}
+
+static void geo_fn(const void* ctx, const double* y, double* f) {
+  const orc_bh* bh = (const orc_bh*)ctx;
+  orc_rhs(bh->M, bh->a, y, f);
+}
+static void ham_fn(const void* ctx, const double* y, double* f) {
+  const orc_bh* bh = (const orc_bh*)ctx;
+  orc_rhs_hamiltonian(bh->M, bh->a, y, f);
+}
+static void lin_fn(const void* ctx, const double* y, double* f) { f[0] = *(const double*)ctx * y[0]; }
+
+void orc_rk4_linear_test(double lam, double h, int nsteps, double* y) {
+  for (int i = 0; i < nsteps; ++i) rk4_generic(lin_fn, &lam, 1, h, y, 0, NULL);
+}
+void orc_rk4_step(double M, double a, double h, double y[8]) {
+  orc_bh bh = {M, a};
+  rk4_generic(geo_fn, &bh, 8, h, y, 1, NULL);
+}
+void orc_rk4_step_hamiltonian(double M, double a, double h, double z[8]) {
+  orc_bh bh = {M, a};
+  rk4_generic(ham_fn, &bh, 8, h, z, 1, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* integration with termination                                              */
+/* ------------------------------------------------------------------------ */
+
+static int all_finite(const double y[8]) {
+  for (int i = 0; i < 8; ++i)
+    if (!isfinite(y[i])) return 0;
+  return 1;
+}
+
+/* Integrate one ray.  After every completed step: captured if the radius
+ * reached (1+eps) r_+ (the paper's per-thread horizon stop, Sec. 5) -- at the
+ * new state or at any of the step's intermediate stage points, since a stage
+ * that lands inside r_+ (Delta < 0) spoils the whole step; escaped if
+ * r >= r_esc; non-finite if any component is not finite; after n_steps_cap
+ * steps: capped.  The reported state is the post-step state.  The step size
+ * is fixed (dl) or dl_r_scale * r at the start of the step, held for all four
+ * stages.  traj (optional) receives sample k (k*stride steps) at
+ * traj[k*8 ...]; samples after termination are NaN. */
+int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, double y[8],
+                  double* lambda, uint32_t* steps, double* traj, uint32_t stride) {
+  double r_cap = (1.0 + t->eps_hor) * orc_r_plus(M, a);
+  uint32_t ns = (traj && stride) ? t->n_steps_cap / stride + 1 : 0;
+  int fate = ORC_FATE_CAPPED;
+  uint32_t n = 0;
+  double lam = 0.0;
+  memcpy(y, y0, 8 * sizeof(double));
+  if (ns) memcpy(traj, y, 8 * sizeof(double));
+  while (n < t->n_steps_cap) {
+    double h = (t->dl_r_scale > 0.0) ? t->dl_r_scale * y[1] : t->dl;
+    double r_stage_min;
+    orc_bh bh = {M, a};
+    rk4_generic(geo_fn, &bh, 8, h, y, 1, &r_stage_min);
+    lam += h;
+    ++n;
+    if (ns && n % stride == 0) memcpy(traj + (size_t)(n / stride) * 8, y, 8 * sizeof(double));
+    if (y[1] <= r_cap || r_stage_min <= r_cap) { fate = ORC_FATE_CAPTURED; break; }
+    if (y[1] >= t->r_esc) { fate = ORC_FATE_ESCAPED; break; }
+    if (!all_finite(y)) { fate = ORC_FATE_NONFINITE; break; }
+  }
+  if (ns)
+    for (uint32_t k = n / stride + 1; k < ns; ++k)
+      for (int c = 0; c < 8; ++c) traj[(size_t)k * 8 + c] = NAN;
+  *lambda = lam;
+  *steps = n;
+  return fate;
+}
+
+int orc_trace_many(double M, double a, const double* a_per_ray, const double* ics, uint64_t n,
+                   const orc_term* t, double* y_out, double* lambda, double* inv0, double* inv1,
+                   uint32_t* steps, uint8_t* fate, double* traj, uint32_t stride, int nthreads) {
+  int used = 1;
+  size_t ns = (traj && stride) ? t->n_steps_cap / stride + 1 : 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+  used = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t i = 0; i < (int64_t)n; ++i) {
+    double ai = a_per_ray ? a_per_ray[i] : a;
+    double y0[8], y[8], inv[4], lam;
+    uint32_t st;
+    for (int c = 0; c < 8; ++c) y0[c] = ics[(size_t)c * n + i];
+    if (inv0) {
+      orc_invariants(M, ai, y0, inv);
+      for (int c = 0; c < 4; ++c) inv0[(size_t)c * n + i] = inv[c];
+    }
+    int f = orc_trace_one(M, ai, y0, t, y, &lam, &st, ns ? traj + (size_t)i * ns * 8 : NULL, stride);
+    for (int c = 0; c < 8; ++c) y_out[(size_t)c * n + i] = y[c];
+    if (lambda) lambda[i] = lam;
+    if (steps) steps[i] = st;
+    if (fate) fate[i] = (uint8_t)f;
+    if (inv1) {
+      orc_invariants(M, ai, y, inv);
+      for (int c = 0; c < 4; ++c) inv1[(size_t)c * n + i] = inv[c];
+    }
+  }
+  return used;
+}
+
+/* ------------------------------------------------------------------------ */
+/* conserved quantities                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* p_m = g_{mn} u^n; E = -p_t; L_z = p_phi; norm = g_{mn} u^m u^n (the
+ * constraint 2L = -1 of eq. geo for timelike, 0 for null); Carter's constant
+ * [not in paper] Q = p_th^2 + cos^2 th (a^2 (mu^2 - E^2) + L_z^2 / sin^2 th)
+ * with mu^2 = -norm. */
+void orc_invariants(double M, double a, const double y[8], double inv[4]) {
+  double g[16], p[4];
+  orc_metric(M, a, y[1], y[2], g);
+  double norm = 0.0;
+  for (int m = 0; m < 4; ++m) {
+    p[m] = 0.0;
+    for (int n = 0; n < 4; ++n) p[m] += g[IDX2(m, n)] * y[4 + n];
+    norm += p[m] * y[4 + m];
+  }
+  double E = -p[0], Lz = p[3], mu2 = -norm;
+  double s = sin(y[2]), c = cos(y[2]);
+  inv[0] = E;
+  inv[1] = Lz;
+  inv[2] = p[2] * p[2] + c * c * (a * a * (mu2 - E * E) + Lz * Lz / (s * s));
+  inv[3] = norm;
+}
+
+/* ------------------------------------------------------------------------ */
+/* initial conditions                                                        */
+/* ------------------------------------------------------------------------ */
+
+static void momenta_to_state(double M, double a, const double x[4], const double p[4], double y[8]) {
+  double gi[16];
+  orc_inverse_metric(M, a, x[1], x[2], gi);
+  for (int m = 0; m < 4; ++m) {
+    y[m] = x[m];
+    double acc = 0.0;
+    for (int n = 0; n < 4; ++n) acc += gi[IDX2(m, n)] * p[n];
+    y[4 + m] = acc;
+  }
+}
+
+/* The paper's initial-condition rows (Sec. 5: t, r, th, ph, p_t, p_r, p_th,
+ * p_ph) list p_t = +E; covariant p_t = -E.  u^m = g^{mn} p_n. */
+void orc_paper_to_state(double M, double a, const double xp[8], double y[8]) {
+  double p[4] = {-xp[4], xp[5], xp[6], xp[7]};
+  momenta_to_state(M, a, xp, p, y);
+}
+
+void orc_state_to_momenta(double M, double a, const double y[8], double p[4]) {
+  double g[16];
+  orc_metric(M, a, y[1], y[2], g);
+  for (int m = 0; m < 4; ++m) {
+    p[m] = 0.0;
+    for (int n = 0; n < 4; ++n) p[m] += g[IDX2(m, n)] * y[4 + n];
+  }
+}
+
+/* BL -> Cartesian map, Sec. 2 eq. coord. */
+void orc_bl_to_cartesian(double a, double r, double th, double ph, double xyz[3]) {
+  double R = sqrt(r * r + a * a);
+  xyz[0] = R * sin(th) * cos(ph);
+  xyz[1] = R * sin(th) * sin(ph);
+  xyz[2] = r * cos(th);
+}
+
+/* Schwarzschild circular orbits, Sec. 4 eqs. COrbit, COrbit2:
+ * E^2 = (4M^2 - 4Mr + r^2)/(r(r - 3M)), L^2 = M r^2/(r - 3M). */
+void orc_schw_circular(double M, double r, double* E, double* L) {
+  *E = sqrt((4.0 * M * M - 4.0 * M * r + r * r) / (r * (r - 3.0 * M)));
+  *L = sqrt(M * r * r / (r - 3.0 * M));
+}
+
+/* Sec. 4 eq. gralorbits with r = kM: p_t = sqrt((k^2-4k+4)/(k(k-3))), p_phi = kM/sqrt(k-3). */
+void orc_schw_gralorbits(double k, double M, double* pt, double* pphi) {
+  *pt = sqrt((k * k - 4.0 * k + 4.0) / (k * (k - 3.0)));
+  *pphi = k * M / sqrt(k - 3.0);
+}
+
+/* Sec. 3 eqs. energia and momento exactly as printed, with the sign sgn = +1
+ * or -1 taking the place of the +- symbol both inside the root and in front
+ * of L; R from the definition after eq. momento. */
+void orc_kerr_circular_paper(double M, double a, double r, int sgn, double* E, double* L) {
+  double R = r * r *
+             (-12.0 * M * M * M * r + 5.0 * M * M * a * a + 16.0 * M * M * r * r -
+              3.0 * M * a * a * r - 7.0 * M * r * r * r + r * r * r * r);
+  double w = 2.0 * M * r - a * a - r * r;
+  double root = sqrt(R + sgn * 2.0 * pow(M, 1.5) * pow(r, 1.5) * w * a);
+  *E = fabs((4.0 * M * M * r - M * a * a - 4.0 * M * r * r + r * r * r) / root);
+  *L = sgn * fabs((M * a * (4.0 * M * r - a * a - 3.0 * r * r) + pow(r, 1.5) * w * sqrt(M)) / root);
+}
+
+/* Bardeen, Press & Teukolsky (1972) circular equatorial orbits [closed form,
+ * the paper's reference for the ISCO limits]:
+ *   E = (r^{3/2} - 2M r^{1/2} +- a M^{1/2}) / (r^{3/4} sqrt(r^{3/2} - 3M r^{1/2} +- 2a M^{1/2}))
+ *   L = +- M^{1/2}(r^2 -+ 2a M^{1/2} r^{1/2} + a^2) / (same denominator)
+ * upper sign prograde (co-rotating). */
+void orc_kerr_circular_bardeen(double M, double a, double r, int prograde, double* E, double* L) {
+  double sg = prograde ? 1.0 : -1.0;
+  double sr = sqrt(r), sM = sqrt(M);
+  double den = pow(r, 0.75) * sqrt(r * sr - 3.0 * M * sr + sg * 2.0 * a * sM);
+  *E = (r * sr - 2.0 * M * sr + sg * a * sM) / den;
+  *L = sg * sM * (r * r - sg * 2.0 * a * sM * sr + a * a) / den;
+}
+
+/* Sec. 3 eq. omega: omega = (-2 M a p_t + (2M - r) p_phi) / (r (2Mr - a^2 - r^2)),
+ * with the paper's p_t = +E. */
+double orc_kerr_omega(double M, double a, double r, double pt_paper, double pphi) {
+  return (-2.0 * M * a * pt_paper + (2.0 * M - r) * pphi) / (r * (2.0 * M * r - a * a - r * r));
+}
+
+/* Bardeen-Press-Teukolsky ISCO:
+ *   Z1 = 1 + (1 - a^2/M^2)^{1/3} ((1 + a/M)^{1/3} + (1 - a/M)^{1/3}),
+ *   Z2 = sqrt(3 a^2/M^2 + Z1^2),
+ *   r = M (3 + Z2 -+ sqrt((3 - Z1)(3 + Z1 + 2 Z2)))   (upper: prograde). */
+double orc_isco_bardeen(double M, double a, int prograde) {
+  double x = a / M;
+  double Z1 = 1.0 + cbrt(1.0 - x * x) * (cbrt(1.0 + x) + cbrt(1.0 - x));
+  double Z2 = sqrt(3.0 * x * x + Z1 * Z1);
+  double sg = prograde ? -1.0 : 1.0;
+  return M * (3.0 + Z2 + sg * sqrt((3.0 - Z1) * (3.0 + Z1 + 2.0 * Z2)));
+}
+
+/* Sec. 3 eq. iscokerr exactly as printed (sgn = +1 for the upper sign);
+ * returns NaN where a square root of a negative number appears. */
+double orc_isco_paper_literal(double M, double a, int sgn) {
+  double a2 = a * a, M2 = M * M;
+  double base = a2 * a2 * a2 + 17.0 * a2 * a2 * M2 - 45.0 * a2 * M2 * M2 + 27.0 * M2 * M2 * M2 +
+                8.0 * sqrt(pow(a, 10) * M2 - 2.0 * pow(a, 8) * M2 * M2 + pow(a, 6) * M2 * M2 * M2);
+  double cb = cbrt(base);
+  double A = 4.0 * (a2 * a2 - 10.0 * a2 * M2 + 9.0 * M2 * M2) / cb;
+  double B = 4.0 * cb;
+  double C = 36.0 * M2 + 4.0 * (a2 - 6.0 * M2);
+  double s1 = A + B + C;
+  if (s1 < 0.0) return NAN;
+  double q = -A - B + 2.0 * C + (224.0 * a2 * M + 1728.0 * M * (a2 - 6.0 * M2)) / (4.0 * sqrt(s1));
+  if (q < 0.0) return NAN;
+  return 3.0 * M + 0.5 * sqrt(s1) - sgn * sqrt(q);
+}
+
+/* Sec. 3 eq. ISCO: the ISCO is the root of dE/dr = 0.  dE/dr by a central
+ * difference of the Bardeen E(r), root by bisection on [r_lo, r_hi]. */
+static double dEdr(double M, double a, int prograde, double r) {
+  double hh = 1e-5 * r, Ep, Em, L;
+  orc_kerr_circular_bardeen(M, a, r + hh, prograde, &Ep, &L);
+  orc_kerr_circular_bardeen(M, a, r - hh, prograde, &Em, &L);
+  return (Ep - Em) / (2.0 * hh);
+}
+double orc_dEdr_numeric_root(double M, double a, int prograde, double r_lo, double r_hi) {
+  double flo = dEdr(M, a, prograde, r_lo);
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (r_lo + r_hi);
+    double fm = dEdr(M, a, prograde, mid);
+    if ((fm < 0.0) == (flo < 0.0)) { r_lo = mid; flo = fm; } else { r_hi = mid; }
+  }
+  return 0.5 * (r_lo + r_hi);
+}
+
+/* Circular equatorial photon orbits [not in paper; Bardeen 1972]:
+ * r_ph = 2M (1 + cos(2/3 arccos(-+ a/M)))  (upper: prograde). */
+double orc_photon_orbit(double M, double a, int prograde) {
+  double sg = prograde ? -1.0 : 1.0;
+  return 2.0 * M * (1.0 + cos(2.0 / 3.0 * acos(sg * a / M)));
+}
+
+/* Circular equatorial timelike orbit at radius r: p = (-E, 0, 0, L) from the
+ * Bardeen E, L; u = g^{-1} p. */
+void orc_circular_state(double M, double a, double r, int prograde, double y[8]) {
+  double E, L;
+  orc_kerr_circular_bardeen(M, a, r, prograde, &E, &L);
+  double x[4] = {0.0, r, M_PI / 2.0, 0.0};
+  double p[4] = {-E, 0.0, 0.0, L};
+  momenta_to_state(M, a, x, p, y);
+}
+
+/* Backward null-ray camera [not in paper; Bardeen 1973 impact parameters].
+ * Pixel pix = j*nx + i, i along alpha, j along beta, pixel centres
+ *   alpha = -fov + 2 fov (i + 1/2)/nx,   beta = -fov + 2 fov (j + 1/2)/ny.
+ * Arriving photon: E = 1, L = -alpha sin th_o, Q = beta^2 + cos^2 th_o (alpha^2 - a^2),
+ *   p_th = sign(beta) sqrt(Theta(th_o)), Theta = Q + a^2 cos^2 - L^2 cot^2,
+ *   p_r = +sqrt(R(r_o))/Delta(r_o), R = ((r^2 + a^2) E - a L)^2 - Delta (Q + (L - a E)^2).
+ * The ray is traced backward by integrating forward in lambda with the
+ * momentum reversed, p~ = -p; u = g^{-1} p~; x = (0, r_o, th_o, 0). */
+void orc_camera_ic(double M, double a, double r_o, double th_o, double fov_half, uint32_t nx,
+                   uint32_t ny, uint64_t pix, double y[8]) {
+  uint64_t i = pix % nx, j = pix / nx;
+  double alpha = -fov_half + 2.0 * fov_half * ((double)i + 0.5) / (double)nx;
+  double beta = -fov_half + 2.0 * fov_half * ((double)j + 0.5) / (double)ny;
+  double E = 1.0;
+  double so = sin(th_o), co = cos(th_o);
+  double L = -alpha * so;
+  double Q = beta * beta + co * co * (alpha * alpha - a * a);
+  double Theta = Q + a * a * co * co - L * L * co * co / (so * so);
+  if (Theta < 0.0) Theta = 0.0;
+  double pth = (beta >= 0.0 ? 1.0 : -1.0) * sqrt(Theta);
+  double Delta = r_o * r_o - 2.0 * M * r_o + a * a;
+  double Rr = ((r_o * r_o + a * a) * E - a * L) * ((r_o * r_o + a * a) * E - a * L) -
+              Delta * (Q + (L - a * E) * (L - a * E));
+  if (Rr < 0.0) Rr = 0.0;
+  double pr = sqrt(Rr) / Delta;
+  double x[4] = {0.0, r_o, th_o, 0.0};
+  double p[4] = {E, -pr, -pth, -L}; /* reversed: -(-E, pr, pth, L) */
+  momenta_to_state(M, a, x, p, y);
+}
+
+/* Distance in the (alpha, beta) plane from a point to the Kerr critical curve
+ * (boundary of the shadow) [not in paper; Bardeen 1973]:
+ *   xi(r) = (r^2 (3M - r) - a^2 (r + M)) / (a (r - M)),
+ *   eta(r) = r^3 (4 a^2 M - r (r - 3M)^2) / (a^2 (r - M)^2),
+ *   alpha = -xi / sin th_o, beta = +- sqrt(eta + a^2 cos^2 th_o - xi^2 cot^2 th_o),
+ * for r between the prograde and retrograde photon orbits; for a = 0 a circle
+ * of radius 3 sqrt(3) M.  Plain dense sampling of r plus a local refinement. */
+static double cc_dist_at(double M, double a, double th_o, double r, double al, double be) {
+  double xi = (r * r * (3.0 * M - r) - a * a * (r + M)) / (a * (r - M));
+  double eta = r * r * r * (4.0 * a * a * M - r * (r - 3.0 * M) * (r - 3.0 * M)) / (a * a * (r - M) * (r - M));
+  double so = sin(th_o), co = cos(th_o);
+  double b2 = eta + a * a * co * co - xi * xi * co * co / (so * so);
+  if (b2 < 0.0) return INFINITY;
+  double ac = -xi / so, bc = sqrt(b2);
+  double d1 = hypot(al - ac, be - bc), d2 = hypot(al - ac, be + bc);
+  return d1 < d2 ? d1 : d2;
+}
+double orc_critical_curve_distance(double M, double a, double th_o, double alpha, double beta) {
+  if (fabs(a) < 1e-12) return fabs(hypot(alpha, beta) - 3.0 * sqrt(3.0) * M);
+  double r1 = orc_photon_orbit(M, fabs(a), 1), r2 = orc_photon_orbit(M, fabs(a), 0);
+  int N = 20000;
+  double best = INFINITY, rbest = r1;
+  for (int k = 0; k <= N; ++k) {
+    double r = r1 + (r2 - r1) * k / N;
+    double d = cc_dist_at(M, a, th_o, r, alpha, beta);
+    if (d < best) { best = d; rbest = r; }
+  }
+  double lo = rbest - (r2 - r1) / N, hi = rbest + (r2 - r1) / N;
+  if (lo < r1) lo = r1;
+  if (hi > r2) hi = r2;
+  for (int k = 0; k <= 2000; ++k) {
+    double d = cc_dist_at(M, a, th_o, lo + (hi - lo) * k / 2000.0, alpha, beta);
+    if (d < best) best = d;
+  }
+  return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* generic bound orbits [not in paper]                                       */
+/* ------------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea & Flood 2014) used as a counter-based generator:
+ * the output for counter k is the SplitMix64 output after k+1 increments of
+ * the state seeded with `seed`. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t counter) {
+  uint64_t z = seed + (counter + 1u) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+/* uniform in [0, 1): top 53 bits times 2^-53 */
+double orc_uniform(uint64_t seed, uint64_t counter) {
+  return (double)(orc_splitmix64(seed, counter) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* Kerr radial potential with mu = 1:
+ * R(r) = (E (r^2 + a^2) - a L_z)^2 - Delta (r^2 + (L_z - a E)^2 + Q). */
+double orc_radial_potential(double M, double a, double E, double Lz, double Q, double r) {
+  double Delta = r * r - 2.0 * M * r + a * a;
+  double P = E * (r * r + a * a) - a * Lz;
+  return P * P - Delta * (r * r + (Lz - a * E) * (Lz - a * E) + Q);
+}
+
+/* Solve for (E, L_z, Q) of the bound orbit with periapsis rp, eccentricity e
+ * (apoapsis ra = rp (1+e)/(1-e)) and inclination iota (cos iota = L_z /
+ * sqrt(L_z^2 + Q)).  Unknowns (E, L) with L_z = L cos iota, Q = L^2 sin^2 iota.
+ * Equations R(rp) = R(ra) = 0, or R(rp) = R'(rp) = 0 when e < 1e-6.  Newton's
+ * method with a finite-difference Jacobian, from the Schwarzschild guess with
+ * semi-latus rectum p = rp (1 + e).  Returns 0 for a bound, stable orbit;
+ * 1 no convergence, 2 E >= 1 or E <= 0, 3 third root r3 >= rp (plunging),
+ * 4 the region between rp and ra is not allowed. */
+static void bound_residual(double M, double a, double rp, double ra, int circ, double ci,
+                           double si, double E, double L, double F[2]) {
+  double Lz = L * ci, Q = L * L * si * si;
+  F[0] = orc_radial_potential(M, a, E, Lz, Q, rp);
+  if (circ) {
+    /* R'(r) = 2 P (2 E r) - (2r - 2M)(r^2 + (L_z - aE)^2 + Q) - 2 r Delta, P = E (r^2 + a^2) - a L_z */
+    double Delta = rp * rp - 2.0 * M * rp + a * a;
+    double P = E * (rp * rp + a * a) - a * Lz;
+    F[1] = 2.0 * P * 2.0 * E * rp - (2.0 * rp - 2.0 * M) * (rp * rp + (Lz - a * E) * (Lz - a * E) + Q) -
+           2.0 * rp * Delta;
+  } else {
+    F[1] = orc_radial_potential(M, a, E, Lz, Q, ra);
+  }
+}
+
+int orc_bound_orbit_solve(double M, double a, double rp, double e, double iota, double* E_out,
+                          double* Lz_out, double* Q_out, double* r3_out) {
+  int circ = e < 1e-6;
+  double ra = circ ? rp : rp * (1.0 + e) / (1.0 - e);
+  double ci = cos(iota), si = sin(iota);
+  double pM = rp * (1.0 + e) / M;
+  double den = pM - 3.0 - e * e;
+  double E, L;
+  if (den > 0.05) {
+    E = sqrt((pM - 2.0 - 2.0 * e) * (pM - 2.0 + 2.0 * e) / (pM * den));
+    L = M * pM / sqrt(den);
+  } else {
+    E = 0.95;
+    L = 4.0 * M;
+  }
+  int ok = 0;
+  for (int it = 0; it < 200; ++it) {
+    double F[2], Fe[2], Fl[2];
+    bound_residual(M, a, rp, ra, circ, ci, si, E, L, F);
+    double scale = rp * rp * rp * rp;
+    if (fabs(F[0]) < 1e-14 * scale && fabs(F[1]) < 1e-14 * scale) { ok = 1; break; }
+    double dE = 1e-7 * fmax(fabs(E), 1e-3), dL = 1e-7 * fmax(fabs(L), 1e-3);
+    bound_residual(M, a, rp, ra, circ, ci, si, E + dE, L, Fe);
+    bound_residual(M, a, rp, ra, circ, ci, si, E, L + dL, Fl);
+    double J00 = (Fe[0] - F[0]) / dE, J10 = (Fe[1] - F[1]) / dE;
+    double J01 = (Fl[0] - F[0]) / dL, J11 = (Fl[1] - F[1]) / dL;
+    double det = J00 * J11 - J01 * J10;
+    if (det == 0.0 || !isfinite(det)) break;
+    double sE = -(J11 * F[0] - J01 * F[1]) / det;
+    double sL = -(-J10 * F[0] + J00 * F[1]) / det;
+    /* damping: keep the update within 10% of the current values */
+    double lim = 0.1;
+    double fac = 1.0;
+    if (fabs(sE) > lim * fabs(E)) fac = fmin(fac, lim * fabs(E) / fabs(sE));
+    if (fabs(sL) > lim * fabs(L)) fac = fmin(fac, lim * fabs(L) / fabs(sL));
+    E += fac * sE;
+    L += fac * sL;
+  }
+  if (!ok) {
+    /* one last residual check: Newton may stop at the tolerance edge */
+    double F[2];
+    bound_residual(M, a, rp, ra, circ, ci, si, E, L, F);
+    double scale = rp * rp * rp * rp;
+    if (!(fabs(F[0]) < 1e-11 * scale && fabs(F[1]) < 1e-11 * scale)) return 1;
+  }
+  if (!(E > 0.0 && E < 1.0) || !(L > 0.0)) return 2;
+  double Lz = L * ci, Q = L * L * si * si;
+  /* remaining roots of R(r) = (E^2 - 1)(r - ra)(r - rp)(r - r3)(r - r4):
+   * sum of roots 2M/(1 - E^2), product a^2 Q/(1 - E^2) */
+  double S = 2.0 * M / (1.0 - E * E) - ra - rp;
+  double P = a * a * Q / ((1.0 - E * E) * ra * rp);
+  double disc = S * S - 4.0 * P;
+  double r3 = disc >= 0.0 ? 0.5 * (S + sqrt(disc)) : -INFINITY;
+  if (r3_out) *r3_out = r3;
+  if (r3 >= rp) return 3;
+  if (!circ && !(orc_radial_potential(M, a, E, Lz, Q, 0.5 * (rp + ra)) > 0.0)) return 4;
+  *E_out = E;
+  *Lz_out = Lz;
+  *Q_out = Q;
+  return 0;
+}
+
+/* Seeded generic bound-orbit sampler.  Particle `index` draws its spin
+ * a = a_max U(counter index*256) (or takes a = a_max when spin_fixed), then candidates j = 0..63 with
+ *   rp = r_lo + (10M - r_lo) U(index*256 + 4j + 1),  r_lo = ISCO_prograde(a) + 0.5M,
+ *   e = 0.7 U(index*256 + 4j + 2),  iota = pi U(index*256 + 4j + 3),
+ * and keeps the first bound, stable one.  State: x = (0, rp, pi/2, 0),
+ * p = (-E, 0, +sqrt(Q), L_z), u = g^{-1} p.  Returns the accepted candidate
+ * index, or -1 when all 64 were rejected (then the prograde circular
+ * equatorial orbit at r = 10M is used).  cand = (rp, e, iota, attempts). */
+int orc_bound_sample(double M, double a_max, int spin_fixed, uint64_t seed, uint64_t index,
+                     double* a_out, double y[8], double cand[4]) {
+  uint64_t base = index * 256u;
+  double a = spin_fixed ? a_max : a_max * orc_uniform(seed, base);
+  double r_lo = orc_isco_bardeen(M, a, 1) + 0.5 * M, r_hi = 10.0 * M;
+  *a_out = a;
+  for (int j = 0; j < 64; ++j) {
+    double rp = r_lo + (r_hi - r_lo) * orc_uniform(seed, base + 4u * j + 1u);
+    double e = 0.7 * orc_uniform(seed, base + 4u * j + 2u);
+    double iota = M_PI * orc_uniform(seed, base + 4u * j + 3u);
+    double E, Lz, Q, r3;
+    if (orc_bound_orbit_solve(M, a, rp, e, iota, &E, &Lz, &Q, &r3) == 0) {
+      double x[4] = {0.0, rp, M_PI / 2.0, 0.0};
+      double p[4] = {-E, 0.0, sqrt(Q), Lz};
+      momenta_to_state(M, a, x, p, y);
+      if (cand) { cand[0] = rp; cand[1] = e; cand[2] = iota; cand[3] = j + 1; }
+      return j;
+    }
+  }
+  orc_circular_state(M, a, r_hi, 1, y);
+  if (cand) { cand[0] = r_hi; cand[1] = 0.0; cand[2] = 0.0; cand[3] = 64; }
+  return -1;
+}
