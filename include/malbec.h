@@ -1,0 +1,259 @@
+/*
+ * malbec.h -- C ABI of libmalbec.so, a single-GPU (GB300, sm_103a) library
+ * that integrates timelike and null geodesics of the Schwarzschild and Kerr
+ * black holes in Boyer-Lindquist (BL) coordinates with classical fixed-step
+ * RK4, one ray per GPU thread (Quiroga, "MALBEC: a new CUDA-C ray-tracer in
+ * General Relativity", arXiv:1803.08320).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Units G = c = 1.  Coordinates x^mu = (t, r, theta, phi), index order
+ *    0..3.  A state is y = (x^0..x^3, u^0..u^3), u^mu = dx^mu/dlambda.
+ *  - Arrays of states are structure-of-arrays: component c of ray i lives at
+ *    ptr[c * n + i] (c = 0..7).
+ *  - Pointers documented as "device" must point to memory of the current CUDA
+ *    device (e.g. tensors allocated by PyTorch).  The caller owns all such
+ *    memory; the library never frees it.  Pointers documented as "host" are
+ *    ordinary host memory.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and the call returns without waiting, unless stated otherwise.
+ *  - Return value: MALBEC_OK (0) or a negative MALBEC_E* code.  Invalid
+ *    arguments are rejected before any work is enqueued.  Per-ray outcomes
+ *    (capture, escape, cap, non-finite) are fate codes in the output, not
+ *    call errors.  A CUDA launch or allocation failure returns MALBEC_ECUDA;
+ *    malbec_last_cuda_error() gives the CUDA error string.
+ *  - Every entry point is thread-safe with respect to other entry points; two
+ *    calls on different streams run concurrently on the GPU.
+ */
+#ifndef MALBEC_H
+#define MALBEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* malbec_stream; /* == cudaStream_t */
+
+/* ---------------------------------------------------------------- errors */
+#define MALBEC_OK 0
+#define MALBEC_EINVAL (-1)    /* bad argument (a >= M, M <= 0, r0 <= r_+, NaN, n == 0 with out, ...) */
+#define MALBEC_ENOMEM (-2)    /* over the HBM budget, or a device allocation failed */
+#define MALBEC_EBUSY (-3)     /* admission queue full: retry later */
+#define MALBEC_ETIMEDOUT (-4) /* a bounded device-side wait gave up */
+#define MALBEC_ECUDA (-5)     /* CUDA runtime error; see malbec_last_cuda_error() */
+#define MALBEC_ENOTFOUND (-6) /* unknown job id */
+
+/* Human-readable text of a MALBEC_* code (static storage, never NULL). */
+const char* malbec_strerror(int code);
+/* Text of the last CUDA error seen by this thread (static storage). */
+const char* malbec_last_cuda_error(void);
+
+/* ---------------------------------------------------------------- fates */
+/* Per-ray termination, tested after every completed RK4 step in this order
+ * (Sec. 5 of the paper stops a thread at the horizon, r <= 1 + sqrt(1 - a^2)
+ * for M = 1; this library generalises it to (1 + eps_hor) r_+ and adds the
+ * escape radius, a non-finite check and the step cap):
+ *   CAPTURED  r <= (1+eps_hor) r_+ at the new state or at one of the step's
+ *             intermediate RK4 stage points (r_+ = M + sqrt(M^2 - a^2));
+ *   NONFINITE some component of the new state is NaN or infinite;
+ *   ESCAPED   r >= r_esc;
+ *   CAPPED    n_steps_cap steps taken. */
+#define MALBEC_FATE_CAPTURED 1
+#define MALBEC_FATE_ESCAPED 2
+#define MALBEC_FATE_CAPPED 3
+#define MALBEC_FATE_NONFINITE 4
+
+/* ---------------------------------------------------------------- parameters */
+/* Black hole.  Kerr metric in BL coordinates, Sec. 2 eq. kerr; a = 0 is
+ * Schwarzschild (Sec. 4) and selects the specialised Schwarzschild kernel.
+ * Requires M > 0 and 0 <= a < M (Sec. 2 restricts to a <= M; a = M is
+ * rejected because r_+ = M makes the capture radius degenerate).
+ * a_per_ray: optional device array of n spins (overrides a per ray; each
+ * must satisfy 0 <= a_i < M; not validated on the host -- a ray with an
+ * invalid spin ends NONFINITE). */
+typedef struct {
+  double M;
+  double a;
+  const double* a_per_ray;
+} malbec_metric;
+
+/* Step rule and termination.  The step is h = dl, or h = dl_r_scale * r_n
+ * (r at the start of the step, held for all four stages) when
+ * dl_r_scale > 0.  The paper uses a fixed h (Sec. 6).  Requires eps_hor >= 0,
+ * r_esc > (1+eps_hor) r_+, and a finite positive step. */
+typedef struct {
+  double eps_hor;
+  double r_esc;
+  uint32_t n_steps_cap;
+  double dl;
+  double dl_r_scale;
+} malbec_term;
+
+typedef enum {
+  MALBEC_OUT_FINAL = 0,  /* final state, lambda, invariants, steps, fate */
+  MALBEC_OUT_STRIDED = 1 /* FINAL plus a trajectory sample every `stride` steps */
+} malbec_out_mode;
+
+typedef enum {
+  MALBEC_FP64 = 0,      /* every operation in double precision */
+  MALBEC_FP32_MIXED = 1 /* FP32 RHS and stages, compensated (hi, lo) FP32 state,
+                           FP64 steps inside the FP64 zone, FP64 lambda and invariants */
+} malbec_precision;
+
+/* FP32_MIXED FP64 zone: a step runs in FP64 when, at its start,
+ *   r < MALBEC_ZONE_HORIZON_FACTOR * r_+                      (every ray), or
+ *   r < r_ph,retro(a) + MALBEC_ZONE_PHOTON_MARGIN * M        (null rays), or
+ *   |sin theta| < MALBEC_ZONE_POLE_SIN   (near the polar axis, where the BL
+ *                                         Christoffel symbols diverge),
+ * r_ph,retro = 2M (1 + cos(2/3 arccos(a/M))) the retrograde circular photon
+ * orbit, the outer edge of the spherical photon orbits.  A ray is null when
+ * |g(u,u)| <= 1e-6 (u^t)^2 |g_tt| at its start. */
+#define MALBEC_ZONE_HORIZON_FACTOR 2.0
+#define MALBEC_ZONE_PHOTON_MARGIN 0.5
+#define MALBEC_ZONE_POLE_SIN 0.2
+
+/* The FP64 zone in force for subsequent FP32_MIXED calls of this process
+ * (the defaults above until changed).  Larger zones trade speed for accuracy.
+ * Requires horizon_factor >= 1, photon_margin >= 0, 0 <= pole_sin <= 1;
+ * NULL restores the defaults.  Thread-safe; calls already enqueued keep the
+ * zone they were given. */
+typedef struct {
+  double horizon_factor;
+  double photon_margin;
+  double pole_sin;
+} malbec_mixed_zone;
+
+int malbec_set_mixed_zone(const malbec_mixed_zone* zone);
+int malbec_get_mixed_zone(malbec_mixed_zone* zone);
+
+/* ---------------------------------------------------------------- output layout */
+/* Offsets (bytes from the start of `out`) of the output fields of
+ * malbec_trace.  Every field starts on a 256-byte boundary.
+ *   y       double[8][n]     final state (SoA)
+ *   lambda  double[n]        affine parameter (sum of the steps taken)
+ *   inv0    double[4][n]     E = -p_t, L_z = p_phi, Carter Q, norm g(u,u) at the start
+ *   inv1    double[4][n]     the same at the end (always FP64)
+ *   steps   uint32[n]        RK4 steps taken
+ *   fate    uint8[n]         MALBEC_FATE_*
+ *   traj    STRIDED only: per ray `n_samples` samples of 8 components,
+ *           ray-major: traj[(i * n_samples + k) * 8 + c]; double for FP64,
+ *           float (the hi word) for FP32_MIXED.  Sample k is the state after
+ *           k * stride steps (sample 0 = initial state); samples after the
+ *           ray terminated are NaN.  n_samples = n_steps_cap / stride + 1. */
+typedef struct {
+  size_t y, lambda, inv0, inv1, steps, fate, traj;
+  uint64_t n_samples;
+  size_t total; /* bytes to allocate for `out` */
+} malbec_layout;
+
+int malbec_out_layout(malbec_out_mode mode, malbec_precision prec, uint64_t n,
+                      uint32_t n_steps_cap, uint32_t stride, malbec_layout* layout);
+/* = layout.total, or 0 on invalid arguments. */
+size_t malbec_out_bytes(malbec_out_mode mode, malbec_precision prec, uint64_t n,
+                        uint32_t n_steps_cap, uint32_t stride);
+
+/* ---------------------------------------------------------------- tracing */
+/* Integrate n rays from the initial states `ics` (device, double[8][n] SoA)
+ * until each terminates (see fates).  The right-hand side is the geodesic
+ * equation du^mu/dl = -Gamma^mu_ab u^a u^b (the second-order form of the
+ * canonical equations, Sec. 2 eq. Ham) specialised for Schwarzschild or
+ * Kerr; each RK4 step is the classical 4-stage scheme.  Rays are pulled from
+ * a device work queue by persistent warps, and a lane whose ray ends takes
+ * the next one, so uneven step counts do not idle lanes.
+ * out: device, layout.total bytes (malbec_out_layout), caller-owned.
+ * Validation (MALBEC_EINVAL): M > 0, 0 <= a < M, finite step > 0,
+ * r_esc > capture radius, stride > 0 in STRIDED mode, n > 0, non-NULL
+ * pointers.  Initial radii are not read on the host; a ray starting inside
+ * the capture radius ends CAPTURED after one step.
+ * Scratch: a 256-byte work-queue block is taken from the stream-ordered
+ * allocator (cudaMallocAsync / cudaFreeAsync on `stream`). */
+int malbec_trace(malbec_metric m, const double* ics, uint64_t n, malbec_term t,
+                 malbec_out_mode mode, uint32_t stride, malbec_precision prec, void* out,
+                 malbec_stream stream);
+
+/* ---------------------------------------------------------------- camera */
+/* Backward null-ray camera (not in the paper; Bardeen 1973 impact
+ * parameters).  Pixel p = j * nx + i has impact parameters
+ *   alpha = -fov_half + 2 fov_half (i + 1/2)/nx,  beta = -fov_half + 2 fov_half (j + 1/2)/ny.
+ * The arriving photon has E = 1, L_z = -alpha sin(incl),
+ * Q = beta^2 + cos^2(incl)(alpha^2 - a^2), p_theta = sign(beta) sqrt(Theta(incl)),
+ * p_r = +sqrt(R(r_obs))/Delta(r_obs), observer at (t, r, theta, phi) =
+ * (0, r_obs, incl, 0).  The ray is traced backward by integrating forward in
+ * lambda with p reversed; u = g^{-1}(-p).  Initial states are built in the
+ * kernel (no input array). */
+typedef struct {
+  double r_obs; /* observer radius, > capture radius and < r_esc */
+  double incl;  /* observer inclination (radians), in (0, pi) */
+  double fov_half;
+  uint32_t nx, ny;
+} malbec_camera;
+
+/* Camera output offsets (bytes, 256-aligned): fate uint8[n], steps uint32[n],
+ * theta double[n], phi double[n] (final theta and unwrapped phi of each
+ * ray), n = nx * ny. */
+typedef struct {
+  size_t fate, steps, theta, phi;
+  size_t total;
+} malbec_camera_layout;
+
+int malbec_camera_out_layout(const malbec_camera* cam, malbec_camera_layout* layout);
+
+/* Render one camera image: trace every pixel's ray.  m.a_per_ray must be
+ * NULL.  out: device, layout.total bytes. */
+int malbec_trace_camera(malbec_metric m, const malbec_camera* cam, malbec_term t,
+                        malbec_precision prec, void* out, malbec_stream stream);
+
+/* Initial states of the camera pixels `pixels` (device uint64[n] pixel
+ * indices) into ics (device double[8][n]); the same construction the camera
+ * kernel uses. */
+int malbec_ic_camera(malbec_metric m, const malbec_camera* cam, const uint64_t* pixels,
+                     uint64_t n, double* ics, malbec_stream stream);
+
+/* ---------------------------------------------------------------- initial data */
+/* Circular equatorial timelike orbits at the radii `radii` (device double[n]):
+ * Schwarzschild E, L from Sec. 4 eqs. COrbit/COrbit2 when a = 0, Bardeen's
+ * prograde (prograde != 0) or retrograde E, L otherwise; state
+ * x = (0, r, pi/2, 0), u = g^{-1}(-E, 0, 0, L).  ics: device double[8][n].
+ * Radii where no circular orbit exists give NaN states. */
+int malbec_ic_circular(malbec_metric m, const double* radii, uint64_t n, int prograde,
+                       double* ics, malbec_stream stream);
+
+/* Generic bound Kerr orbits (not in the paper).  Particle i draws with the
+ * SplitMix64 counter-based generator (seed, counter i*256 + k):
+ *   a = a_max U (counter i*256), unless spin_fixed (then a = a_max);
+ *   candidates j = 0..63: r_p = r_lo + (10M - r_lo) U(i*256+4j+1) with
+ *   r_lo = ISCO_prograde(a) + 0.5M, e = 0.7 U(i*256+4j+2), iota = pi U(i*256+4j+3);
+ * and keeps the first candidate that is bound and stable: (E, L_z, Q) solve
+ * R(r_p) = R(r_a) = 0 (R(r_p) = R'(r_p) = 0 when e < 1e-6), r_a = r_p (1+e)/(1-e),
+ * cos iota = L_z / sqrt(L_z^2 + Q), 0 < E < 1, third root of R below r_p.
+ * State: x = (0, r_p, pi/2, 0), p = (-E, 0, +sqrt(Q), L_z), u = g^{-1} p.
+ * If all 64 candidates fail, the prograde circular equatorial orbit at 10M.
+ * Outputs (device): ics double[8][n], spins double[n], accepted int32[n]
+ * (candidate index, -1 for the fallback); particle indices run from
+ * index0 to index0 + n - 1. */
+int malbec_ic_bound(double M, double a_max, int spin_fixed, uint64_t seed, uint64_t index0,
+                    uint64_t n, double* ics, double* spins, int32_t* accepted,
+                    malbec_stream stream);
+
+/* E, L_z, Q (Carter), norm g(u,u) of n states (device double[8][n]) into
+ * inv (device double[4][n]), in FP64. */
+int malbec_invariants(malbec_metric m, const double* states, uint64_t n, double* inv,
+                      malbec_stream stream);
+
+/* ---------------------------------------------------------------- measurement */
+/* Measured non-tensor FMA throughput of the current device: FP64
+ * (precision = MALBEC_FP64) or FP32 (MALBEC_FP32_MIXED) dependent-chain-free
+ * FMA loop, all SMs, timed with CUDA events.  Blocks the calling thread.
+ * Writes GFLOP/s (2 flops per FMA). */
+int malbec_measure_fma_peak(malbec_precision prec, double* gflops);
+
+/* Library build information (static string). */
+const char* malbec_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -249,8 +249,8 @@ static int all_finite(const double y[8]) {
 /* Integrate one ray.  After every completed step: captured if the radius
  * reached (1+eps) r_+ (the paper's per-thread horizon stop, Sec. 5) -- at the
  * new state or at any of the step's intermediate stage points, since a stage
- * that lands inside r_+ (Delta < 0) spoils the whole step; escaped if
- * r >= r_esc; non-finite if any component is not finite; after n_steps_cap
+ * that lands inside r_+ (Delta < 0) spoils the whole step; else non-finite if
+ * any component is not finite; else escaped if r >= r_esc; after n_steps_cap
  * steps: capped.  The reported state is the post-step state.  The step size
  * is fixed (dl) or dl_r_scale * r at the start of the step, held for all four
  * stages.  traj (optional) receives sample k (k*stride steps) at
@@ -273,8 +273,8 @@ int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, dou
     ++n;
     if (ns && n % stride == 0) memcpy(traj + (size_t)(n / stride) * 8, y, 8 * sizeof(double));
     if (y[1] <= r_cap || r_stage_min <= r_cap) { fate = ORC_FATE_CAPTURED; break; }
-    if (y[1] >= t->r_esc) { fate = ORC_FATE_ESCAPED; break; }
     if (!all_finite(y)) { fate = ORC_FATE_NONFINITE; break; }
+    if (y[1] >= t->r_esc) { fate = ORC_FATE_ESCAPED; break; }
   }
   if (ns)
     for (uint32_t k = n / stride + 1; k < ns; ++k)

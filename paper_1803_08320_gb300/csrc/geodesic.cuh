@@ -1,0 +1,199 @@
+// geodesic.cuh -- device-side geodesic right-hand sides, RK4 steps and
+// conserved quantities for the Schwarzschild and Kerr metrics in
+// Boyer-Lindquist coordinates (Quiroga, arXiv:1803.08320, Sec. 2 eq. kerr,
+// Sec. 4 for a = 0).
+//
+// The acceleration du^mu/dl = -Gamma^mu_ab u^a u^b is evaluated per metric in
+// closed form.  Kerr uses Gamma^mu_ab u^a u^b = g^{mu nu} W_nu with the
+// first-kind contraction W_nu = Gamma_{nu ab} u^a u^b
+//   = (d_a g_{nu b}) u^a u^b - 1/2 (d_nu g_ab) u^a u^b,
+// which only needs the five metric components, their r- and theta-
+// derivatives along u (the metric depends on r and theta alone) and the
+// closed-form inverse of the (t, phi) block (det = -Delta sin^2).  It is the
+// same bilinear form as the twenty second-kind symbols of BL Kerr, with far
+// fewer operations.  Schwarzschild uses its nine non-zero second-kind symbols
+// directly.  One division per evaluation: 1/rho^2, 1/Delta and 1/sin^2 are
+// products of 1/(rho^2 Delta sin^2).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace malbec {
+
+template <typename T>
+struct Trig;
+template <>
+struct Trig<double> {
+  __device__ __forceinline__ static void sc(double x, double* s, double* c) { sincos(x, s, c); }
+};
+template <>
+struct Trig<float> {
+  __device__ __forceinline__ static void sc(float x, float* s, float* c) { sincosf(x, s, c); }
+};
+
+template <typename T>
+struct BH {
+  T M, a, a2, twoM;
+};
+
+template <typename T>
+__device__ __forceinline__ BH<T> make_bh(double M, double a) {
+  BH<T> b;
+  b.M = T(M);
+  b.a = T(a);
+  b.a2 = T(a * a);
+  b.twoM = T(2.0 * M);
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// Schwarzschild: Gamma^t_tr = M/(r f), Gamma^r_tt = M f / r^3,
+// Gamma^r_rr = -M/(r f), Gamma^r_thth = -f, Gamma^r_phph = -f sin^2,
+// Gamma^th_rth = Gamma^ph_rph = 1/r, Gamma^th_phph = -sin cos,
+// Gamma^ph_thph = cot, with f = r - 2M.
+template <typename T>
+__device__ __forceinline__ void accel_schw(const BH<T>& bh, T r, T th, T ut, T ur, T uth, T uph,
+                                           T acc[4]) {
+  T s, c;
+  Trig<T>::sc(th, &s, &c);
+  const T f = r - bh.twoM;
+  const T rf = r * f;
+  const T inv = T(1) / (rf * s);  // 1 / (r f sin)
+  const T ir = f * s * inv;       // 1/r
+  const T i_f = r * s * inv;      // 1/f
+  const T cot = c * rf * inv;     // cos/sin
+  const T Mirf = bh.M * ir * i_f; // M/(r f)
+  const T ang = fma(s * s * uph, uph, uth * uth);
+  acc[0] = T(-2) * Mirf * ut * ur;
+  acc[1] = fma(f, ang, fma(Mirf * ur, ur, -(bh.M * f * ir * ir * ir) * ut * ut));
+  acc[2] = fma(s * c * uph, uph, T(-2) * ir * ur * uth);
+  acc[3] = T(-2) * uph * fma(ir, ur, cot * uth);
+}
+
+// ---------------------------------------------------------------------------
+// Kerr (see the file header).  q = 2Mr/rho^2, so that
+//   g_tt = q - 1, g_tph = -a s^2 q, g_phph = s^2 (r^2 + a^2 + a^2 s^2 q),
+//   g_rr = rho^2/Delta, g_thth = rho^2,
+//   d_r q = (2M - 2 r q)/rho^2, d_th q = 2 a^2 s c q / rho^2.
+template <typename T>
+__device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T th, T ut, T ur, T uth, T uph,
+                                           T acc[4]) {
+  T s, c;
+  Trig<T>::sc(th, &s, &c);
+  const T a = bh.a, a2 = bh.a2;
+  const T s2 = s * s, sc = s * c;
+  const T r2 = r * r;
+  const T rho2 = fma(a2, c * c, r2);
+  const T Delta = fma(r, r - bh.twoM, a2);
+  const T Ds2 = Delta * s2;
+  const T inv = T(1) / (rho2 * Ds2);
+  const T irho2 = Ds2 * inv;
+  const T iDelta = rho2 * s2 * inv;
+  const T is2 = rho2 * Delta * inv;
+  const T q = bh.twoM * r * irho2;
+  const T dq_r = fma(T(-2) * r, q, bh.twoM) * irho2;
+  const T dq_th = T(2) * a2 * sc * q * irho2;
+  const T r2a2 = r2 + a2;
+  const T s4 = s2 * s2;
+  // d_r and d_theta of g_tt, g_tph, g_phph, g_rr, g_thth
+  const T dtp_r = -a * s2 * dq_r;
+  const T dtp_th = -a * fma(T(2) * sc, q, s2 * dq_th);
+  const T dpp_r = fma(a2 * s4, dq_r, T(2) * r * s2);
+  const T dpp_th = fma(T(2) * sc, r2a2, a2 * fma(T(4) * s2 * sc, q, s4 * dq_th));
+  const T drr_r = fma(-rho2 * T(2) * (r - bh.M), iDelta, T(2) * r) * iDelta;
+  const T drr_th = T(-2) * a2 * sc * iDelta;
+  const T dhh_r = T(2) * r;
+  const T dhh_th = T(-2) * a2 * sc;
+  // derivatives along u: D = u^r d_r + u^th d_th
+  const T Dtt = fma(ur, dq_r, uth * dq_th);
+  const T Dtp = fma(ur, dtp_r, uth * dtp_th);
+  const T Dpp = fma(ur, dpp_r, uth * dpp_th);
+  const T Drr = fma(ur, drr_r, uth * drr_th);
+  const T Dhh = fma(ur, dhh_r, uth * dhh_th);
+  // W_nu = Gamma_{nu ab} u^a u^b
+  const T Wt = fma(Dtt, ut, Dtp * uph);
+  const T Wp = fma(Dtp, ut, Dpp * uph);
+  const T ut2 = ut * ut, uph2 = uph * uph, utp2 = T(2) * ut * uph, ur2 = ur * ur, uth2 = uth * uth;
+  const T Kr = fma(dq_r, ut2, fma(dtp_r, utp2, fma(dpp_r, uph2, fma(drr_r, ur2, dhh_r * uth2))));
+  const T Kth = fma(dq_th, ut2, fma(dtp_th, utp2, fma(dpp_th, uph2, fma(drr_th, ur2, dhh_th * uth2))));
+  const T Wr = fma(Drr, ur, T(-0.5) * Kr);
+  const T Wth = fma(Dhh, uth, T(-0.5) * Kth);
+  // raise with g^{mu nu}: (t, phi) block inverse has det = -Delta sin^2
+  acc[1] = -Wr * Delta * irho2;
+  acc[2] = -Wth * irho2;
+  const T gpp_s2 = fma(a2 * s2, q, r2a2);
+  acc[0] = fma(gpp_s2, Wt, a * q * Wp) * iDelta;
+  acc[3] = fma(q - T(1), Wp, a * s2 * q * Wt) * iDelta * is2;
+}
+
+template <bool kKerr, typename T>
+__device__ __forceinline__ void accel(const BH<T>& bh, T r, T th, T ut, T ur, T uth, T uph, T acc[4]) {
+  if (kKerr)
+    accel_kerr<T>(bh, r, th, ut, ur, uth, uph, acc);
+  else
+    accel_schw<T>(bh, r, th, ut, ur, uth, uph, acc);
+}
+
+// ---------------------------------------------------------------------------
+// One classical RK4 step (tableau c = (0, 1/2, 1/2, 1), b = (1, 2, 2, 1)/6)
+// of y = (x, u).  t and phi never enter the right-hand side, so their stage
+// values are not formed.  Returns the smallest radius among the three
+// intermediate stage points (used by the capture test).
+template <bool kKerr, typename T>
+__device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
+  const T hh = T(0.5) * h;
+  T a1[4], a2[4], a3[4], a4[4];
+  accel<kKerr, T>(bh, y[1], y[2], y[4], y[5], y[6], y[7], a1);
+  T u2[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u2[j] = fma(hh, a1[j], y[4 + j]);
+  const T r2 = fma(hh, y[5], y[1]), th2 = fma(hh, y[6], y[2]);
+  accel<kKerr, T>(bh, r2, th2, u2[0], u2[1], u2[2], u2[3], a2);
+  T u3[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u3[j] = fma(hh, a2[j], y[4 + j]);
+  const T r3 = fma(hh, u2[1], y[1]), th3 = fma(hh, u2[2], y[2]);
+  accel<kKerr, T>(bh, r3, th3, u3[0], u3[1], u3[2], u3[3], a3);
+  T u4[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u4[j] = fma(h, a3[j], y[4 + j]);
+  const T r4 = fma(h, u3[1], y[1]), th4 = fma(h, u3[2], y[2]);
+  accel<kKerr, T>(bh, r4, th4, u4[0], u4[1], u4[2], u4[3], a4);
+  const T h6 = h * T(1.0 / 6.0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const T dx = y[4 + j] + T(2) * u2[j] + T(2) * u3[j] + u4[j];
+    const T du = a1[j] + T(2) * a2[j] + T(2) * a3[j] + a4[j];
+    y[j] = fma(h6, dx, y[j]);
+    y[4 + j] = fma(h6, du, y[4 + j]);
+  }
+  return fmin(fmin(r2, r3), r4);
+}
+
+// ---------------------------------------------------------------------------
+// Conserved quantities in FP64: p = g u; E = -p_t, L_z = p_ph,
+// Q = p_th^2 + cos^2 (a^2 (mu^2 - E^2) + L_z^2 / sin^2) with mu^2 = -g(u,u),
+// norm = g(u,u).
+__device__ __forceinline__ void invariants64(double M, double a, const double y[8], double inv[4]) {
+  double s, c;
+  sincos(y[2], &s, &c);
+  const double r = y[1], a2 = a * a, s2 = s * s;
+  const double rho2 = fma(a2, c * c, r * r);
+  const double Delta = fma(r, r - 2.0 * M, a2);
+  const double q = 2.0 * M * r / rho2;
+  const double gtt = q - 1.0;
+  const double gtp = -a * s2 * q;
+  const double gpp = s2 * fma(a2 * s2, q, r * r + a2);
+  const double pt = fma(gtt, y[4], gtp * y[7]);
+  const double pp = fma(gtp, y[4], gpp * y[7]);
+  const double pr = rho2 / Delta * y[5];
+  const double pth = rho2 * y[6];
+  const double norm = fma(pt, y[4], fma(pr, y[5], fma(pth, y[6], pp * y[7])));
+  const double E = -pt;
+  inv[0] = E;
+  inv[1] = pp;
+  inv[2] = fma(pth, pth, c * c * fma(a2, -norm - E * E, pp * pp / s2));
+  inv[3] = norm;
+}
+
+}  // namespace malbec

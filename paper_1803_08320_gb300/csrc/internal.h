@@ -1,0 +1,81 @@
+// internal.h -- host-side declarations shared by the translation units of
+// libmalbec.so (not part of the public ABI; see include/malbec.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/malbec.h"
+
+namespace malbec {
+
+enum Source : int { kSrcStates = 0, kSrcCamera = 1 };
+enum Sink : int { kSinkFinal = 0, kSinkStrided = 1, kSinkCamera = 2 };
+
+// Per-image constants of the backward camera (computed on the host in FP64).
+struct CameraConst {
+  double r_obs, incl, fov_half;
+  uint32_t nx, ny;
+  double so, co;             // sin, cos of the inclination
+  double Delta_o, r2a2_o;    // Delta(r_obs), r_obs^2 + a^2
+  double gtt, gtp, gpp, grr, ghh;  // inverse metric at the observer
+};
+
+struct TraceParams {
+  // black hole
+  double M, a;
+  const double* a_per_ray;
+  // step rule / termination
+  double eps_hor, r_esc, dl, dl_r_scale;
+  uint32_t cap;
+  // rays
+  const double* ics;  // SoA [8][n] (kSrcStates)
+  uint64_t n;
+  CameraConst cam;    // kSrcCamera
+  // outputs (kSinkFinal / kSinkStrided)
+  double* y_out;
+  double* lambda_out;
+  double* inv0_out;
+  double* inv1_out;
+  uint32_t* steps_out;
+  uint8_t* fate_out;
+  void* traj;
+  uint32_t stride;
+  uint64_t n_samples;
+  // outputs (kSinkCamera)
+  double* theta_out;
+  double* phi_out;
+  // FP32_MIXED FP64 zone (malbec_mixed_zone)
+  double zone_horizon, zone_photon, zone_pole;
+  // work queue (scratch, zeroed before launch)
+  unsigned long long* head;
+  // launch shape
+  int refill_min;  // refill when at least this many lanes of a warp are idle
+};
+
+struct LaunchShape {
+  int threads_per_block;
+  int blocks;
+};
+
+// trace.cu
+cudaError_t launch_trace(const TraceParams& p, bool kerr, bool mixed, Source src, Sink sink,
+                         const LaunchShape& shape, cudaStream_t stream);
+int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, int threads_per_block);
+
+// ic.cu
+cudaError_t launch_ic_circular(double M, double a, const double* radii, uint64_t n, int prograde,
+                               double* ics, cudaStream_t stream);
+cudaError_t launch_ic_camera(double M, double a, const CameraConst& cam, const uint64_t* pixels,
+                             uint64_t n, double* ics, cudaStream_t stream);
+cudaError_t launch_ic_bound(double M, double a_max, int spin_fixed, uint64_t seed, uint64_t index0,
+                            uint64_t n, double* ics, double* spins, int32_t* accepted,
+                            cudaStream_t stream);
+cudaError_t launch_invariants(double M, double a, const double* a_per_ray, const double* states,
+                              uint64_t n, double* inv, cudaStream_t stream);
+
+// api.cu
+int set_cuda_error(cudaError_t e);
+void fill_zone(TraceParams& p);
+CameraConst make_camera_const(double M, double a, const malbec_camera& cam);
+
+}  // namespace malbec

@@ -1,0 +1,354 @@
+// trace.cu -- persistent work-queue RK4 geodesic kernels.
+//
+// One ray per lane.  Warps stay resident and pull ray indices from a device
+// counter: after every RK4 step each lane tests its ray for termination
+// (capture at (1+eps) r_+, escape, non-finite, step cap; the paper's
+// per-thread horizon stop, Sec. 5), a warp ballot counts idle lanes, and once
+// at least `refill_min` lanes are idle the warp takes that many new rays with
+// a single atomicAdd and hands them to the idle lanes.  Rays therefore never
+// share a lane's time with a long-running neighbour; results do not depend on
+// which lane or warp ran a ray.
+//
+// Precision: FP64 (every operation in double), or FP32_MIXED: the state is
+// kept as a compensated pair (hi, lo) of floats, the RHS and RK4 stages run in
+// FP32, and the increments h/6 (k1 + 2k2 + 2k3 + k4) -- with h/6 as a float
+// pair -- are added with TwoSum.  lambda is accumulated in FP64 and the
+// invariants are evaluated in FP64; a step whose start lies inside the FP64
+// zone (near the horizon, near the photon orbits for null rays, or near the
+// polar axis where the BL Christoffel symbols diverge) runs entirely in FP64.  An FP32 step costs one FP64 add (lambda): on a part
+// whose FP64 rate is 1/64 of its FP32 rate every FP64 operation in the bulk
+// path counts.  FP32 steps test termination on the hi words against the
+// thresholds rounded to float.
+#include <math.h>
+
+#include "camera.cuh"
+#include "geodesic.cuh"
+#include "internal.h"
+
+namespace malbec {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxTPB = 256;
+
+__device__ __forceinline__ double dev_r_plus(double M, double a) { return M + sqrt(fma(-a, a, M * M)); }
+
+// Retrograde circular photon orbit 2M (1 + cos(2/3 arccos(a/M))).
+__device__ __forceinline__ double dev_r_photon_retro(double M, double a) {
+  return 2.0 * M * (1.0 + cos((2.0 / 3.0) * acos(a / M)));
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += d + d_err, renormalised so that hi = fl(hi + lo).
+__device__ __forceinline__ void comp_add(float& hi, float& lo, float d, float d_err) {
+  float s, e;
+  two_sum(hi, d, s, e);
+  e += lo + d_err;
+  two_sum(s, e, hi, lo);
+}
+
+// Non-finite test on the exponent bits (integer pipe, no FP64 compare).
+__device__ __forceinline__ bool finite8(const double y[8]) {
+  int bad = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) bad |= ((__double2hiint(y[c]) & 0x7ff00000) == 0x7ff00000);
+  return !bad;
+}
+__device__ __forceinline__ bool finite8f(const float y[8]) {
+  int bad = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) bad |= ((__float_as_int(y[c]) & 0x7f800000) == 0x7f800000);
+  return !bad;
+}
+
+template <bool kMixed>
+__device__ __forceinline__ void store_sample(const TraceParams& p, uint64_t id, uint64_t k, const double y[8],
+                                             const float hi[8]) {
+  const size_t off = ((size_t)id * p.n_samples + k) * 8;
+  if (kMixed) {
+    float4* t = reinterpret_cast<float4*>(static_cast<float*>(p.traj) + off);
+    t[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    t[1] = make_float4(hi[4], hi[5], hi[6], hi[7]);
+  } else {
+    double2* t = reinterpret_cast<double2*>(static_cast<double*>(p.traj) + off);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) t[c] = make_double2(y[2 * c], y[2 * c + 1]);
+  }
+}
+
+template <bool kMixed>
+__device__ __forceinline__ void store_nan_samples(const TraceParams& p, uint64_t id, uint64_t k0) {
+  for (uint64_t k = k0; k < p.n_samples; ++k) {
+    const size_t off = ((size_t)id * p.n_samples + k) * 8;
+    if (kMixed) {
+      const float fn = __int_as_float(0x7fc00000);
+      float4* t = reinterpret_cast<float4*>(static_cast<float*>(p.traj) + off);
+      t[0] = make_float4(fn, fn, fn, fn);
+      t[1] = make_float4(fn, fn, fn, fn);
+    } else {
+      const double qn = __longlong_as_double(0x7ff8000000000000ll);
+      double2* t = reinterpret_cast<double2*>(static_cast<double*>(p.traj) + off);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) t[c] = make_double2(qn, qn);
+    }
+  }
+}
+
+// One FP32 RK4 step on the compensated state (hi, lo).  The stage points are
+// hi + (lo + c h k), so the low words enter the right-hand side; the
+// increments h/6 (k1 + 2k2 + 2k3 + k4) use h/6 as a float pair (h6h, h6l) and
+// are added with TwoSum.  Returns the smallest stage radius.
+template <bool kKerr>
+__device__ __forceinline__ float rk4_step_mixed(const BH<float>& bh, float hf, float h6h, float h6l, float hi[8],
+                                                float lo[8]) {
+  const float hh = 0.5f * hf;
+  float a1[4], a2[4], a3[4], a4[4], u2[4], u3[4], u4[4];
+  accel<kKerr, float>(bh, hi[1], hi[2], hi[4], hi[5], hi[6], hi[7], a1);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u2[j] = hi[4 + j] + fmaf(hh, a1[j], lo[4 + j]);
+  const float r2 = hi[1] + fmaf(hh, hi[5], lo[1]);
+  const float th2 = hi[2] + fmaf(hh, hi[6], lo[2]);
+  accel<kKerr, float>(bh, r2, th2, u2[0], u2[1], u2[2], u2[3], a2);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u3[j] = hi[4 + j] + fmaf(hh, a2[j], lo[4 + j]);
+  const float r3 = hi[1] + fmaf(hh, u2[1], lo[1]);
+  const float th3 = hi[2] + fmaf(hh, u2[2], lo[2]);
+  accel<kKerr, float>(bh, r3, th3, u3[0], u3[1], u3[2], u3[3], a3);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u4[j] = hi[4 + j] + fmaf(hf, a3[j], lo[4 + j]);
+  const float r4 = hi[1] + fmaf(hf, u3[1], lo[1]);
+  const float th4 = hi[2] + fmaf(hf, u3[2], lo[2]);
+  accel<kKerr, float>(bh, r4, th4, u4[0], u4[1], u4[2], u4[3], a4);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float sx = fmaf(2.f, u2[j] + u3[j], hi[4 + j] + u4[j]);
+    const float su = fmaf(2.f, a2[j] + a3[j], a1[j] + a4[j]);
+    const float dx = h6h * sx;
+    const float dxe = fmaf(h6h, sx, -dx) + h6l * sx;
+    const float du = h6h * su;
+    const float due = fmaf(h6h, su, -du) + h6l * su;
+    comp_add(hi[j], lo[j], dx, dxe);
+    comp_add(hi[4 + j], lo[4 + j], du, due);
+  }
+  return fminf(fminf(r2, r3), r4);
+}
+
+__device__ __forceinline__ void split_pair(const double y[8], float hi[8], float lo[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    hi[c] = (float)y[c];
+    lo[c] = (float)(y[c] - (double)hi[c]);
+  }
+}
+
+template <bool kKerr, bool kMixed, int kSrc, int kSink>
+__global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const double M = p.M;
+  // FP32-path constants: fixed step as a float pair, 1/6 as a float pair
+  const float h_fix = (float)p.dl;
+  const double h6_fix = p.dl / 6.0;
+  const float h6_fix_h = (float)h6_fix, h6_fix_l = (float)(h6_fix - (double)h6_fix_h);
+  const float k6h = (float)(1.0 / 6.0), k6l = (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0));
+  const float scale_f = (float)p.dl_r_scale;
+  const float r_esc_f = (float)p.r_esc;
+  const float pole_f = (float)p.zone_pole;
+
+  double y[8];
+  float hi[8], lo[8];
+  double lam = 0.0;
+  uint32_t nst = 0;
+  uint64_t id = 0;
+  double a = p.a, r_cap = 0.0;
+  float r_cap_f = 0.f, r_zone_f = 0.f;
+  bool active = false, drained = false;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    y[c] = 0.0;
+    hi[c] = 0.f;
+    lo[c] = 0.f;
+  }
+
+  while (true) {
+    const unsigned act = __ballot_sync(kFull, active);
+    const int idle = 32 - __popc(act);
+    if (!drained && idle > 0 && (idle >= p.refill_min || act == 0)) {
+      // ---- hand the next `idle` rays of the queue to the idle lanes
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(p.head, (unsigned long long)idle);
+      base = __shfl_sync(kFull, base, 0);
+      if (base + (unsigned long long)idle >= p.n) drained = true;
+      const unsigned long long my = base + __popc(~act & lt_mask);
+      if (!active && my < p.n) {
+        id = my;
+        active = true;
+        if (kSrc == kSrcStates) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) y[c] = p.ics[(size_t)c * p.n + id];
+          if (p.a_per_ray) a = p.a_per_ray[id];
+        } else {
+          camera_state(p.cam, a, id, y);
+        }
+        const double rp = dev_r_plus(M, a);
+        r_cap = (1.0 + p.eps_hor) * rp;
+        lam = 0.0;
+        nst = 0;
+        if (kMixed || kSink != kSinkCamera) {
+          double inv[4];
+          invariants64(M, a, y, inv);
+          if (kSink != kSinkCamera) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) p.inv0_out[(size_t)c * p.n + id] = inv[c];
+          }
+          if (kMixed) {
+            const double cth = cos(y[2]);
+            const double gtt = 2.0 * M * y[1] / fma(a * a, cth * cth, y[1] * y[1]) - 1.0;
+            const bool is_null = fabs(inv[3]) <= 1e-6 * fabs(gtt) * y[4] * y[4];
+            double rz = p.zone_horizon * rp;
+            if (is_null) rz = fmax(rz, dev_r_photon_retro(M, a) + p.zone_photon * M);
+            r_zone_f = (float)rz;
+            r_cap_f = (float)r_cap;
+            split_pair(y, hi, lo);
+          }
+        }
+        if (kSink == kSinkStrided) store_sample<kMixed>(p, id, 0, y, hi);
+      }
+      continue;
+    }
+    if (act == 0) break;  // queue drained and no lane busy
+    if (!active) continue;
+
+    int fate = 0;
+    if (nst < p.cap) {
+      // ---- one RK4 step
+      bool captured, escaped, finite;
+      if (!kMixed) {
+        const double h = p.dl_r_scale > 0.0 ? p.dl_r_scale * y[1] : p.dl;
+        const double rmin = rk4_step<kKerr, double>(make_bh<double>(M, a), h, y);
+        lam += h;
+        captured = (y[1] <= r_cap) | (rmin <= r_cap);
+        escaped = y[1] >= p.r_esc;
+        finite = finite8(y);
+      } else if (hi[1] < r_zone_f || fabsf(__sinf(hi[2])) < pole_f) {
+        // FP64 zone (horizon, photon orbits, polar axis)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
+        const double h = p.dl_r_scale > 0.0 ? p.dl_r_scale * y[1] : p.dl;
+        const double rmin = rk4_step<kKerr, double>(make_bh<double>(M, a), h, y);
+        lam += h;
+        split_pair(y, hi, lo);
+        captured = (y[1] <= r_cap) | (rmin <= r_cap);
+        escaped = y[1] >= p.r_esc;
+        finite = finite8(y);
+      } else {
+        float hf, h6h, h6l;
+        if (p.dl_r_scale > 0.0) {
+          hf = scale_f * hi[1];
+          h6h = hf * k6h;
+          h6l = fmaf(hf, k6h, -h6h) + hf * k6l;
+          lam += (double)hf;
+        } else {
+          hf = h_fix;
+          h6h = h6_fix_h;
+          h6l = h6_fix_l;
+          lam += p.dl;
+        }
+        const float rmin = rk4_step_mixed<kKerr>(make_bh<float>(M, a), hf, h6h, h6l, hi, lo);
+        captured = (hi[1] <= r_cap_f) | (rmin <= r_cap_f);
+        escaped = hi[1] >= r_esc_f;
+        finite = finite8f(hi) & finite8f(lo);
+      }
+      ++nst;
+      if (kSink == kSinkStrided && (nst % p.stride) == 0) store_sample<kMixed>(p, id, nst / p.stride, y, hi);
+      // ---- termination tests, in the documented order
+      if (captured)
+        fate = MALBEC_FATE_CAPTURED;
+      else if (!finite)
+        fate = MALBEC_FATE_NONFINITE;
+      else if (escaped)
+        fate = MALBEC_FATE_ESCAPED;
+      else if (nst >= p.cap)
+        fate = MALBEC_FATE_CAPPED;
+    } else {
+      fate = MALBEC_FATE_CAPPED;  // n_steps_cap == 0
+    }
+
+    if (fate != 0) {
+      if (kMixed) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
+      }
+      if (kSink == kSinkCamera) {
+        p.fate_out[id] = (uint8_t)fate;
+        p.steps_out[id] = nst;
+        p.theta_out[id] = y[2];
+        p.phi_out[id] = y[3];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) p.y_out[(size_t)c * p.n + id] = y[c];
+        p.lambda_out[id] = lam;
+        p.steps_out[id] = nst;
+        p.fate_out[id] = (uint8_t)fate;
+        double inv[4];
+        invariants64(M, a, y, inv);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p.inv1_out[(size_t)c * p.n + id] = inv[c];
+        if (kSink == kSinkStrided) store_nan_samples<kMixed>(p, id, (uint64_t)nst / p.stride + 1);
+      }
+      active = false;
+    }
+  }
+}
+
+template <bool kKerr, bool kMixed, int kSrc, int kSink>
+const void* kernel_ptr() {
+  return reinterpret_cast<const void*>(&trace_kernel<kKerr, kMixed, kSrc, kSink>);
+}
+
+const void* pick(bool kerr, bool mixed, Source src, Sink sink) {
+#define MALBEC_PICK(K, X, S, T) \
+  if (kerr == K && mixed == X && src == S && sink == T) return kernel_ptr<K, X, S, T>();
+  MALBEC_PICK(false, false, kSrcStates, kSinkFinal)
+  MALBEC_PICK(true, false, kSrcStates, kSinkFinal)
+  MALBEC_PICK(false, true, kSrcStates, kSinkFinal)
+  MALBEC_PICK(true, true, kSrcStates, kSinkFinal)
+  MALBEC_PICK(false, false, kSrcStates, kSinkStrided)
+  MALBEC_PICK(true, false, kSrcStates, kSinkStrided)
+  MALBEC_PICK(false, true, kSrcStates, kSinkStrided)
+  MALBEC_PICK(true, true, kSrcStates, kSinkStrided)
+  MALBEC_PICK(false, false, kSrcCamera, kSinkCamera)
+  MALBEC_PICK(true, false, kSrcCamera, kSinkCamera)
+  MALBEC_PICK(false, true, kSrcCamera, kSinkCamera)
+  MALBEC_PICK(true, true, kSrcCamera, kSinkCamera)
+#undef MALBEC_PICK
+  return nullptr;
+}
+
+}  // namespace
+
+int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, int threads_per_block) {
+  const void* k = pick(kerr, mixed, src, sink);
+  if (!k) return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads_per_block, 0) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_trace(const TraceParams& p, bool kerr, bool mixed, Source src, Sink sink,
+                         const LaunchShape& shape, cudaStream_t stream) {
+  const void* k = pick(kerr, mixed, src, sink);
+  if (!k) return cudaErrorInvalidValue;
+  if (shape.threads_per_block <= 0 || shape.threads_per_block > kMaxTPB ||
+      shape.threads_per_block % 32 != 0 || shape.blocks <= 0)
+    return cudaErrorInvalidConfiguration;
+  void* args[] = {const_cast<TraceParams*>(&p)};
+  return cudaLaunchKernel(k, dim3(shape.blocks), dim3(shape.threads_per_block), args, 0, stream);
+}
+
+}  // namespace malbec

@@ -1,0 +1,321 @@
+"""Python binding of libmalbec.so: argument marshalling only.
+
+Every step of the geodesic path runs in the library's CUDA kernels; this module
+allocates device buffers with PyTorch, passes raw pointers and the current CUDA
+stream through ctypes, and returns tensor views into the library's output
+layout.  There is no CPU fallback: if the library is missing or no GPU is
+present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmalbec.so")
+
+FP64, FP32_MIXED = 0, 1
+OUT_FINAL, OUT_STRIDED = 0, 1
+FATE_CAPTURED, FATE_ESCAPED, FATE_CAPPED, FATE_NONFINITE = 1, 2, 3, 4
+OK, EINVAL, ENOMEM, EBUSY, ETIMEDOUT, ECUDA, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
+
+_D = ctypes.c_double
+_U32 = ctypes.c_uint32
+_U64 = ctypes.c_uint64
+_SZ = ctypes.c_size_t
+_VP = ctypes.c_void_p
+
+
+class Metric(ctypes.Structure):
+    _fields_ = [("M", _D), ("a", _D), ("a_per_ray", _VP)]
+
+
+class Term(ctypes.Structure):
+    _fields_ = [("eps_hor", _D), ("r_esc", _D), ("n_steps_cap", _U32), ("dl", _D), ("dl_r_scale", _D)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("r_obs", _D), ("incl", _D), ("fov_half", _D), ("nx", _U32), ("ny", _U32)]
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [("y", _SZ), ("lam", _SZ), ("inv0", _SZ), ("inv1", _SZ), ("steps", _SZ), ("fate", _SZ),
+                ("traj", _SZ), ("n_samples", _U64), ("total", _SZ)]
+
+
+class CameraLayout(ctypes.Structure):
+    _fields_ = [("fate", _SZ), ("steps", _SZ), ("theta", _SZ), ("phi", _SZ), ("total", _SZ)]
+
+
+class MixedZone(ctypes.Structure):
+    _fields_ = [("horizon_factor", _D), ("photon_margin", _D), ("pole_sin", _D)]
+
+
+class MalbecError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = f"{where}: {strerror(code)}"
+        if code == ECUDA:
+            msg += f" ({last_cuda_error()})"
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libmalbec.so (built by paper_1803_08320_gb300.build).  Raises if it
+    has not been built: there is no fallback path."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not found: build it with `python -m paper_1803_08320_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def _declare(L):
+    def sig(name, res, *args):
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = list(args)
+
+    sig("malbec_strerror", ctypes.c_char_p, ctypes.c_int)
+    sig("malbec_last_cuda_error", ctypes.c_char_p)
+    sig("malbec_build_info", ctypes.c_char_p)
+    sig("malbec_out_layout", ctypes.c_int, ctypes.c_int, ctypes.c_int, _U64, _U32, _U32, ctypes.POINTER(Layout))
+    sig("malbec_out_bytes", _SZ, ctypes.c_int, ctypes.c_int, _U64, _U32, _U32)
+    sig("malbec_trace", ctypes.c_int, Metric, _VP, _U64, Term, ctypes.c_int, _U32, ctypes.c_int, _VP, _VP)
+    sig("malbec_camera_out_layout", ctypes.c_int, ctypes.POINTER(Camera), ctypes.POINTER(CameraLayout))
+    sig("malbec_trace_camera", ctypes.c_int, Metric, ctypes.POINTER(Camera), Term, ctypes.c_int, _VP, _VP)
+    sig("malbec_ic_camera", ctypes.c_int, Metric, ctypes.POINTER(Camera), _VP, _U64, _VP, _VP)
+    sig("malbec_ic_circular", ctypes.c_int, Metric, _VP, _U64, ctypes.c_int, _VP, _VP)
+    sig("malbec_ic_bound", ctypes.c_int, _D, _D, ctypes.c_int, _U64, _U64, _U64, _VP, _VP, _VP, _VP)
+    sig("malbec_invariants", ctypes.c_int, Metric, _VP, _U64, _VP, _VP)
+    sig("malbec_measure_fma_peak", ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D))
+    sig("malbec_set_mixed_zone", ctypes.c_int, ctypes.POINTER(MixedZone))
+    sig("malbec_get_mixed_zone", ctypes.c_int, ctypes.POINTER(MixedZone))
+
+
+def strerror(code: int) -> str:
+    return lib().malbec_strerror(code).decode()
+
+
+def last_cuda_error() -> str:
+    return lib().malbec_last_cuda_error().decode()
+
+
+def build_info() -> str:
+    return lib().malbec_build_info().decode()
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise MalbecError(code, where)
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _VP(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else _VP(t.data_ptr())
+
+
+def _dev_f64(x, n_expected=None):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor):
+        x = torch.as_tensor(np.asarray(x, dtype=np.float64))
+    if x.device.type != "cuda":
+        x = x.to("cuda")
+    x = x.to(torch.float64).contiguous()
+    return x
+
+
+@dataclass
+class Termination:
+    eps_hor: float = 0.01
+    r_esc: float = 1100.0
+    n_steps_cap: int = 10_000
+    dl: float = 0.01
+    dl_r_scale: float = 0.0
+
+    def c(self) -> Term:
+        return Term(float(self.eps_hor), float(self.r_esc), int(self.n_steps_cap), float(self.dl),
+                    float(self.dl_r_scale))
+
+
+def term_from(t) -> Termination:
+    if isinstance(t, Termination):
+        return t
+    return Termination(t.eps_hor, t.r_esc, t.n_steps_cap, t.dl, t.dl_r_scale)
+
+
+def _prec(p) -> int:
+    if isinstance(p, str):
+        return {"fp64": FP64, "fp32_mixed": FP32_MIXED, "mixed": FP32_MIXED}[p]
+    return int(p)
+
+
+def out_layout(mode: int, precision, n: int, n_steps_cap: int, stride: int) -> Layout:
+    L = Layout()
+    _check(lib().malbec_out_layout(mode, _prec(precision), n, n_steps_cap, stride, ctypes.byref(L)),
+           "malbec_out_layout")
+    return L
+
+
+def _views_final(buf, L: Layout, n: int, mode: int, precision):
+    torch = _torch()
+
+    def v(off, count, dtype, shape):
+        itemsize = torch.empty((), dtype=dtype).element_size()
+        return buf[off: off + count * itemsize].view(dtype).view(*shape)
+
+    out = {
+        "y": v(L.y, 8 * n, torch.float64, (8, n)),
+        "lambda": v(L.lam, n, torch.float64, (n,)),
+        "inv0": v(L.inv0, 4 * n, torch.float64, (4, n)),
+        "inv1": v(L.inv1, 4 * n, torch.float64, (4, n)),
+        "steps": v(L.steps, n, torch.int32, (n,)),
+        "fate": v(L.fate, n, torch.uint8, (n,)),
+        "buffer": buf,
+    }
+    if mode == OUT_STRIDED:
+        ns = int(L.n_samples)
+        dt = torch.float64 if _prec(precision) == FP64 else torch.float32
+        out["traj"] = v(L.traj, n * ns * 8, dt, (n, ns, 8))
+    return out
+
+
+def trace(M: float, a: float, ics, term, mode: int = OUT_FINAL, stride: int = 0, precision="fp64",
+          a_per_ray=None, stream=None, out=None):
+    """Integrate the rays `ics` ((8, n) float64 on the GPU, SoA).  Returns a
+    dict of views: y (8, n), lambda, inv0 (4, n), inv1 (4, n), steps (int32
+    view of the uint32 field), fate, [traj (n, n_samples, 8)]."""
+    torch = _torch()
+    ics = _dev_f64(ics)
+    n = ics.shape[1]
+    t = term_from(term)
+    L = out_layout(mode, precision, n, t.n_steps_cap, stride if mode == OUT_STRIDED else 0)
+    if out is None:
+        out = torch.empty(L.total, dtype=torch.uint8, device=ics.device)
+    apr = None if a_per_ray is None else _dev_f64(a_per_ray)
+    m = Metric(float(M), float(a), _ptr(apr))
+    _check(lib().malbec_trace(m, _ptr(ics), n, t.c(), mode, stride if mode == OUT_STRIDED else 0,
+                              _prec(precision), _ptr(out), _stream(stream)), "malbec_trace")
+    res = _views_final(out, L, n, mode, precision)
+    res["_keep"] = (ics, apr)
+    return res
+
+
+def camera_layout(cam: Camera) -> CameraLayout:
+    L = CameraLayout()
+    _check(lib().malbec_camera_out_layout(ctypes.byref(cam), ctypes.byref(L)), "malbec_camera_out_layout")
+    return L
+
+
+def make_camera(r_obs, incl, fov_half, nx, ny) -> Camera:
+    return Camera(float(r_obs), float(incl), float(fov_half), int(nx), int(ny))
+
+
+def trace_camera(M: float, a: float, cam: Camera, term, precision="fp64", stream=None, out=None):
+    """Render the backward camera.  Returns views fate (n,), steps, theta, phi."""
+    torch = _torch()
+    L = camera_layout(cam)
+    n = cam.nx * cam.ny
+    if out is None:
+        out = torch.empty(L.total, dtype=torch.uint8, device="cuda")
+    _check(lib().malbec_trace_camera(Metric(float(M), float(a), None), ctypes.byref(cam), term_from(term).c(),
+                                     _prec(precision), _ptr(out), _stream(stream)), "malbec_trace_camera")
+    return {
+        "fate": out[L.fate: L.fate + n],
+        "steps": out[L.steps: L.steps + 4 * n].view(torch.int32),
+        "theta": out[L.theta: L.theta + 8 * n].view(torch.float64),
+        "phi": out[L.phi: L.phi + 8 * n].view(torch.float64),
+        "buffer": out,
+    }
+
+
+def ic_camera(M: float, a: float, cam: Camera, pixels, stream=None):
+    torch = _torch()
+    px = torch.as_tensor(np.asarray(pixels, dtype=np.int64)).to("cuda")
+    n = px.numel()
+    ics = torch.empty((8, n), dtype=torch.float64, device="cuda")
+    _check(lib().malbec_ic_camera(Metric(float(M), float(a), None), ctypes.byref(cam), _ptr(px), n, _ptr(ics),
+                                  _stream(stream)), "malbec_ic_camera")
+    return ics
+
+
+def ic_circular(M: float, a: float, radii, prograde: bool = True, stream=None):
+    torch = _torch()
+    r = _dev_f64(radii)
+    n = r.numel()
+    ics = torch.empty((8, n), dtype=torch.float64, device="cuda")
+    _check(lib().malbec_ic_circular(Metric(float(M), float(a), None), _ptr(r), n, int(bool(prograde)), _ptr(ics),
+                                    _stream(stream)), "malbec_ic_circular")
+    return ics
+
+
+def ic_bound(M: float, a_max: float, seed: int, n: int, index0: int = 0, spin_fixed: bool = False, stream=None):
+    """Generic bound-orbit ensemble: returns (ics (8, n), spins (n,), accepted (n,) int32)."""
+    torch = _torch()
+    ics = torch.empty((8, n), dtype=torch.float64, device="cuda")
+    spins = torch.empty(n, dtype=torch.float64, device="cuda")
+    acc = torch.empty(n, dtype=torch.int32, device="cuda")
+    _check(lib().malbec_ic_bound(float(M), float(a_max), int(bool(spin_fixed)), int(seed) & (2**64 - 1),
+                                 int(index0), int(n), _ptr(ics), _ptr(spins), _ptr(acc), _stream(stream)),
+           "malbec_ic_bound")
+    return ics, spins, acc
+
+
+def invariants(M: float, a: float, states, a_per_ray=None, stream=None):
+    torch = _torch()
+    y = _dev_f64(states)
+    n = y.shape[1]
+    inv = torch.empty((4, n), dtype=torch.float64, device="cuda")
+    apr = None if a_per_ray is None else _dev_f64(a_per_ray)
+    _check(lib().malbec_invariants(Metric(float(M), float(a), _ptr(apr)), _ptr(y), n, _ptr(inv), _stream(stream)),
+           "malbec_invariants")
+    return inv
+
+
+def set_mixed_zone(horizon_factor=None, photon_margin=None, pole_sin=None, reset=False):
+    """Change the FP64 zone of the FP32_MIXED path (None keeps a field)."""
+    if reset:
+        _check(lib().malbec_set_mixed_zone(None), "malbec_set_mixed_zone")
+        return get_mixed_zone()
+    z = get_mixed_zone()
+    if horizon_factor is not None:
+        z.horizon_factor = float(horizon_factor)
+    if photon_margin is not None:
+        z.photon_margin = float(photon_margin)
+    if pole_sin is not None:
+        z.pole_sin = float(pole_sin)
+    _check(lib().malbec_set_mixed_zone(ctypes.byref(z)), "malbec_set_mixed_zone")
+    return z
+
+
+def get_mixed_zone() -> MixedZone:
+    z = MixedZone()
+    _check(lib().malbec_get_mixed_zone(ctypes.byref(z)), "malbec_get_mixed_zone")
+    return z
+
+
+def measure_fma_peak(precision="fp64") -> float:
+    """Measured FMA GFLOP/s of the current GPU (blocks the caller)."""
+    g = _D()
+    _check(lib().malbec_measure_fma_peak(_prec(precision), ctypes.byref(g)), "malbec_measure_fma_peak")
+    return g.value

@@ -704,9 +704,9 @@ def test_bound_orbit_conserves_carter_constant(orc):
 
 # --------------------------------------------------------------------------- termination logic
 def test_termination_fates_and_step_rule(orc):
-    """Captured / escaped / capped / non-finite after each completed step, in
-    that order of precedence; h = dl_r_scale * r at the step start; lambda is
-    the sum of the steps taken."""
+    """Captured / non-finite / escaped after each completed step, in that order
+    of precedence, capped after the last; h = dl_r_scale * r at the step start;
+    lambda is the sum of the steps taken."""
     # radial infall E = 1, L = 0 from r = 10: captured
     y0 = np.zeros(8)
     y0[1], y0[2] = 10.0, math.pi / 2
