@@ -360,6 +360,14 @@ def test_results_independent_of_batch_composition(mb, orc, W):
     inv[perm] = torch.arange(3000, device="cuda")
     assert torch.equal(a["y"], b["y"][:, inv[:100]])
     assert torch.equal(a["steps"], b["steps"][inv[:100]])
+    # FP32_MIXED: the FP64-zone decision is taken per ray, never per warp
+    am = mb.trace(wl.M, 0.0, ics[:, :100], t, precision="fp32_mixed", a_per_ray=spins[:100])
+    bm = mb.trace(wl.M, 0.0, ics[:, perm], t, precision="fp32_mixed", a_per_ray=spins[perm])
+    torch.cuda.synchronize()
+    ya, yb = am["y"], bm["y"][:, inv[:100]]
+    assert torch.equal(torch.isnan(ya), torch.isnan(yb))
+    assert torch.equal(torch.nan_to_num(ya), torch.nan_to_num(yb))
+    assert torch.equal(am["steps"], bm["steps"][inv[:100]])
 
 
 # --------------------------------------------------------------------------- FP32-mixed path
