@@ -45,6 +45,7 @@ typedef struct CUstream_st* malbec_stream; /* == cudaStream_t */
 #define MALBEC_ETIMEDOUT (-4) /* a bounded device-side wait gave up */
 #define MALBEC_ECUDA (-5)     /* CUDA runtime error; see malbec_last_cuda_error() */
 #define MALBEC_ENOTFOUND (-6) /* unknown job id */
+#define MALBEC_ESCRATCH (-7)  /* a no-allocation call needs more scratch than its static block holds */
 
 /* Human-readable text of a MALBEC_* code (static storage, never NULL). */
 const char* malbec_strerror(int code);
@@ -173,6 +174,32 @@ size_t malbec_out_bytes(malbec_out_mode mode, malbec_precision prec, uint64_t n,
 int malbec_trace(malbec_metric m, const double* ics, uint64_t n, malbec_term t,
                  malbec_out_mode mode, uint32_t stride, malbec_precision prec, void* out,
                  malbec_stream stream);
+
+/* malbec_trace for callers that cannot allocate device memory.  (The paper
+ * has no counterpart: this is a property of the library, not of the method.)
+ * Who needs it: code that records work into a CUDA graph under a capture mode
+ * that forbids allocation calls, real-time loops that must never enter the
+ * allocator (an allocation may synchronise or grow a memory pool at an
+ * unpredictable moment), and embedders that hand out every byte of device
+ * memory from their own arena and do not let libraries call cudaMalloc.
+ * Same arguments, validation, results and errors as malbec_trace, but the
+ * 256-byte work-queue block lives in a static __device__ array of
+ * MALBEC_NOALLOC_SCRATCH_BYTES bytes inside libmalbec.so, held by every GPU
+ * that loads the library until the process exits.  No cudaMalloc, cudaFree,
+ * stream-ordered or library allocation is made: the call enqueues a memset of
+ * the block (it keeps the previous call's contents) and the kernel.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array: calls whose work overlaps
+ *    on the GPU (different streams, or graphs replayed concurrently) race on
+ *    the work queue and give wrong results.  Serialise them.
+ *  - A call whose scratch would exceed MALBEC_NOALLOC_SCRATCH_BYTES returns
+ *    MALBEC_ESCRATCH; a trace needs one 256-byte block whatever n is. */
+#define MALBEC_NOALLOC_SCRATCH_BYTES 256
+int malbec_trace_noalloc(malbec_metric m, const double* ics, uint64_t n, malbec_term t,
+                         malbec_out_mode mode, uint32_t stride, malbec_precision prec, void* out,
+                         malbec_stream stream);
 
 /* ---------------------------------------------------------------- camera */
 /* Backward null-ray camera (not in the paper; Bardeen 1973 impact

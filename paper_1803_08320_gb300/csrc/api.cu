@@ -22,6 +22,8 @@ bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
 
 double host_r_plus(double M, double a) { return M + sqrt(M * M - a * a); }
 
+}  // namespace
+
 int check_metric(const malbec_metric& m) {
   if (!finite_pos(m.M) || !isfinite(m.a) || m.a < 0.0 || !(m.a < m.M)) return MALBEC_EINVAL;
   return MALBEC_OK;
@@ -38,6 +40,8 @@ int check_term(const malbec_term& t, const malbec_metric& m) {
   if (!isfinite(t.r_esc) || !(t.r_esc > (1.0 + t.eps_hor) * rp)) return MALBEC_EINVAL;
   return MALBEC_OK;
 }
+
+namespace {
 
 struct DeviceInfo {
   int sm_count = 0;
@@ -59,6 +63,8 @@ int device_sms(int* sms) {
   return MALBEC_OK;
 }
 
+}  // namespace
+
 // Launch shape: persistent warps, as many as fit (occupancy) but no more than
 // the rays need; small batches spread one warp per block across the SMs.
 int choose_shape(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, LaunchShape* shape, int* refill_min) {
@@ -77,6 +83,8 @@ int choose_shape(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, Launc
   *refill_min = 1;
   return MALBEC_OK;
 }
+
+namespace {
 
 // Enqueue scratch allocation + zeroing, the trace kernel and the scratch free.
 int run_trace(TraceParams& p, bool kerr, bool mixed, Source src, Sink sink, cudaStream_t stream) {
@@ -157,6 +165,7 @@ const char* malbec_strerror(int code) {
     case MALBEC_ETIMEDOUT: return "bounded device wait timed out";
     case MALBEC_ECUDA: return "CUDA runtime error";
     case MALBEC_ENOTFOUND: return "unknown job";
+    case MALBEC_ESCRATCH: return "needs more scratch than the static no-allocation block holds";
     default: return "unknown error code";
   }
 }

@@ -76,6 +76,9 @@ cudaError_t launch_invariants(double M, double a, const double* a_per_ray, const
 // api.cu
 int set_cuda_error(cudaError_t e);
 void fill_zone(TraceParams& p);
+int check_metric(const malbec_metric& m);
+int check_term(const malbec_term& t, const malbec_metric& m);
+int choose_shape(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, LaunchShape* shape, int* refill_min);
 CameraConst make_camera_const(double M, double a, const malbec_camera& cam);
 
 }  // namespace malbec

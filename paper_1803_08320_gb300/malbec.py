@@ -91,6 +91,7 @@ def _declare(L):
     sig("malbec_out_layout", ctypes.c_int, ctypes.c_int, ctypes.c_int, _U64, _U32, _U32, ctypes.POINTER(Layout))
     sig("malbec_out_bytes", _SZ, ctypes.c_int, ctypes.c_int, _U64, _U32, _U32)
     sig("malbec_trace", ctypes.c_int, Metric, _VP, _U64, Term, ctypes.c_int, _U32, ctypes.c_int, _VP, _VP)
+    sig("malbec_trace_noalloc", ctypes.c_int, Metric, _VP, _U64, Term, ctypes.c_int, _U32, ctypes.c_int, _VP, _VP)
     sig("malbec_camera_out_layout", ctypes.c_int, ctypes.POINTER(Camera), ctypes.POINTER(CameraLayout))
     sig("malbec_trace_camera", ctypes.c_int, Metric, ctypes.POINTER(Camera), Term, ctypes.c_int, _VP, _VP)
     sig("malbec_ic_camera", ctypes.c_int, Metric, ctypes.POINTER(Camera), _VP, _U64, _VP, _VP)
@@ -219,6 +220,22 @@ def trace(M: float, a: float, ics, term, mode: int = OUT_FINAL, stride: int = 0,
     res = _views_final(out, L, n, mode, precision)
     res["_keep"] = (ics, apr)
     return res
+
+
+def trace_noalloc(M: float, a: float, ics, term, out, mode: int = OUT_FINAL, stride: int = 0,
+                  precision="fp64", a_per_ray=None, stream=None):
+    """`trace` through malbec_trace_noalloc, for callers that cannot allocate
+    device memory: `out` (a uint8 CUDA tensor of out_layout(...).total bytes)
+    and `ics` must already be on the device; the library uses its static
+    work-queue block and allocates nothing.  Calls that overlap on the GPU
+    share that block and race: serialise them."""
+    t = term_from(term)
+    n = ics.shape[1]
+    L = out_layout(mode, precision, n, t.n_steps_cap, stride if mode == OUT_STRIDED else 0)
+    m = Metric(float(M), float(a), _ptr(a_per_ray))
+    _check(lib().malbec_trace_noalloc(m, _ptr(ics), n, t.c(), mode, stride if mode == OUT_STRIDED else 0,
+                                      _prec(precision), _ptr(out), _stream(stream)), "malbec_trace_noalloc")
+    return _views_final(out, L, n, mode, precision)
 
 
 def camera_layout(cam: Camera) -> CameraLayout:
