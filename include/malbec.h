@@ -107,8 +107,12 @@ typedef enum {
 /* FP32_MIXED FP64 zone: a step runs in FP64 when, at its start,
  *   r < MALBEC_ZONE_HORIZON_FACTOR * r_+                      (every ray), or
  *   r < r_ph,retro(a) + MALBEC_ZONE_PHOTON_MARGIN * M        (null rays), or
- *   |sin theta| < MALBEC_ZONE_POLE_SIN   (near the polar axis, where the BL
- *                                         Christoffel symbols diverge),
+ *   |sin theta| < MALBEC_ZONE_POLE_SIN   (timelike rays near the polar axis,
+ *                                         where the BL Christoffel symbols
+ *                                         diverge: keeps E, L_z, Q drift
+ *                                         below 1e-6; null rays that come
+ *                                         this close are ill-conditioned in
+ *                                         any precision),
  * r_ph,retro = 2M (1 + cos(2/3 arccos(a/M))) the retrograde circular photon
  * orbit, the outer edge of the spherical photon orbits.  A ray is null when
  * |g(u,u)| <= 1e-6 (u^t)^2 |g_tt| at its start. */
@@ -129,6 +133,33 @@ typedef struct {
 
 int malbec_set_mixed_zone(const malbec_mixed_zone* zone);
 int malbec_get_mixed_zone(malbec_mixed_zone* zone);
+
+/* Launch configuration of the persistent trace kernels (process-wide, for
+ * subsequent calls; a 0 field keeps the automatic choice):
+ *   threads_per_block  32..256, a multiple of 32 (automatic: 128, or 32 for
+ *                      batches smaller than 4 warps per SM);
+ *   blocks_per_sm      resident blocks per SM, capped by occupancy
+ *                      (automatic: 4 warps per SM for FP64 -- one per SM
+ *                      sub-partition saturates the FP64 unit --, 8 for
+ *                      FP32_MIXED);
+ *   refill_min         a warp takes new rays once this many lanes are idle
+ *                      (automatic: 1);
+ *   zone_batch         FP32_MIXED: an FP64-zone warp step waits for this many
+ *                      lanes (automatic: 8) ...
+ *   zone_wait          ... or until a waiting lane sat out this many warp
+ *                      steps (automatic: 64).
+ * The choice changes speed only: every ray's arithmetic is the same.
+ * NULL restores all-automatic.  Thread-safe. */
+typedef struct {
+  uint32_t threads_per_block;
+  uint32_t blocks_per_sm;
+  uint32_t refill_min;
+  uint32_t zone_batch;
+  uint32_t zone_wait;
+} malbec_launch_config;
+
+int malbec_set_launch_config(const malbec_launch_config* cfg);
+int malbec_get_launch_config(malbec_launch_config* cfg);
 
 /* ---------------------------------------------------------------- output layout */
 /* Offsets (bytes from the start of `out`) of the output fields of

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmalbec.so")
 SOURCES = ["api.cu", "trace.cu", "ic.cu", "peaks.cu", "noalloc.cu"]
-HEADERS = ["geodesic.cuh", "camera.cuh", "internal.h"]
+HEADERS = ["geodesic.cuh", "camera.cuh", "bound.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

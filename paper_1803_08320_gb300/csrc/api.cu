@@ -65,22 +65,43 @@ int device_sms(int* sms) {
 
 }  // namespace
 
+namespace {
+std::mutex g_launch_mu;
+malbec_launch_config g_launch = {0, 0, 0, 0, 0};
+
+malbec_launch_config launch_config() {
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  return g_launch;
+}
+}  // namespace
+
 // Launch shape: persistent warps, as many as fit (occupancy) but no more than
 // the rays need; small batches spread one warp per block across the SMs.
 int choose_shape(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, LaunchShape* shape, int* refill_min) {
   int sms = 0;
   int rc = device_sms(&sms);
   if (rc) return rc;
+  const malbec_launch_config cfg = launch_config();
   const uint64_t warps_needed = (n + 31) / 32;
   int tpb = 128;
   if (warps_needed < (uint64_t)sms * 4) tpb = 32;
+  if (cfg.threads_per_block) tpb = (int)cfg.threads_per_block;
   int per_sm = trace_max_blocks_per_sm(kerr, mixed, src, sink, tpb);
   if (per_sm <= 0) per_sm = 1;
+  // Resident warps per SM.  FP64: one warp per SM sub-partition already
+  // saturates the FP64 unit (it costs the same per warp instruction whatever
+  // the number of active lanes), and more warps only slow the longest rays,
+  // which set the end of the launch.  FP32_MIXED: two per sub-partition.
+  const int target_warps = mixed ? 8 : 4;
+  int want = target_warps / (tpb / 32);
+  if (want < 1) want = 1;
+  if (cfg.blocks_per_sm) want = (int)cfg.blocks_per_sm;
+  if (want < per_sm) per_sm = want;
   const uint64_t max_blocks = (uint64_t)sms * per_sm;
   const uint64_t blocks_needed = (warps_needed + (tpb / 32) - 1) / (tpb / 32);
   shape->threads_per_block = tpb;
   shape->blocks = (int)(blocks_needed < max_blocks ? blocks_needed : max_blocks);
-  *refill_min = 1;
+  *refill_min = cfg.refill_min ? (int)cfg.refill_min : 1;
   return MALBEC_OK;
 }
 
@@ -114,10 +135,15 @@ malbec_mixed_zone g_zone = {MALBEC_ZONE_HORIZON_FACTOR, MALBEC_ZONE_PHOTON_MARGI
 }  // namespace
 
 void fill_zone(TraceParams& p) {
-  std::lock_guard<std::mutex> lk(g_zone_mu);
-  p.zone_horizon = g_zone.horizon_factor;
-  p.zone_photon = g_zone.photon_margin;
-  p.zone_pole = g_zone.pole_sin;
+  {
+    std::lock_guard<std::mutex> lk(g_zone_mu);
+    p.zone_horizon = g_zone.horizon_factor;
+    p.zone_photon = g_zone.photon_margin;
+    p.zone_pole = g_zone.pole_sin;
+  }
+  const malbec_launch_config cfg = launch_config();
+  p.zone_batch = cfg.zone_batch ? (int)cfg.zone_batch : 8;
+  p.zone_wait = cfg.zone_wait ? (int)cfg.zone_wait : 64;
 }
 
 int set_cuda_error(cudaError_t e) {
@@ -182,6 +208,26 @@ int malbec_set_mixed_zone(const malbec_mixed_zone* z) {
   }
   std::lock_guard<std::mutex> lk(g_zone_mu);
   g_zone = v;
+  return MALBEC_OK;
+}
+
+int malbec_set_launch_config(const malbec_launch_config* cfg) {
+  malbec_launch_config v = {0, 0, 0, 0, 0};
+  if (cfg) {
+    if (cfg->threads_per_block && (cfg->threads_per_block % 32 != 0 || cfg->threads_per_block > 256))
+      return MALBEC_EINVAL;
+    if (cfg->blocks_per_sm > 64 || cfg->refill_min > 32 || cfg->zone_batch > 32 || cfg->zone_wait > 1000000)
+      return MALBEC_EINVAL;
+    v = *cfg;
+  }
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  g_launch = v;
+  return MALBEC_OK;
+}
+
+int malbec_get_launch_config(malbec_launch_config* cfg) {
+  if (!cfg) return MALBEC_EINVAL;
+  *cfg = launch_config();
   return MALBEC_OK;
 }
 

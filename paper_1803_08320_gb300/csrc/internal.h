@@ -44,8 +44,9 @@ struct TraceParams {
   // outputs (kSinkCamera)
   double* theta_out;
   double* phi_out;
-  // FP32_MIXED FP64 zone (malbec_mixed_zone)
+  // FP32_MIXED FP64 zone (malbec_mixed_zone) and the batching of zone steps
   double zone_horizon, zone_photon, zone_pole;
+  int zone_batch, zone_wait;
   // work queue (scratch, zeroed before launch)
   unsigned long long* head;
   // launch shape

@@ -166,7 +166,10 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
   uint32_t nst = 0;
   uint64_t id = 0;
   double a = p.a, r_cap = 0.0;
-  float r_cap_f = 0.f, r_zone_f = 0.f;
+  float r_cap_f = 0.f, r_zone_f = 0.f, pole_lane = -1.f;
+  BH<double> bh64 = make_bh<double>(M, p.a);
+  BH<float> bh32 = make_bh<float>(M, p.a);
+  int zone_waited = 0;
   bool active = false, drained = false;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -195,10 +198,13 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
         } else {
           camera_state(p.cam, a, id, y);
         }
+        bh64 = make_bh<double>(M, a);
+        if (kMixed) bh32 = make_bh<float>(M, a);
         const double rp = dev_r_plus(M, a);
         r_cap = (1.0 + p.eps_hor) * rp;
         lam = 0.0;
         nst = 0;
+        zone_waited = 0;
         if (kMixed || kSink != kSinkCamera) {
           double inv[4];
           invariants64(M, a, y, inv);
@@ -214,6 +220,7 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
             if (is_null) rz = fmax(rz, dev_r_photon_retro(M, a) + p.zone_photon * M);
             r_zone_f = (float)rz;
             r_cap_f = (float)r_cap;
+            pole_lane = is_null ? -1.f : pole_f;
             split_pair(y, hi, lo);
           }
         }
@@ -222,7 +229,24 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
       continue;
     }
     if (act == 0) break;  // queue drained and no lane busy
+    // FP32_MIXED: one warp step is either an FP64-zone step (for every lane
+    // that wants one) or an FP32 step (for the others), never both.  FP64
+    // steps are deferred until zone_batch lanes want one, no lane wants an
+    // FP32 step, or a waiting lane has sat out zone_wait warp steps.  Only the
+    // timing of a ray's steps changes, never their arithmetic.
+    bool in_zone = false, take = true;
+    if (kMixed) {
+      in_zone = active && nst < p.cap && (hi[1] < r_zone_f || fabsf(__sinf(hi[2])) < pole_lane);
+      const bool want32 = active && nst < p.cap && !in_zone;
+      const unsigned m64 = __ballot_sync(kFull, in_zone);
+      const unsigned m32 = __ballot_sync(kFull, want32);
+      const unsigned urgent = __ballot_sync(kFull, in_zone && zone_waited >= p.zone_wait);
+      const bool do64 = m32 == 0 || urgent != 0 || __popc(m64) >= p.zone_batch;
+      take = do64 ? in_zone : want32;
+      if (in_zone) zone_waited = do64 ? 0 : zone_waited + 1;
+    }
     if (!active) continue;
+    if (kMixed && nst < p.cap && !take) continue;
 
     int fate = 0;
     if (nst < p.cap) {
@@ -230,17 +254,17 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
       bool captured, escaped, finite;
       if (!kMixed) {
         const double h = p.dl_r_scale > 0.0 ? p.dl_r_scale * y[1] : p.dl;
-        const double rmin = rk4_step<kKerr, double>(make_bh<double>(M, a), h, y);
+        const double rmin = rk4_step<kKerr, double>(bh64, h, y);
         lam += h;
         captured = (y[1] <= r_cap) | (rmin <= r_cap);
         escaped = y[1] >= p.r_esc;
         finite = finite8(y);
-      } else if (hi[1] < r_zone_f || fabsf(__sinf(hi[2])) < pole_f) {
+      } else if (in_zone) {
         // FP64 zone (horizon, photon orbits, polar axis)
 #pragma unroll
         for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
         const double h = p.dl_r_scale > 0.0 ? p.dl_r_scale * y[1] : p.dl;
-        const double rmin = rk4_step<kKerr, double>(make_bh<double>(M, a), h, y);
+        const double rmin = rk4_step<kKerr, double>(bh64, h, y);
         lam += h;
         split_pair(y, hi, lo);
         captured = (y[1] <= r_cap) | (rmin <= r_cap);
@@ -259,7 +283,7 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
           h6l = h6_fix_l;
           lam += p.dl;
         }
-        const float rmin = rk4_step_mixed<kKerr>(make_bh<float>(M, a), hf, h6h, h6l, hi, lo);
+        const float rmin = rk4_step_mixed<kKerr>(bh32, hf, h6h, h6l, hi, lo);
         captured = (hi[1] <= r_cap_f) | (rmin <= r_cap_f);
         escaped = hi[1] >= r_esc_f;
         finite = finite8f(hi) & finite8f(lo);

@@ -54,6 +54,14 @@ class MixedZone(ctypes.Structure):
     _fields_ = [("horizon_factor", _D), ("photon_margin", _D), ("pole_sin", _D)]
 
 
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("threads_per_block", _U32), ("blocks_per_sm", _U32), ("refill_min", _U32),
+                ("zone_batch", _U32), ("zone_wait", _U32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class MalbecError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -99,6 +107,8 @@ def _declare(L):
     sig("malbec_ic_bound", ctypes.c_int, _D, _D, ctypes.c_int, _U64, _U64, _U64, _VP, _VP, _VP, _VP)
     sig("malbec_invariants", ctypes.c_int, Metric, _VP, _U64, _VP, _VP)
     sig("malbec_measure_fma_peak", ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D))
+    sig("malbec_set_launch_config", ctypes.c_int, ctypes.POINTER(LaunchConfig))
+    sig("malbec_get_launch_config", ctypes.c_int, ctypes.POINTER(LaunchConfig))
     sig("malbec_set_mixed_zone", ctypes.c_int, ctypes.POINTER(MixedZone))
     sig("malbec_get_mixed_zone", ctypes.c_int, ctypes.POINTER(MixedZone))
 
@@ -323,6 +333,24 @@ def set_mixed_zone(horizon_factor=None, photon_margin=None, pole_sin=None, reset
         z.pole_sin = float(pole_sin)
     _check(lib().malbec_set_mixed_zone(ctypes.byref(z)), "malbec_set_mixed_zone")
     return z
+
+
+def set_launch_config(threads_per_block=0, blocks_per_sm=0, refill_min=0, zone_batch=0, zone_wait=0,
+                      reset=False) -> LaunchConfig:
+    """Process-wide launch configuration of the trace kernels (0 = automatic)."""
+    if reset:
+        _check(lib().malbec_set_launch_config(None), "malbec_set_launch_config")
+    else:
+        c = LaunchConfig(int(threads_per_block), int(blocks_per_sm), int(refill_min), int(zone_batch),
+                         int(zone_wait))
+        _check(lib().malbec_set_launch_config(ctypes.byref(c)), "malbec_set_launch_config")
+    return get_launch_config()
+
+
+def get_launch_config() -> LaunchConfig:
+    c = LaunchConfig()
+    _check(lib().malbec_get_launch_config(ctypes.byref(c)), "malbec_get_launch_config")
+    return c
 
 
 def get_mixed_zone() -> MixedZone:
