@@ -270,6 +270,110 @@ int malbec_trace_camera(malbec_metric m, const malbec_camera* cam, malbec_term t
 int malbec_ic_camera(malbec_metric m, const malbec_camera* cam, const uint64_t* pixels,
                      uint64_t n, double* ics, malbec_stream stream);
 
+/* ---------------------------------------------------------------- uneven bundles */
+/* Many independent bundles of rays, each with its own black hole, kind, step
+ * rule, step cap and output buffer, traced by ONE persistent work-queue
+ * launch (not in the paper, whose runs trace one set of initial conditions
+ * at a time).  Warps take rays bundle by bundle, the costliest bundles first
+ * (estimated cost n * cap for orbits, n * min(cap, 300) for camera rays), so
+ * bundles whose rays end after very different step counts keep every lane
+ * busy. */
+#define MALBEC_BUNDLE_STATES 0 /* rays from `ics` (device double[8][n]) */
+#define MALBEC_BUNDLE_CAMERA 1 /* backward camera pixels 0..n-1 (n <= nx * ny) */
+#define MALBEC_BUNDLE_BOUND 2  /* generic bound orbits of malbec_ic_bound with
+                                  the spin fixed at `a`, particles 0..n-1 of `seed` */
+typedef struct {
+  int32_t kind;
+  uint32_t n;          /* rays, >= 1 */
+  double M, a;         /* M > 0, 0 <= a < M */
+  malbec_term term;
+  malbec_camera camera; /* CAMERA only */
+  const double* ics;    /* STATES only */
+  uint64_t seed;        /* BOUND only */
+  void* out;            /* device, 256-byte aligned, malbec_bundle_out_bytes() bytes */
+} malbec_bundle;
+
+/* Output of one bundle: STATES and BOUND use the FINAL layout of
+ * malbec_out_layout(MALBEC_OUT_FINAL, prec, n, cap, 0); CAMERA the camera
+ * layout of an n x 1 camera (fate, steps, theta, phi of n pixels). */
+size_t malbec_bundle_out_bytes(const malbec_bundle* b, malbec_precision prec);
+
+/* Trace `count` bundles (host array) in one launch on `stream`.  Every
+ * bundle is validated as malbec_trace / malbec_trace_camera would
+ * (MALBEC_EINVAL before anything is enqueued).  Scratch (job table, counters)
+ * comes from the stream-ordered allocator. */
+int malbec_trace_bundles(const malbec_bundle* bundles, uint32_t count, malbec_precision prec,
+                         malbec_stream stream);
+
+/* A plan: the bundles uploaded once and their launch recorded as a CUDA
+ * graph (reset of the work-queue counters + the persistent kernel), replayed
+ * by malbec_plan_launch with a single cudaGraphLaunch.  The plan owns its
+ * device table (cudaMalloc at creation); the bundles' `ics` and `out`
+ * buffers must stay valid while it is used.  Plans take the launch
+ * configuration in force at creation, or the one malbec_plan_autotune picks:
+ * it replays the plan under candidate configurations (block size, blocks per
+ * SM, refill granularity, FP64-zone batching) on `stream`, blocking the
+ * caller, and keeps the fastest (written to `best` if non-NULL). */
+typedef struct malbec_plan malbec_plan;
+int malbec_plan_create(const malbec_bundle* bundles, uint32_t count, malbec_precision prec,
+                       malbec_plan** plan);
+int malbec_plan_launch(malbec_plan* plan, malbec_stream stream);
+int malbec_plan_autotune(malbec_plan* plan, malbec_stream stream, malbec_launch_config* best);
+int malbec_plan_destroy(malbec_plan* plan);
+
+/* ---------------------------------------------------------------- serving */
+/* A request loop with continuous batching (not in the paper).  Jobs are
+ * bundles (malbec_bundle without `out`: the server allocates each job's
+ * output from its HBM budget).  One resident trace kernel serves every
+ * admitted job at once: idle lanes take rays from the active jobs,
+ * smallest estimated job first, so a request that arrives while others run
+ * starts as soon as lanes free up and its rays overlap with theirs on the
+ * device.  A ray's result does not depend on which other jobs ran with it.
+ *  - Admission: a job is admitted when the active set has a free place
+ *    (max_active) and its output fits in hbm_budget minus the bytes held by
+ *    admitted, not yet released jobs; otherwise it waits in a FIFO of at most
+ *    max_pending jobs (malbec_submit returns MALBEC_EBUSY when that is full).
+ *  - The kernel leaves by itself after idle_timeout_s without work (a bounded
+ *    wait on the device clock), and is relaunched by the next submit or poll
+ *    that finds work.  Job slots form a ring of 65536 descriptors.
+ *  - Completion is signalled by the device in mapped host memory; polling
+ *    never synchronises the device.
+ * All calls are thread-safe.  malbec_server_destroy waits for running rays
+ * to finish (new rays are no longer started) and frees everything. */
+typedef struct malbec_server malbec_server;
+typedef struct {
+  size_t hbm_budget;      /* bytes for job outputs (e.g. 150e9) */
+  uint32_t max_active;    /* jobs served at once, 1..4096 */
+  uint32_t max_pending;   /* queued jobs beyond that, >= 1 */
+  malbec_precision precision;
+  double idle_timeout_s;  /* kernel exit after this long without work, > 0 */
+} malbec_server_config;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, released;
+  uint64_t pending, active;
+  uint64_t bytes_in_use;
+  uint64_t kernel_launches;
+} malbec_server_stats;
+
+int malbec_server_create(const malbec_server_config* cfg, malbec_server** server);
+int malbec_server_destroy(malbec_server* server);
+/* Non-blocking.  `job->out` is ignored.  STATES jobs read `ics` while they
+ * run: keep it valid until the job is done. */
+int malbec_submit(malbec_server* server, const malbec_bundle* job, uint64_t* job_id);
+/* Non-blocking: *done = 1 once every ray of the job has finished. */
+int malbec_poll(malbec_server* server, uint64_t job_id, int* done);
+/* Device pointer and size of a finished job's output (bundle layout); valid
+ * until malbec_job_release.  MALBEC_EBUSY while the job runs. */
+int malbec_job_output(malbec_server* server, uint64_t job_id, void** out, size_t* bytes);
+/* Copy a finished job's output (all `bytes` of it) to `dst` (device or
+ * pinned host memory) on `stream`.  MALBEC_EBUSY while the job runs. */
+int malbec_job_copy_output(malbec_server* server, uint64_t job_id, void* dst, size_t bytes,
+                           malbec_stream stream);
+/* Give the job's memory back to the budget (after its output was read). */
+int malbec_job_release(malbec_server* server, uint64_t job_id);
+int malbec_server_stats_get(malbec_server* server, malbec_server_stats* stats);
+
 /* ---------------------------------------------------------------- initial data */
 /* Circular equatorial timelike orbits at the radii `radii` (device double[n]):
  * Schwarzschild E, L from Sec. 4 eqs. COrbit/COrbit2 when a = 0, Bardeen's

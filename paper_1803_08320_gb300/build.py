@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmalbec.so")
-SOURCES = ["api.cu", "trace.cu", "ic.cu", "peaks.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "trace.cu", "ic.cu", "peaks.cu", "noalloc.cu", "bundles.cu", "server.cu"]
 HEADERS = ["geodesic.cuh", "camera.cuh", "bound.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -78,10 +78,14 @@ malbec_launch_config launch_config() {
 // Launch shape: persistent warps, as many as fit (occupancy) but no more than
 // the rays need; small batches spread one warp per block across the SMs.
 int choose_shape(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, LaunchShape* shape, int* refill_min) {
+  return choose_shape_cfg(kerr, mixed, src, sink, n, launch_config(), shape, refill_min);
+}
+
+int choose_shape_cfg(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, const malbec_launch_config& cfg,
+                     LaunchShape* shape, int* refill_min) {
   int sms = 0;
   int rc = device_sms(&sms);
   if (rc) return rc;
-  const malbec_launch_config cfg = launch_config();
   const uint64_t warps_needed = (n + 31) / 32;
   int tpb = 128;
   if (warps_needed < (uint64_t)sms * 4) tpb = 32;
@@ -345,6 +349,14 @@ static int check_camera(const malbec_metric& m, const malbec_camera* cam, const 
   if (t && !(cam->r_obs < t->r_esc)) return MALBEC_EINVAL;
   return MALBEC_OK;
 }
+
+}  // extern "C"
+
+int malbec::check_camera_desc(const malbec_metric& m, const malbec_camera* cam, const malbec_term* t) {
+  return check_camera(m, cam, t);
+}
+
+extern "C" {
 
 int malbec_trace_camera(malbec_metric m, const malbec_camera* cam, malbec_term t, malbec_precision prec, void* out,
                         malbec_stream stream) {

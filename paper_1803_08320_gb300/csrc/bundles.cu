@@ -1,0 +1,397 @@
+// bundles.cu -- uneven bundles of rays in one persistent launch (host side):
+// validation, the device job table, the costliest-first job order, the
+// one-shot entry point, and plans (table uploaded once, launch recorded as a
+// CUDA graph, launch configuration autotuned by replay).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+namespace malbec {
+namespace {
+
+size_t align256(size_t x) { return (x + 255u) & ~(size_t)255u; }
+
+struct CameraFields {
+  size_t fate, steps, theta, phi, total;
+};
+
+CameraFields camera_fields(uint64_t n) {
+  CameraFields f;
+  size_t off = 0;
+  f.fate = off;
+  off = align256(off + n);
+  f.steps = off;
+  off = align256(off + n * sizeof(uint32_t));
+  f.theta = off;
+  off = align256(off + n * sizeof(double));
+  f.phi = off;
+  off = align256(off + n * sizeof(double));
+  f.total = off;
+  return f;
+}
+
+int validate(const malbec_bundle& b, malbec_precision prec) {
+  if (b.n == 0 || !b.out || ((uintptr_t)b.out & 255u) != 0) return MALBEC_EINVAL;
+  const malbec_metric m = {b.M, b.a, nullptr};
+  int rc = check_metric(m);
+  if (rc) return rc;
+  rc = check_term(b.term, m);
+  if (rc) return rc;
+  if (b.kind == MALBEC_BUNDLE_CAMERA) {
+    rc = check_camera_desc(m, &b.camera, &b.term);
+    if (rc) return rc;
+    if ((uint64_t)b.n > (uint64_t)b.camera.nx * b.camera.ny) return MALBEC_EINVAL;
+  } else if (b.kind == MALBEC_BUNDLE_STATES) {
+    if (!b.ics) return MALBEC_EINVAL;
+  } else if (b.kind != MALBEC_BUNDLE_BOUND) {
+    return MALBEC_EINVAL;
+  }
+  if (prec != MALBEC_FP64 && prec != MALBEC_FP32_MIXED) return MALBEC_EINVAL;
+  return MALBEC_OK;
+}
+
+}  // namespace
+
+int validate_job(const malbec_bundle& b, malbec_precision prec) {
+  malbec_bundle c = b;
+  c.out = reinterpret_cast<void*>(256);  // the server allocates the output
+  return validate(c, prec);
+}
+
+void fill_job_desc(const malbec_bundle& b, malbec_precision prec, void* out, uint64_t job_id, JobDesc* J,
+                   double* cost) {
+  memset(J, 0, sizeof(*J));
+  J->kind = b.kind;
+  J->cap = b.term.n_steps_cap;
+  J->n = b.n;
+  J->job_id = job_id;
+  J->M = b.M;
+  J->a = b.a;
+  J->eps_hor = b.term.eps_hor;
+  J->r_esc = b.term.r_esc;
+  J->dl = b.term.dl;
+  J->dl_r_scale = b.term.dl_r_scale;
+  J->seed = b.seed;
+  J->ics = b.ics;
+  char* o = static_cast<char*>(out);
+  if (b.kind == MALBEC_BUNDLE_CAMERA) {
+    J->cam = make_camera_const(b.M, b.a, b.camera);
+    const CameraFields f = camera_fields(b.n);
+    J->fate_out = reinterpret_cast<uint8_t*>(o + f.fate);
+    J->steps_out = reinterpret_cast<uint32_t*>(o + f.steps);
+    J->theta_out = reinterpret_cast<double*>(o + f.theta);
+    J->phi_out = reinterpret_cast<double*>(o + f.phi);
+    *cost = (double)b.n * std::min<double>(b.term.n_steps_cap, 300.0);
+  } else {
+    malbec_layout L;
+    malbec_out_layout(MALBEC_OUT_FINAL, prec, b.n, b.term.n_steps_cap, 0, &L);
+    J->y_out = reinterpret_cast<double*>(o + L.y);
+    J->lambda_out = reinterpret_cast<double*>(o + L.lambda);
+    J->inv0_out = reinterpret_cast<double*>(o + L.inv0);
+    J->inv1_out = reinterpret_cast<double*>(o + L.inv1);
+    J->steps_out = reinterpret_cast<uint32_t*>(o + L.steps);
+    J->fate_out = reinterpret_cast<uint8_t*>(o + L.fate);
+    *cost = (double)b.n * (double)b.term.n_steps_cap;
+  }
+}
+
+namespace {
+
+int build_jobs(const malbec_bundle* bundles, uint32_t count, malbec_precision prec, std::vector<JobDesc>& jobs,
+               std::vector<uint32_t>& order, uint64_t* total_rays) {
+  if (!bundles || count == 0) return MALBEC_EINVAL;
+  jobs.assign(count, JobDesc());
+  uint64_t total = 0;
+  std::vector<double> cost(count);
+  for (uint32_t i = 0; i < count; ++i) {
+    const malbec_bundle& b = bundles[i];
+    int rc = validate(b, prec);
+    if (rc) return rc;
+    JobDesc& J = jobs[i];
+    memset(&J, 0, sizeof(J));
+    J.kind = b.kind;
+    J.cap = b.term.n_steps_cap;
+    J.n = b.n;
+    J.M = b.M;
+    J.a = b.a;
+    J.eps_hor = b.term.eps_hor;
+    J.r_esc = b.term.r_esc;
+    J.dl = b.term.dl;
+    J.dl_r_scale = b.term.dl_r_scale;
+    J.seed = b.seed;
+    J.ics = b.ics;
+    char* o = static_cast<char*>(b.out);
+    if (b.kind == MALBEC_BUNDLE_CAMERA) {
+      J.cam = make_camera_const(b.M, b.a, b.camera);
+      const CameraFields f = camera_fields(b.n);
+      J.fate_out = reinterpret_cast<uint8_t*>(o + f.fate);
+      J.steps_out = reinterpret_cast<uint32_t*>(o + f.steps);
+      J.theta_out = reinterpret_cast<double*>(o + f.theta);
+      J.phi_out = reinterpret_cast<double*>(o + f.phi);
+      cost[i] = (double)b.n * std::min<double>(b.term.n_steps_cap, 300.0);
+    } else {
+      malbec_layout L;
+      rc = malbec_out_layout(MALBEC_OUT_FINAL, prec, b.n, b.term.n_steps_cap, 0, &L);
+      if (rc) return rc;
+      J.y_out = reinterpret_cast<double*>(o + L.y);
+      J.lambda_out = reinterpret_cast<double*>(o + L.lambda);
+      J.inv0_out = reinterpret_cast<double*>(o + L.inv0);
+      J.inv1_out = reinterpret_cast<double*>(o + L.inv1);
+      J.steps_out = reinterpret_cast<uint32_t*>(o + L.steps);
+      J.fate_out = reinterpret_cast<uint8_t*>(o + L.fate);
+      cost[i] = (double)b.n * (double)b.term.n_steps_cap;
+    }
+    total += b.n;
+  }
+  order.resize(count);
+  std::iota(order.begin(), order.end(), 0u);
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return cost[x] > cost[y]; });
+  *total_rays = total;
+  return MALBEC_OK;
+}
+
+// Scratch block: [jobs][order][counters][cursor], each 256-aligned; the
+// counters and the cursor (the tail from `ctr` on) are zeroed before a launch.
+struct BlockLayout {
+  size_t jobs, ctr, order, cursor, total;
+};
+BlockLayout block_layout(uint32_t count) {
+  BlockLayout b;
+  size_t off = 0;
+  b.jobs = off;
+  off = align256(off + count * sizeof(JobDesc));
+  b.order = off;
+  off = align256(off + count * sizeof(uint32_t));
+  b.ctr = off;
+  off = align256(off + count * sizeof(JobCounter));
+  b.cursor = off;
+  off = align256(off + sizeof(unsigned int));
+  b.total = off;
+  return b;
+}
+
+void fill_params(TraceParams& p, char* block, const BlockLayout& bl, uint32_t count, uint64_t total_rays) {
+  memset(&p, 0, sizeof(p));
+  p.M = 1.0;
+  p.n = total_rays;
+  p.stride = 1;
+  p.jobs = reinterpret_cast<const JobDesc*>(block + bl.jobs);
+  p.job_ctr = reinterpret_cast<JobCounter*>(block + bl.ctr);
+  p.job_order = reinterpret_cast<const uint32_t*>(block + bl.order);
+  p.n_jobs = count;
+  p.job_cursor = reinterpret_cast<unsigned int*>(block + bl.cursor);
+  fill_zone(p);
+}
+
+}  // namespace
+}  // namespace malbec
+
+using namespace malbec;
+
+struct malbec_plan {
+  int device = 0;
+  uint32_t count = 0;
+  uint64_t total_rays = 0;
+  bool mixed = false;
+  void* block = nullptr;
+  BlockLayout bl;
+  malbec_launch_config cfg = {0, 0, 0, 0, 0};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+// Record [zero the counters and the cursor] + [the persistent kernel] with
+// launch configuration `cfg` as the plan's graph.
+int record_plan(malbec_plan* P, const malbec_launch_config& cfg) {
+  TraceParams p;
+  fill_params(p, static_cast<char*>(P->block), P->bl, P->count, P->total_rays);
+  LaunchShape shape;
+  int refill_min = 1;
+  int rc = choose_shape_cfg(true, P->mixed, kSrcJobs, kSinkJobs, P->total_rays, cfg, &shape, &refill_min);
+  if (rc) return rc;
+  p.refill_min = refill_min;
+  if (cfg.zone_batch) p.zone_batch = (int)cfg.zone_batch;
+  if (cfg.zone_wait) p.zone_wait = (int)cfg.zone_wait;
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    char* blk = static_cast<char*>(P->block);
+    cudaError_t e1 = cudaMemsetAsync(blk + P->bl.ctr, 0, P->bl.total - P->bl.ctr, s);
+    cudaError_t e2 = e1 == cudaSuccess ? launch_trace(p, true, P->mixed, kSrcJobs, kSinkJobs, shape, s) : e1;
+    e = cudaStreamEndCapture(s, &g);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return set_cuda_error(e);
+  }
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return set_cuda_error(e);
+  }
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  P->graph = g;
+  P->exec = x;
+  P->cfg = cfg;
+  return MALBEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t malbec_bundle_out_bytes(const malbec_bundle* b, malbec_precision prec) {
+  if (!b || b->n == 0) return 0;
+  if (b->kind == MALBEC_BUNDLE_CAMERA) return camera_fields(b->n).total;
+  return malbec_out_bytes(MALBEC_OUT_FINAL, prec, b->n, b->term.n_steps_cap, 0);
+}
+
+int malbec_trace_bundles(const malbec_bundle* bundles, uint32_t count, malbec_precision prec, malbec_stream stream) {
+  std::vector<JobDesc> jobs;
+  std::vector<uint32_t> order;
+  uint64_t total = 0;
+  int rc = build_jobs(bundles, count, prec, jobs, order, &total);
+  if (rc) return rc;
+  const bool mixed = prec == MALBEC_FP32_MIXED;
+  const BlockLayout bl = block_layout(count);
+  cudaStream_t s = (cudaStream_t)stream;
+  void* block = nullptr;
+  cudaError_t e = cudaMallocAsync(&block, bl.total, s);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  char* blk = static_cast<char*>(block);
+  e = cudaMemcpyAsync(blk + bl.jobs, jobs.data(), count * sizeof(JobDesc), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(blk + bl.order, order.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(blk + bl.ctr, 0, bl.total - bl.ctr, s);
+  if (e == cudaSuccess) {
+    TraceParams p;
+    fill_params(p, blk, bl, count, total);
+    LaunchShape shape;
+    int refill_min = 1;
+    rc = choose_shape(true, mixed, kSrcJobs, kSinkJobs, total, &shape, &refill_min);
+    if (rc == MALBEC_OK) {
+      p.refill_min = refill_min;
+      e = launch_trace(p, true, mixed, kSrcJobs, kSinkJobs, shape, s);
+    }
+  }
+  cudaError_t e2 = cudaFreeAsync(block, s);
+  if (rc) return rc;
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (e2 != cudaSuccess) return set_cuda_error(e2);
+  return MALBEC_OK;
+}
+
+int malbec_plan_create(const malbec_bundle* bundles, uint32_t count, malbec_precision prec, malbec_plan** plan) {
+  if (!plan) return MALBEC_EINVAL;
+  *plan = nullptr;
+  std::vector<JobDesc> jobs;
+  std::vector<uint32_t> order;
+  uint64_t total = 0;
+  int rc = build_jobs(bundles, count, prec, jobs, order, &total);
+  if (rc) return rc;
+  malbec_plan* P = new malbec_plan();
+  cudaGetDevice(&P->device);
+  P->count = count;
+  P->total_rays = total;
+  P->mixed = prec == MALBEC_FP32_MIXED;
+  P->bl = block_layout(count);
+  cudaError_t e = cudaMalloc(&P->block, P->bl.total);
+  if (e != cudaSuccess) {
+    delete P;
+    return set_cuda_error(e);
+  }
+  char* blk = static_cast<char*>(P->block);
+  e = cudaMemcpy(blk + P->bl.jobs, jobs.data(), count * sizeof(JobDesc), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(blk + P->bl.order, order.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(P->block);
+    delete P;
+    return set_cuda_error(e);
+  }
+  malbec_launch_config cfg;
+  malbec_get_launch_config(&cfg);
+  rc = record_plan(P, cfg);
+  if (rc) {
+    malbec_plan_destroy(P);
+    return rc;
+  }
+  *plan = P;
+  return MALBEC_OK;
+}
+
+int malbec_plan_launch(malbec_plan* plan, malbec_stream stream) {
+  if (!plan || !plan->exec) return MALBEC_EINVAL;
+  cudaError_t e = cudaGraphLaunch(plan->exec, (cudaStream_t)stream);
+  return e == cudaSuccess ? MALBEC_OK : set_cuda_error(e);
+}
+
+int malbec_plan_autotune(malbec_plan* plan, malbec_stream stream, malbec_launch_config* best) {
+  if (!plan) return MALBEC_EINVAL;
+  std::vector<malbec_launch_config> cand;
+  if (!plan->mixed) {
+    for (uint32_t bps : {1u, 2u})
+      for (uint32_t rm : {1u, 4u}) cand.push_back({128u, bps, rm, 0u, 0u});
+    cand.push_back({64u, 2u, 1u, 0u, 0u});
+  } else {
+    for (uint32_t bps : {1u, 2u})
+      for (uint32_t zb : {8u, 16u})
+        for (uint32_t zw : {64u, 256u}) cand.push_back({128u, bps, 1u, zb, zw});
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  malbec_launch_config best_cfg = plan->cfg;
+  int rc = MALBEC_OK;
+  for (const malbec_launch_config& c : cand) {
+    rc = record_plan(plan, c);
+    if (rc) break;
+    cudaError_t e = cudaGraphLaunch(plan->exec, s);  // warm-up replay
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(plan->exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      rc = set_cuda_error(e);
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_cfg = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  rc = record_plan(plan, best_cfg);
+  if (rc == MALBEC_OK && best) *best = best_cfg;
+  return rc;
+}
+
+int malbec_plan_destroy(malbec_plan* plan) {
+  if (!plan) return MALBEC_EINVAL;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  if (plan->block) cudaFree(plan->block);
+  delete plan;
+  return MALBEC_OK;
+}
+
+}  // extern "C"

@@ -8,8 +8,8 @@
 
 namespace malbec {
 
-enum Source : int { kSrcStates = 0, kSrcCamera = 1 };
-enum Sink : int { kSinkFinal = 0, kSinkStrided = 1, kSinkCamera = 2 };
+enum Source : int { kSrcStates = 0, kSrcCamera = 1, kSrcJobs = 2, kSrcServe = 3 };
+enum Sink : int { kSinkFinal = 0, kSinkStrided = 1, kSinkCamera = 2, kSinkJobs = 3 };
 
 // Per-image constants of the backward camera (computed on the host in FP64).
 struct CameraConst {
@@ -18,6 +18,32 @@ struct CameraConst {
   double so, co;             // sin, cos of the inclination
   double Delta_o, r2a2_o;    // Delta(r_obs), r_obs^2 + a^2
   double gtt, gtp, gpp, grr, ghh;  // inverse metric at the observer
+};
+
+// One job (bundle) of the multi-job trace kernel, resident in device memory.
+struct JobDesc {
+  int32_t kind;  // MALBEC_BUNDLE_*
+  uint32_t cap;
+  uint64_t n;
+  uint64_t job_id;  // serving: the id whose slot this is (0 = empty)
+  double M, a, eps_hor, r_esc, dl, dl_r_scale;
+  uint64_t seed;
+  CameraConst cam;
+  const double* ics;
+  // outputs: FINAL layout (states, bound) or camera layout (camera)
+  double* y_out;
+  double* lambda_out;
+  double* inv0_out;
+  double* inv1_out;
+  uint32_t* steps_out;
+  uint8_t* fate_out;
+  double* theta_out;
+  double* phi_out;
+};
+
+struct JobCounter {
+  unsigned long long next;  // rays handed out
+  unsigned long long done;  // rays finished
 };
 
 struct TraceParams {
@@ -49,6 +75,22 @@ struct TraceParams {
   int zone_batch, zone_wait;
   // work queue (scratch, zeroed before launch)
   unsigned long long* head;
+  // multi-job source: job table, per-job counters (zeroed), longest-first
+  // job order and the cursor into it (zeroed)
+  const JobDesc* jobs;
+  JobCounter* job_ctr;
+  const uint32_t* job_order;
+  uint32_t n_jobs;
+  unsigned int* job_cursor;
+  // serving source: `jobs`/`job_ctr` form a ring of n_jobs slots (slot =
+  // job_id % n_jobs); the active list, the stop flag and the completion
+  // flags live in mapped host memory
+  const volatile uint64_t* active_ids;
+  const volatile uint32_t* active_count;
+  const volatile uint32_t* stop_flag;
+  volatile uint64_t* done_flags;
+  uint32_t max_active;
+  uint64_t idle_ns;
   // launch shape
   int refill_min;  // refill when at least this many lanes of a warp are idle
 };
@@ -80,6 +122,14 @@ void fill_zone(TraceParams& p);
 int check_metric(const malbec_metric& m);
 int check_term(const malbec_term& t, const malbec_metric& m);
 int choose_shape(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, LaunchShape* shape, int* refill_min);
+int choose_shape_cfg(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, const malbec_launch_config& cfg,
+                     LaunchShape* shape, int* refill_min);
+int check_camera_desc(const malbec_metric& m, const malbec_camera* cam, const malbec_term* t);
+
+// bundles.cu
+int validate_job(const malbec_bundle& b, malbec_precision prec);
+void fill_job_desc(const malbec_bundle& b, malbec_precision prec, void* out, uint64_t job_id, JobDesc* J,
+                   double* cost);
 CameraConst make_camera_const(double M, double a, const malbec_camera& cam);
 
 }  // namespace malbec

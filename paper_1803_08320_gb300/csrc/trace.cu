@@ -21,6 +21,7 @@
 // thresholds rounded to float.
 #include <math.h>
 
+#include "bound.cuh"
 #include "camera.cuh"
 #include "geodesic.cuh"
 #include "internal.h"
@@ -138,6 +139,33 @@ __device__ __forceinline__ float rk4_step_mixed(const BH<float>& bh, float hf, f
   return fminf(fminf(r2, r3), r4);
 }
 
+__device__ __forceinline__ void step_consts(double dl, double dl_scale, double r_esc, float& h_fix, float& h6h,
+                                            float& h6l, float& scale_f, float& r_esc_f) {
+  h_fix = (float)dl;
+  const double h6 = dl / 6.0;
+  h6h = (float)h6;
+  h6l = (float)(h6 - (double)h6h);
+  scale_f = (float)dl_scale;
+  r_esc_f = (float)r_esc;
+}
+
+// A job descriptor read around L1 (its slot may have been rewritten by the
+// host since this SM last looked at it).
+__device__ __forceinline__ JobDesc load_job(const JobDesc* src) {
+  JobDesc d;
+  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+  unsigned long long* t = reinterpret_cast<unsigned long long*>(&d);
+#pragma unroll
+  for (int k = 0; k < (int)(sizeof(JobDesc) / 8); ++k) t[k] = __ldcg(s + k);
+  return d;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ void split_pair(const double y[8], float hi[8], float lo[8]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -150,15 +178,16 @@ template <bool kKerr, bool kMixed, int kSrc, int kSink>
 __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const double M = p.M;
-  // FP32-path constants: fixed step as a float pair, 1/6 as a float pair
-  const float h_fix = (float)p.dl;
-  const double h6_fix = p.dl / 6.0;
-  const float h6_fix_h = (float)h6_fix, h6_fix_l = (float)(h6_fix - (double)h6_fix_h);
   const float k6h = (float)(1.0 / 6.0), k6l = (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0));
-  const float scale_f = (float)p.dl_r_scale;
-  const float r_esc_f = (float)p.r_esc;
   const float pole_f = (float)p.zone_pole;
+  // Step rule and termination of the lane's ray: uniform, except for rays of
+  // a job table, which carry their job's values.
+  double M = p.M, dl = p.dl, dl_scale = p.dl_r_scale, r_esc = p.r_esc, eps_hor = p.eps_hor;
+  uint32_t cap = p.cap;
+  // FP32-path constants: fixed step as a float pair, 1/6 as a float pair
+  float h_fix, h6_fix_h, h6_fix_l, scale_f, r_esc_f;
+  step_consts(dl, dl_scale, r_esc, h_fix, h6_fix_h, h6_fix_l, scale_f, r_esc_f);
+  uint32_t job = 0;
 
   double y[8];
   float hi[8], lo[8];
@@ -170,6 +199,8 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
   BH<double> bh64 = make_bh<double>(M, p.a);
   BH<float> bh32 = make_bh<float>(M, p.a);
   int zone_waited = 0;
+  unsigned long long idle_since = 0ull;
+  int claim_backoff = 0;
   bool active = false, drained = false;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -181,17 +212,136 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
   while (true) {
     const unsigned act = __ballot_sync(kFull, active);
     const int idle = 32 - __popc(act);
-    if (!drained && idle > 0 && (idle >= p.refill_min || act == 0)) {
-      // ---- hand the next `idle` rays of the queue to the idle lanes
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(p.head, (unsigned long long)idle);
-      base = __shfl_sync(kFull, base, 0);
-      if (base + (unsigned long long)idle >= p.n) drained = true;
-      const unsigned long long my = base + __popc(~act & lt_mask);
-      if (!active && my < p.n) {
-        id = my;
+    if (kSrc == kSrcServe && claim_backoff > 0) --claim_backoff;
+    if (!drained && idle > 0 && (idle >= p.refill_min || act == 0) && (act == 0 || claim_backoff == 0)) {
+      bool got = false;
+      if (kSrc == kSrcStates || kSrc == kSrcCamera) {
+        // ---- hand the next `idle` rays of the queue to the idle lanes
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(p.head, (unsigned long long)idle);
+        base = __shfl_sync(kFull, base, 0);
+        if (base + (unsigned long long)idle >= p.n) drained = true;
+        const unsigned long long my = base + __popc(~act & lt_mask);
+        if (!active && my < p.n) {
+          id = my;
+          got = true;
+        }
+      } else if (kSrc == kSrcServe) {
+        // ---- claim rays from the active jobs, in the order the host
+        // publishes (smallest first), until every idle lane has one or no
+        // job has rays left; no new claims once the host asked to stop
+        unsigned need = ~act;
+        while (need != 0u) {
+          const int cnt = __popc(need);
+          int slot = -1;
+          unsigned long long base = 0, nj = 0;
+          if (lane == 0 && *p.stop_flag == 0u) {
+            uint32_t na = *p.active_count;
+            if (na > p.max_active) na = p.max_active;
+            for (uint32_t i = 0; i < na; ++i) {
+              const uint64_t jid = p.active_ids[i];
+              if (jid == 0) continue;
+              const uint32_t s = (uint32_t)(jid % p.n_jobs);
+              if (__ldcg(reinterpret_cast<const unsigned long long*>(&p.jobs[s].job_id)) != jid) continue;
+              const unsigned long long ns = __ldcg(reinterpret_cast<const unsigned long long*>(&p.jobs[s].n));
+              if (*reinterpret_cast<volatile unsigned long long*>(&p.job_ctr[s].next) >= ns) continue;
+              const unsigned long long b = atomicAdd(&p.job_ctr[s].next, (unsigned long long)cnt);
+              if (b < ns) {
+                slot = (int)s;
+                base = b;
+                nj = ns;
+                break;
+              }
+            }
+          }
+          slot = __shfl_sync(kFull, slot, 0);
+          base = __shfl_sync(kFull, base, 0);
+          nj = __shfl_sync(kFull, nj, 0);
+          if (slot < 0) break;
+          const unsigned long long avail = nj - base < (unsigned long long)cnt ? nj - base : (unsigned long long)cnt;
+          const bool mine = (need >> lane) & 1u;
+          const unsigned rank = __popc(need & lt_mask);
+          const bool take_it = mine && rank < avail;
+          if (take_it) {
+            job = (uint32_t)slot;
+            id = base + rank;
+            got = true;
+          }
+          need &= ~__ballot_sync(kFull, take_it);
+        }
+      } else {
+        // ---- claim rays job by job, costliest jobs first, until every idle
+        // lane has one or the table is exhausted
+        unsigned need = ~act;
+        while (need != 0u) {
+          const int cnt = __popc(need);
+          unsigned cur = 0;
+          unsigned long long base = 0;
+          if (lane == 0) {
+            cur = *reinterpret_cast<volatile unsigned*>(p.job_cursor);
+            if (cur < p.n_jobs) base = atomicAdd(&p.job_ctr[p.job_order[cur]].next, (unsigned long long)cnt);
+          }
+          cur = __shfl_sync(kFull, cur, 0);
+          base = __shfl_sync(kFull, base, 0);
+          if (cur >= p.n_jobs) {
+            drained = true;
+            break;
+          }
+          const uint32_t jidx = p.job_order[cur];
+          const unsigned long long nj = p.jobs[jidx].n;
+          const unsigned long long avail = base < nj ? (nj - base < (unsigned long long)cnt ? nj - base : cnt) : 0ull;
+          if (avail < (unsigned long long)cnt && lane == 0) atomicCAS(p.job_cursor, cur, cur + 1u);
+          const bool mine = (need >> lane) & 1u;
+          const unsigned rank = __popc(need & lt_mask);
+          const bool take_it = mine && rank < avail;
+          if (take_it) {
+            job = jidx;
+            id = base + rank;
+            got = true;
+          }
+          need &= ~__ballot_sync(kFull, take_it);
+        }
+      }
+      if (kSrc == kSrcServe) {
+        // no ray for any lane of this warp: nap, and leave after idle_ns of
+        // idleness or once the host asks to stop (bounded wait; lane 0 decides)
+        if (act == 0 && __ballot_sync(kFull, got) == 0u) {
+          bool quit = false;
+          if (lane == 0) {
+            const unsigned long long now = global_ns();
+            if (idle_since == 0ull) idle_since = now;
+            quit = *p.stop_flag != 0u || now - idle_since > p.idle_ns;
+          }
+          if (__shfl_sync(kFull, quit, 0)) break;
+          __nanosleep(2000);
+          continue;
+        }
+        idle_since = 0ull;
+        // busy lanes but nothing to claim: look again after 32 warp steps
+        if (__ballot_sync(kFull, got) == 0u) claim_backoff = 32;
+      }
+      if (got) {
         active = true;
-        if (kSrc == kSrcStates) {
+        if (kSrc == kSrcJobs || kSrc == kSrcServe) {
+          const JobDesc J = load_job(&p.jobs[job]);
+          M = J.M;
+          a = J.a;
+          dl = J.dl;
+          dl_scale = J.dl_r_scale;
+          r_esc = J.r_esc;
+          eps_hor = J.eps_hor;
+          cap = J.cap;
+          step_consts(dl, dl_scale, r_esc, h_fix, h6_fix_h, h6_fix_l, scale_f, r_esc_f);
+          if (J.kind == MALBEC_BUNDLE_CAMERA) {
+            camera_state(J.cam, a, id, y);
+          } else if (J.kind == MALBEC_BUNDLE_BOUND) {
+            double a_s;
+            bound_sample(M, a, 1, J.seed, id, y, &a_s);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) y[c] = J.ics[(size_t)c * J.n + id];
+          }
+        } else if (kSrc == kSrcStates) {
 #pragma unroll
           for (int c = 0; c < 8; ++c) y[c] = p.ics[(size_t)c * p.n + id];
           if (p.a_per_ray) a = p.a_per_ray[id];
@@ -201,16 +351,23 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
         bh64 = make_bh<double>(M, a);
         if (kMixed) bh32 = make_bh<float>(M, a);
         const double rp = dev_r_plus(M, a);
-        r_cap = (1.0 + p.eps_hor) * rp;
+        r_cap = (1.0 + eps_hor) * rp;
         lam = 0.0;
         nst = 0;
         zone_waited = 0;
-        if (kMixed || kSink != kSinkCamera) {
+        const bool from_jobs = kSrc == kSrcJobs || kSrc == kSrcServe;
+        const JobDesc* Jp = from_jobs ? &p.jobs[job] : nullptr;
+        const bool camera_ray = kSink == kSinkCamera ||
+                                (from_jobs && __ldcg(reinterpret_cast<const int*>(&Jp->kind)) == MALBEC_BUNDLE_CAMERA);
+        if (kMixed || !camera_ray) {
           double inv[4];
           invariants64(M, a, y, inv);
-          if (kSink != kSinkCamera) {
+          if (!camera_ray) {
+            double* inv0 = from_jobs ? reinterpret_cast<double*>(__ldcg(reinterpret_cast<const unsigned long long*>(&Jp->inv0_out)))
+                                     : p.inv0_out;
+            const uint64_t nn = from_jobs ? __ldcg(reinterpret_cast<const unsigned long long*>(&Jp->n)) : p.n;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) p.inv0_out[(size_t)c * p.n + id] = inv[c];
+            for (int c = 0; c < 4; ++c) inv0[(size_t)c * nn + id] = inv[c];
           }
           if (kMixed) {
             const double cth = cos(y[2]);
@@ -236,8 +393,8 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
     // timing of a ray's steps changes, never their arithmetic.
     bool in_zone = false, take = true;
     if (kMixed) {
-      in_zone = active && nst < p.cap && (hi[1] < r_zone_f || fabsf(__sinf(hi[2])) < pole_lane);
-      const bool want32 = active && nst < p.cap && !in_zone;
+      in_zone = active && nst < cap && (hi[1] < r_zone_f || fabsf(__sinf(hi[2])) < pole_lane);
+      const bool want32 = active && nst < cap && !in_zone;
       const unsigned m64 = __ballot_sync(kFull, in_zone);
       const unsigned m32 = __ballot_sync(kFull, want32);
       const unsigned urgent = __ballot_sync(kFull, in_zone && zone_waited >= p.zone_wait);
@@ -246,33 +403,33 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
       if (in_zone) zone_waited = do64 ? 0 : zone_waited + 1;
     }
     if (!active) continue;
-    if (kMixed && nst < p.cap && !take) continue;
+    if (kMixed && nst < cap && !take) continue;
 
     int fate = 0;
-    if (nst < p.cap) {
+    if (nst < cap) {
       // ---- one RK4 step
       bool captured, escaped, finite;
       if (!kMixed) {
-        const double h = p.dl_r_scale > 0.0 ? p.dl_r_scale * y[1] : p.dl;
+        const double h = dl_scale > 0.0 ? dl_scale * y[1] : dl;
         const double rmin = rk4_step<kKerr, double>(bh64, h, y);
         lam += h;
         captured = (y[1] <= r_cap) | (rmin <= r_cap);
-        escaped = y[1] >= p.r_esc;
+        escaped = y[1] >= r_esc;
         finite = finite8(y);
       } else if (in_zone) {
         // FP64 zone (horizon, photon orbits, polar axis)
 #pragma unroll
         for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
-        const double h = p.dl_r_scale > 0.0 ? p.dl_r_scale * y[1] : p.dl;
+        const double h = dl_scale > 0.0 ? dl_scale * y[1] : dl;
         const double rmin = rk4_step<kKerr, double>(bh64, h, y);
         lam += h;
         split_pair(y, hi, lo);
         captured = (y[1] <= r_cap) | (rmin <= r_cap);
-        escaped = y[1] >= p.r_esc;
+        escaped = y[1] >= r_esc;
         finite = finite8(y);
       } else {
         float hf, h6h, h6l;
-        if (p.dl_r_scale > 0.0) {
+        if (dl_scale > 0.0) {
           hf = scale_f * hi[1];
           h6h = hf * k6h;
           h6l = fmaf(hf, k6h, -h6h) + hf * k6l;
@@ -281,7 +438,7 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
           hf = h_fix;
           h6h = h6_fix_h;
           h6l = h6_fix_l;
-          lam += p.dl;
+          lam += dl;
         }
         const float rmin = rk4_step_mixed<kKerr>(bh32, hf, h6h, h6l, hi, lo);
         captured = (hi[1] <= r_cap_f) | (rmin <= r_cap_f);
@@ -297,7 +454,7 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
         fate = MALBEC_FATE_NONFINITE;
       else if (escaped)
         fate = MALBEC_FATE_ESCAPED;
-      else if (nst >= p.cap)
+      else if (nst >= cap)
         fate = MALBEC_FATE_CAPPED;
     } else {
       fate = MALBEC_FATE_CAPPED;  // n_steps_cap == 0
@@ -308,7 +465,33 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
       }
-      if (kSink == kSinkCamera) {
+      if (kSink == kSinkJobs) {
+        const JobDesc J = load_job(&p.jobs[job]);
+        if (J.kind == MALBEC_BUNDLE_CAMERA) {
+          J.fate_out[id] = (uint8_t)fate;
+          J.steps_out[id] = nst;
+          J.theta_out[id] = y[2];
+          J.phi_out[id] = y[3];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) J.y_out[(size_t)c * J.n + id] = y[c];
+          J.lambda_out[id] = lam;
+          J.steps_out[id] = nst;
+          J.fate_out[id] = (uint8_t)fate;
+          double inv[4];
+          invariants64(M, a, y, inv);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) J.inv1_out[(size_t)c * J.n + id] = inv[c];
+        }
+        // this ray's outputs are visible device-wide before it is counted
+        __threadfence();
+        const unsigned long long finished = atomicAdd(&p.job_ctr[job].done, 1ull) + 1ull;
+        if (kSrc == kSrcServe && finished == J.n) {
+          // last ray of the job: every output is visible, tell the host
+          __threadfence_system();
+          p.done_flags[job] = J.job_id;
+        }
+      } else if (kSink == kSinkCamera) {
         p.fate_out[id] = (uint8_t)fate;
         p.steps_out[id] = nst;
         p.theta_out[id] = y[2];
@@ -338,6 +521,10 @@ const void* kernel_ptr() {
 const void* pick(bool kerr, bool mixed, Source src, Sink sink) {
 #define MALBEC_PICK(K, X, S, T) \
   if (kerr == K && mixed == X && src == S && sink == T) return kernel_ptr<K, X, S, T>();
+  MALBEC_PICK(true, false, kSrcJobs, kSinkJobs)
+  MALBEC_PICK(true, true, kSrcJobs, kSinkJobs)
+  MALBEC_PICK(true, false, kSrcServe, kSinkJobs)
+  MALBEC_PICK(true, true, kSrcServe, kSinkJobs)
   MALBEC_PICK(false, false, kSrcStates, kSinkFinal)
   MALBEC_PICK(true, false, kSrcStates, kSinkFinal)
   MALBEC_PICK(false, true, kSrcStates, kSinkFinal)

@@ -54,9 +54,30 @@ class MixedZone(ctypes.Structure):
     _fields_ = [("horizon_factor", _D), ("photon_margin", _D), ("pole_sin", _D)]
 
 
+BUNDLE_STATES, BUNDLE_CAMERA, BUNDLE_BOUND = 0, 1, 2
+
+
+class Bundle(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", _U32), ("M", _D), ("a", _D), ("term", Term), ("camera", Camera),
+                ("ics", _VP), ("seed", _U64), ("out", _VP)]
+
+
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("threads_per_block", _U32), ("blocks_per_sm", _U32), ("refill_min", _U32),
                 ("zone_batch", _U32), ("zone_wait", _U32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", _SZ), ("max_active", _U32), ("max_pending", _U32), ("precision", ctypes.c_int),
+                ("idle_timeout_s", _D)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", _U64), ("admitted", _U64), ("completed", _U64), ("released", _U64),
+                ("pending", _U64), ("active", _U64), ("bytes_in_use", _U64), ("kernel_launches", _U64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -107,6 +128,20 @@ def _declare(L):
     sig("malbec_ic_bound", ctypes.c_int, _D, _D, ctypes.c_int, _U64, _U64, _U64, _VP, _VP, _VP, _VP)
     sig("malbec_invariants", ctypes.c_int, Metric, _VP, _U64, _VP, _VP)
     sig("malbec_measure_fma_peak", ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D))
+    sig("malbec_bundle_out_bytes", _SZ, ctypes.POINTER(Bundle), ctypes.c_int)
+    sig("malbec_trace_bundles", ctypes.c_int, ctypes.POINTER(Bundle), _U32, ctypes.c_int, _VP)
+    sig("malbec_plan_create", ctypes.c_int, ctypes.POINTER(Bundle), _U32, ctypes.c_int, ctypes.POINTER(_VP))
+    sig("malbec_plan_launch", ctypes.c_int, _VP, _VP)
+    sig("malbec_plan_autotune", ctypes.c_int, _VP, _VP, ctypes.POINTER(LaunchConfig))
+    sig("malbec_plan_destroy", ctypes.c_int, _VP)
+    sig("malbec_server_create", ctypes.c_int, ctypes.POINTER(ServerConfig), ctypes.POINTER(_VP))
+    sig("malbec_server_destroy", ctypes.c_int, _VP)
+    sig("malbec_submit", ctypes.c_int, _VP, ctypes.POINTER(Bundle), ctypes.POINTER(_U64))
+    sig("malbec_poll", ctypes.c_int, _VP, _U64, ctypes.POINTER(ctypes.c_int))
+    sig("malbec_job_output", ctypes.c_int, _VP, _U64, ctypes.POINTER(_VP), ctypes.POINTER(_SZ))
+    sig("malbec_job_copy_output", ctypes.c_int, _VP, _U64, _VP, _SZ, _VP)
+    sig("malbec_job_release", ctypes.c_int, _VP, _U64)
+    sig("malbec_server_stats_get", ctypes.c_int, _VP, ctypes.POINTER(ServerStats))
     sig("malbec_set_launch_config", ctypes.c_int, ctypes.POINTER(LaunchConfig))
     sig("malbec_get_launch_config", ctypes.c_int, ctypes.POINTER(LaunchConfig))
     sig("malbec_set_mixed_zone", ctypes.c_int, ctypes.POINTER(MixedZone))
@@ -246,6 +281,158 @@ def trace_noalloc(M: float, a: float, ics, term, out, mode: int = OUT_FINAL, str
     _check(lib().malbec_trace_noalloc(m, _ptr(ics), n, t.c(), mode, stride if mode == OUT_STRIDED else 0,
                                       _prec(precision), _ptr(out), _stream(stream)), "malbec_trace_noalloc")
     return _views_final(out, L, n, mode, precision)
+
+
+def make_bundle(kind: int, n: int, M: float, a: float, term, camera: Camera | None = None, ics=None,
+                seed: int = 0) -> Bundle:
+    """Describe one bundle (outputs attached by `attach_outputs`)."""
+    b = Bundle()
+    b.kind = int(kind)
+    b.n = int(n)
+    b.M = float(M)
+    b.a = float(a)
+    b.term = term_from(term).c()
+    if camera is not None:
+        b.camera = camera
+    b.ics = None if ics is None else _VP(ics.data_ptr())
+    b.seed = int(seed) & (2**64 - 1)
+    return b
+
+
+def bundle_views(b: Bundle, buf, precision):
+    """Tensor views into a bundle's output buffer."""
+    torch = _torch()
+    n = int(b.n)
+    if b.kind == BUNDLE_CAMERA:
+        L = camera_layout(Camera(1000.0, 1.0, 1.0, n, 1))
+        return {"fate": buf[L.fate: L.fate + n], "steps": buf[L.steps: L.steps + 4 * n].view(torch.int32),
+                "theta": buf[L.theta: L.theta + 8 * n].view(torch.float64),
+                "phi": buf[L.phi: L.phi + 8 * n].view(torch.float64), "buffer": buf}
+    L = out_layout(OUT_FINAL, precision, n, int(b.term.n_steps_cap), 0)
+    return _views_final(buf, L, n, OUT_FINAL, precision)
+
+
+def attach_outputs(bundles, precision):
+    """Allocate (torch) and attach an output buffer to every bundle; returns
+    the per-bundle views."""
+    torch = _torch()
+    views = []
+    for b in bundles:
+        nbytes = lib().malbec_bundle_out_bytes(ctypes.byref(b), _prec(precision))
+        if nbytes == 0:
+            raise MalbecError(EINVAL, "malbec_bundle_out_bytes")
+        buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        b.out = _VP(buf.data_ptr())
+        views.append(bundle_views(b, buf, precision))
+    return views
+
+
+def _bundle_array(bundles):
+    arr = (Bundle * len(bundles))()
+    for i, b in enumerate(bundles):
+        arr[i] = b
+    return arr
+
+
+def trace_bundles(bundles, precision="fp64", stream=None):
+    """Trace a list of Bundle (outputs attached) in one persistent launch."""
+    arr = _bundle_array(bundles)
+    _check(lib().malbec_trace_bundles(arr, len(bundles), _prec(precision), _stream(stream)), "malbec_trace_bundles")
+
+
+class Plan:
+    """Bundles uploaded once; launch replayed as a CUDA graph."""
+
+    def __init__(self, bundles, precision="fp64"):
+        self._arr = _bundle_array(bundles)
+        self._h = _VP()
+        _check(lib().malbec_plan_create(self._arr, len(bundles), _prec(precision), ctypes.byref(self._h)),
+               "malbec_plan_create")
+
+    def launch(self, stream=None):
+        _check(lib().malbec_plan_launch(self._h, _stream(stream)), "malbec_plan_launch")
+
+    def autotune(self, stream=None) -> dict:
+        best = LaunchConfig()
+        _check(lib().malbec_plan_autotune(self._h, _stream(stream), ctypes.byref(best)), "malbec_plan_autotune")
+        return best.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().malbec_plan_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (malbec_server_*)."""
+
+    def __init__(self, hbm_budget: int = 150 * 10**9, max_active: int = 1024, max_pending: int = 100_000,
+                 precision="fp32_mixed", idle_timeout_s: float = 0.002):
+        self.precision = precision
+        cfg = ServerConfig(int(hbm_budget), int(max_active), int(max_pending), _prec(precision),
+                           float(idle_timeout_s))
+        self._h = _VP()
+        _check(lib().malbec_server_create(ctypes.byref(cfg), ctypes.byref(self._h)), "malbec_server_create")
+        self._specs = {}
+
+    def submit(self, bundle: Bundle) -> int:
+        jid = _U64()
+        _check(lib().malbec_submit(self._h, ctypes.byref(bundle), ctypes.byref(jid)), "malbec_submit")
+        self._specs[jid.value] = bundle
+        return jid.value
+
+    def try_submit(self, bundle: Bundle):
+        """submit, or None when the admission queue is full."""
+        jid = _U64()
+        rc = lib().malbec_submit(self._h, ctypes.byref(bundle), ctypes.byref(jid))
+        if rc == EBUSY:
+            return None
+        _check(rc, "malbec_submit")
+        self._specs[jid.value] = bundle
+        return jid.value
+
+    def poll(self, job_id: int) -> bool:
+        d = ctypes.c_int()
+        _check(lib().malbec_poll(self._h, job_id, ctypes.byref(d)), "malbec_poll")
+        return bool(d.value)
+
+    def output(self, job_id: int, stream=None):
+        """Copy a finished job's output into a new CUDA tensor; returns views."""
+        torch = _torch()
+        ptr, nbytes = _VP(), _SZ()
+        _check(lib().malbec_job_output(self._h, job_id, ctypes.byref(ptr), ctypes.byref(nbytes)), "malbec_job_output")
+        buf = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+        _check(lib().malbec_job_copy_output(self._h, job_id, _VP(buf.data_ptr()), nbytes.value, _stream(stream)),
+               "malbec_job_copy_output")
+        return bundle_views(self._specs[job_id], buf, self.precision)
+
+    def release(self, job_id: int):
+        # copies of the output made with `output` run on the current stream
+        _torch().cuda.current_stream().synchronize()
+        _check(lib().malbec_job_release(self._h, job_id), "malbec_job_release")
+        self._specs.pop(job_id, None)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().malbec_server_stats_get(self._h, ctypes.byref(s)), "malbec_server_stats_get")
+        return s.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().malbec_server_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def camera_layout(cam: Camera) -> CameraLayout:
