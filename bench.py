@@ -148,17 +148,48 @@ def cpu_baseline(seconds: float = 12.0, max_seconds: float = 30.0) -> dict:
                       f"{el:.1f} s incl. initial-data construction), OpenMP over rays"}
 
 
+REFERENCE_PIXELS_PER_STEP = 16384
+
+
 def run_reference(args) -> None:
+    """The oracle as it stands, on this host's cores: every step traces a
+    fresh seeded sample of REFERENCE_PIXELS_PER_STEP pixels of the same camera
+    (W warm-up samples, then K timed ones)."""
+    import numpy as np
+
+    import oracle
+
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cb = cpu_baseline(seconds=max(3.0, 10.0 * (args.steps / max(args.steps, 1))))
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": cb["sample"]},
-            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
-                                        "d2h_bytes_per_step": 0}}
+    cw, _ = camera_setup()
+    t_term = oracle.make_term(cw.term.eps_hor, cw.term.r_esc, cw.term.n_steps_cap, cw.term.dl, cw.term.dl_r_scale)
+    rng = np.random.default_rng(20261)
+
+    def sample():
+        pix = rng.choice(cw.n, REFERENCE_PIXELS_PER_STEP, replace=False)
+        t0 = time.perf_counter()
+        ics = oracle.camera_ics(cw.M, cw.a, cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny, pix)
+        out = oracle.trace_many(cw.M, cw.a, ics, t_term, nthreads=0)
+        return int(out["steps"].sum()), time.perf_counter() - t0, out["threads"]
+
+    for _ in range(args.warmup):
+        sample()
+    steps = secs = 0
+    threads = 0
+    for _ in range(args.steps):
+        s, t, threads = sample()
+        steps += s
+        secs += t
+    value = steps / secs
+    cb = {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+          "sample": f"{args.steps} x {REFERENCE_PIXELS_PER_STEP} seeded random pixels of the {cw.nx}x{cw.ny} camera "
+                    f"({steps} RK4 steps in {secs:.1f} s incl. initial data), OpenMP over rays"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": cb["sample"]}, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
@@ -198,6 +229,288 @@ def run_profile_case(args) -> None:
     print(json.dumps({"profile_case": args.profile_case, "rays": cw.n, "rk4_steps": steps}))
 
 
+BUNDLE_FOV_HALF, BUNDLE_R_OBS = 25.0, 1000.0
+
+
+def bundle_of(mb, kind: str, n: int, a: float, cap: int, incl: float, seed: int, side: int = 0):
+    """One malbec_bundle from a workload item: a camera patch (the first n
+    pixels of a side x side camera over +-25M, step 0.05 r) or a generic
+    bound-orbit ensemble sampled in the kernel (dtau = 0.02)."""
+    if kind == "camera":
+        side = side or (math.isqrt(n - 1) + 1)
+        t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=cap, dl=0.0, dl_r_scale=0.05)
+        cam = mb.make_camera(BUNDLE_R_OBS, incl, BUNDLE_FOV_HALF, side, side)
+        return mb.make_bundle(mb.BUNDLE_CAMERA, n, 1.0, a, t, camera=cam)
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=cap, dl=0.02)
+    return mb.make_bundle(mb.BUNDLE_BOUND, n, 1.0, a, t, seed=seed)
+
+
+def steps_of(views) -> int:
+    return int(sum(int(v["steps"].to(__import__("torch").int64).sum().item()) for v in views))
+
+
+def run_bundles_case(mb, torch, stream, flush, count: int, precision: str, K: int, warmup: int,
+                     autotune_every: int = 8) -> dict:
+    """Uneven bundles (the first `count` of the 4096-bundle list): one
+    persistent launch replayed from a CUDA graph after autotuning, against
+    one launch per bundle on the same stream.  Each timed pass is bracketed
+    by CUDA events on the launching stream, with the L2 flushed before it."""
+    from paper_1803_08320_gb300 import workloads as W
+
+    specs = W.bundles()[:count]
+    bundles = [bundle_of(mb, s.kind, s.n, s.a, s.cap, s.incl, s.seed) for s in specs]
+    views = mb.attach_outputs(bundles, precision)
+    rays = sum(s.n for s in specs)
+
+    # autotune on every `autotune_every`-th bundle (same size and cap mix),
+    # then record the full plan with the winning launch configuration
+    saved = mb.get_launch_config().as_dict()
+    sub = bundles[::autotune_every]
+    t_at = time.perf_counter()
+    sub_plan = mb.Plan(sub, precision)
+    best = sub_plan.autotune(stream=stream)
+    torch.cuda.synchronize()
+    sub_plan.close()
+    t_at = time.perf_counter() - t_at
+    mb.set_launch_config(**best)
+    plan = mb.Plan(bundles, precision)
+    mb.set_launch_config(**saved)
+
+    def timed(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for i in range(k):
+            flush.zero_()
+            evs[i][0].record(stream)
+            fn()
+            evs[i][1].record(stream)
+        stream.synchronize()
+        return [s.elapsed_time(e) / 1e3 for s, e in evs]
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            plan.launch(stream=stream)
+        stream.synchronize()
+        t_plan = timed(lambda: plan.launch(stream=stream), K)
+        steps_plan = steps_of(views)
+        fates_plan = [v["fate"].clone() for v in views]
+
+        def per_bundle():
+            for b in bundles:
+                mb.trace_bundles([b], precision, stream=stream)
+
+        per_bundle()
+        stream.synchronize()
+        t_each = timed(per_bundle, K)
+        steps_each = steps_of(views)
+        agree = sum(int((v["fate"] == f).sum().item()) for v, f in zip(views, fates_plan)) / rays
+    plan.close()
+    v_plan = steps_plan / statistics.mean(t_plan)
+    v_each = steps_each / statistics.mean(t_each)
+    return {"bundles": count, "rays": rays, "precision": precision,
+            "rk4_steps_per_pass": steps_plan, "rk4_steps_per_pass_one_launch_each": steps_each,
+            "fate_agreement_between_arms": agree,
+            "persistent_graph": {"value": v_plan, "unit": UNIT, "ms_per_pass": 1e3 * statistics.mean(t_plan),
+                                 "gpu_launches_per_pass": 1},
+            "one_launch_per_bundle": {"value": v_each, "unit": UNIT, "ms_per_pass": 1e3 * statistics.mean(t_each),
+                                      "gpu_launches_per_pass": count},
+            "speedup": v_plan / v_each,
+            "autotune": {"best": best, "on_bundles": len(sub), "seconds": t_at},
+            "l2": "flushed before every timed pass (outside the events)"}
+
+
+def drift_stats(inv0, inv1) -> dict:
+    """Per-particle |inv1 - inv0| / max(|inv0|, 1) of E, L_z, Q and the norm."""
+    import numpy as np
+
+    d = np.abs(inv1 - inv0) / np.maximum(np.abs(inv0), 1.0)
+    out = {}
+    for i, name in enumerate(("E", "Lz", "Q", "norm")):
+        x = d[i][np.isfinite(d[i])]
+        out[name] = {"median": float(np.median(x)), "p99": float(np.quantile(x, 0.99)), "max": float(x.max()),
+                     "frac_le_1e-6": float((x <= 1e-6).mean()), "nonfinite": int((~np.isfinite(d[i])).sum())}
+    return out
+
+
+def cpu_baseline_bound(wl, idx):
+    """The oracle on the 1024-particle subsample of the generic bound-orbit
+    workload (indices k * 1024), on this host's cores: its timing, and its
+    final states for the error statement of the GPU results."""
+    import numpy as np
+
+    import oracle
+
+    t = oracle.make_term(wl.term.eps_hor, wl.term.r_esc, wl.term.n_steps_cap, wl.term.dl, wl.term.dl_r_scale)
+    ys, spins, _ = oracle.bound_samples(wl.M, wl.a_max, wl.seed, idx)
+    t0 = time.perf_counter()
+    ref = oracle.trace_many(wl.M, 0.0, ys, t, a_per_ray=spins, nthreads=0)
+    el = time.perf_counter() - t0
+    steps = int(ref["steps"].sum())
+    return ref, {"value": steps / el, "unit": UNIT, "cores": ref["threads"], "kind": "oracle",
+                 "sample": f"{len(idx)} particles (indices k*1024), {steps} RK4 steps in {el:.1f} s, OpenMP over "
+                           f"particles"}
+
+
+def run_bound_case(mb, torch, stream, flush, n: int, n_steps: int, precisions, with_oracle: bool = True) -> dict:
+    """Generic bound Kerr orbits (spin U[0, 0.998], r_p in [ISCO + 0.5M, 10M],
+    e U[0, 0.7], inclination U[0, pi]; dtau = 0.02): one timed pass per
+    precision (CUDA events on the launching stream, L2 flushed before it;
+    warm-up: the same launch with a 1000-step cap), conserved-quantity drift
+    per particle, and on the subsample k * 1024 the final state against the
+    oracle."""
+    import numpy as np
+
+    from paper_1803_08320_gb300 import workloads as W
+
+    wl = W.bound(n=n, n_steps=n_steps)
+    warm = W.Termination(eps_hor=wl.term.eps_hor, r_esc=wl.term.r_esc, n_steps_cap=1000, dl=wl.term.dl)
+    with torch.cuda.stream(stream):
+        ics, spins, _ = mb.ic_bound(wl.M, wl.a_max, wl.seed, n, stream=stream)
+    stream.synchronize()
+    idx = np.arange(0, n, 1024)[:1024]
+    ref = cb = None
+    if with_oracle:
+        ref, cb = cpu_baseline_bound(wl, idx)
+    res = {"particles": n, "rk4_steps_cap": n_steps, "dtau": wl.term.dl}
+    for prec in precisions:
+        L = mb.out_layout(mb.OUT_FINAL, prec, n, n_steps, 0)
+        out = torch.empty(L.total, dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                mb.trace(wl.M, 0.0, ics, warm, precision=prec, a_per_ray=spins, stream=stream, out=out)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = mb.trace(wl.M, 0.0, ics, wl.term, precision=prec, a_per_ray=spins, stream=stream, out=out)
+            e1.record(stream)
+        stream.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        steps = int(r["steps"].to(torch.int64).sum().item())
+        ent = {"value": steps / sec, "unit": UNIT, "seconds": sec, "rk4_steps": steps,
+               "fates": {k: int((r["fate"] == v).sum().item()) for k, v in
+                         (("captured", 1), ("escaped", 2), ("capped", 3), ("nonfinite", 4))},
+               "drift_all_particles": drift_stats(r["inv0"].cpu().numpy(), r["inv1"].cpu().numpy())}
+        if ref is not None:
+            y = r["y"].cpu().numpy()[:, idx]
+            with np.errstate(invalid="ignore"):
+                rel = np.abs(y - ref["y"]) / np.maximum(np.abs(ref["y"]), 1.0)
+            worst = np.where(np.isfinite(rel), rel, np.inf).max(axis=0)
+            ent["subsample_vs_oracle"] = {
+                "particles": len(idx), "median_max_rel": float(np.median(worst)),
+                "frac_within_1e-9": float((worst <= 1e-9).mean()), "frac_within_1e-6": float((worst <= 1e-6).mean()),
+                "fate_agreement": float((r["fate"].cpu().numpy()[idx] == ref["fate"]).mean()),
+                "oracle_drift": drift_stats(ref["inv0"], ref["inv1"])}
+        res[prec] = ent
+        del out, r
+    if "fp64" in res and "fp32_mixed" in res:
+        res["mixed_speedup_vs_fp64"] = res["fp32_mixed"]["value"] / res["fp64"]["value"]
+    if cb is not None:
+        res["cpu_baseline"] = cb
+    return res
+
+
+def serving_bundle(mb, r):
+    return bundle_of(mb, r.kind, r.n, r.a, r.cap, r.incl, r.seed, side=r.side)
+
+
+def run_serving_case(mb, torch, rate: float, n_req: int, precision: str, budget: int = 150 * 10**9,
+                     timeout_s: float = 300.0) -> dict:
+    """Poisson arrivals at `rate` req/s (the first n_req of the seeded stream),
+    replayed in wall-clock time against (a) the continuous-batching server and
+    (b) one launch per request, in arrival order, on one stream.  Latency =
+    scheduled arrival -> the host sees the job's results complete in HBM.
+    Throughput = all RK4 steps / (first arrival -> last completion)."""
+    from collections import deque
+
+    from paper_1803_08320_gb300 import workloads as W
+
+    reqs = W.serving(rate, duration=50.0 * n_req / rate)[:n_req]
+    n_req = len(reqs)
+    cams = sum(1 for r in reqs if r.kind == "camera")
+
+    def summarise(lat, steps, span):
+        lat = sorted(lat)
+        q = lambda p: lat[min(len(lat) - 1, int(math.ceil(p * len(lat))) - 1)]
+        return {"p50_ms": 1e3 * q(0.50), "p99_ms": 1e3 * q(0.99), "mean_ms": 1e3 * statistics.mean(lat),
+                "max_ms": 1e3 * lat[-1], "steps_per_s": steps / span, "makespan_s": span, "rk4_steps": steps}
+
+    # (a) the server
+    bundles = [serving_bundle(mb, r) for r in reqs]
+    srv = mb.Server(hbm_budget=budget, max_active=1024, precision=precision, idle_timeout_s=0.002)
+    done_at, ids = {}, {}
+    i = 0
+    t0 = time.perf_counter()
+    while len(done_at) < n_req:
+        now = time.perf_counter() - t0
+        assert now < timeout_s, "serving run exceeded its time limit"
+        while i < n_req and reqs[i].t_arrival <= now:
+            ids[srv.submit(bundles[i])] = i
+            i += 1
+        for jid, k in list(ids.items()):
+            if k not in done_at and srv.poll(jid):
+                done_at[k] = time.perf_counter() - t0
+    stats = srv.stats()
+    steps = 0
+    for jid in ids:
+        v = srv.output(jid)
+        steps += int(v["steps"].to(torch.int64).sum().item())
+        srv.release(jid)
+    srv.close()
+    lat = [done_at[k] - reqs[k].t_arrival for k in range(n_req)]
+    served = summarise(lat, steps, max(done_at.values()) - reqs[0].t_arrival)
+    served["gpu_launches"] = int(stats["kernel_launches"])
+
+    # (b) one launch per request, FIFO on one stream
+    stream = torch.cuda.Stream()
+    bundles = [serving_bundle(mb, r) for r in reqs]
+    inflight, bufs, done_at = deque(), [], {}
+    i = 0
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        while len(done_at) < n_req:
+            now = time.perf_counter() - t0
+            assert now < timeout_s, "one-launch-per-request run exceeded its time limit"
+            while i < n_req and reqs[i].t_arrival <= now:
+                (v,) = mb.attach_outputs([bundles[i]], precision)
+                mb.trace_bundles([bundles[i]], precision, stream=stream)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                inflight.append((i, ev))
+                bufs.append(v)
+                i += 1
+            while inflight and inflight[0][1].query():
+                k, _ = inflight.popleft()
+                done_at[k] = time.perf_counter() - t0
+    stream.synchronize()
+    steps_b = steps_of(bufs)
+    lat = [done_at[k] - reqs[k].t_arrival for k in range(n_req)]
+    single = summarise(lat, steps_b, max(done_at.values()) - reqs[0].t_arrival)
+    single["gpu_launches"] = n_req
+    offered = n_req / max(reqs[-1].t_arrival - reqs[0].t_arrival, 1e-9)
+    return {"rate_req_s": rate, "requests": n_req, "camera_requests": cams, "precision": precision,
+            "arrival_span_s": reqs[-1].t_arrival - reqs[0].t_arrival, "offered_req_s": offered,
+            "hbm_budget_bytes": budget, "continuous_batching": served, "one_launch_per_request": single,
+            "p50_speedup": single["p50_ms"] / served["p50_ms"], "p99_speedup": single["p99_ms"] / served["p99_ms"],
+            "throughput_ratio": served["steps_per_s"] / single["steps_per_s"]}
+
+
+def err_stats(torch, dth, dph) -> dict:
+    """|FP32_MIXED - FP64| of the final (theta, phi) of rays both runs call
+    ESCAPED: quantiles, maximum and the count above 1e-6 rad.  Rays that pass
+    within a step of the polar axis are ill-conditioned in both precisions
+    (fixed-step RK4 in Boyer-Lindquist coordinates), so the maximum is
+    dominated by them; the quantiles describe the rest."""
+    out = {"rays": int(dth.numel())}
+    if dth.numel() == 0:
+        return out
+    for name, d in (("theta", dth), ("phi", dph)):
+        d = d.to(torch.float64)
+        qs = torch.quantile(d[:: max(1, d.numel() // 1_000_000)], torch.tensor([0.5, 0.99, 0.999], dtype=torch.float64,
+                                                                              device=d.device))
+        out[name] = {"median": float(qs[0]), "p99": float(qs[1]), "p999": float(qs[2]), "max": float(d.max()),
+                     "above_1e-6": int((d > 1e-6).sum())}
+    return out
+
+
 def timed_renders(mb, cw, cam, precision, K, stream, flush, out=None, host_out=None):
     """K renders, each bracketed by CUDA events on the launching stream; the L2
     is flushed (256 MB write) before each, outside the events."""
@@ -215,6 +528,56 @@ def timed_renders(mb, cw, cam, precision, K, stream, flush, out=None, host_out=N
     return [s.elapsed_time(e) for s, e in evs], res
 
 
+def run_workload(args) -> None:
+    """--workload bundles | serving: one JSON line of its own (1 GPU)."""
+    import torch
+
+    from paper_1803_08320_gb300 import build as _b
+    from paper_1803_08320_gb300 import malbec as mb
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    _b.build()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    dtype = "f64" if args.precision == "fp64" else "f32+f64"
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic"}
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
+        if args.workload == "bundles":
+            count = args.bundle_count or 4096
+            res = run_bundles_case(mb, torch, stream, flush, count, args.precision, K=args.steps,
+                                   warmup=args.warmup)
+            line.update({"value": res["persistent_graph"]["value"],
+                         "ms_per_step": res["persistent_graph"]["ms_per_pass"],
+                         "config": {"workload": f"uneven_bundles_{count}_of_4096_size64-65536_cap1e3-1e5",
+                                    "l2": res["l2"]},
+                         "gpu_launches": args.steps, "bundles": res})
+        elif args.workload == "bound":
+            res = run_bound_case(mb, torch, stream, flush, args.particles, args.bound_steps,
+                                 ["fp64", "fp32_mixed"])
+            line.update({"value": res["fp64"]["value"], "ms_per_step": 1e3 * res["fp64"]["seconds"],
+                         "dtype": "f64",
+                         "config": {"workload": f"kerr_generic_bound_{args.particles}x{args.bound_steps}_dtau0.02",
+                                    "l2": "flushed before the timed pass; state in registers for the whole pass"},
+                         "gpu_launches": 2, "bound": res})
+            if "cpu_baseline" in res:
+                line["cpu_baseline"] = res.pop("cpu_baseline")
+        else:
+            rates = [float(r) for r in args.rates.split(",")]
+            res = [run_serving_case(mb, torch, rate=r, n_req=args.requests, precision=args.precision)
+                   for r in rates]
+            line.update({"value": statistics.mean(r["continuous_batching"]["steps_per_s"] for r in res),
+                         "ms_per_step": None,
+                         "config": {"workload": f"poisson_serving_{args.requests}req_per_rate",
+                                    "rates": rates, "hbm_budget_bytes": 150 * 10**9},
+                         "gpu_launches": sum(r["continuous_batching"]["gpu_launches"] for r in res),
+                         "serving": res})
+    cl = clocks.summary()
+    line["clocks"] = {"sm_mhz": cl["sm_mhz"], "sm_max_mhz": cl["sm_max_mhz"], "reasons": cl["reasons"],
+                      "samples": cl["samples"]}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -224,6 +587,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", choices=["camera_fp64", "camera_mixed"], default=None,
                     help="small case for ncu: a 512x512 render of the same camera, --steps times")
+    ap.add_argument("--workload", choices=["camera", "bundles", "serving", "bound"], default="camera",
+                    help="camera: the headline line (with a bundles and a serving sample); bundles: uneven "
+                         "bundles, persistent graph launch vs one launch per bundle; serving: Poisson "
+                         "arrivals at several rates, continuous batching vs one launch per request; bound: "
+                         "2^20 generic bound Kerr orbits x 10^5 steps, FP64 and FP32_MIXED, drift and error "
+                         "vs the oracle on a 1024-particle subsample")
+    ap.add_argument("--particles", type=int, default=1 << 20, help="particles for --workload bound")
+    ap.add_argument("--bound-steps", type=int, default=100_000, help="step cap for --workload bound")
+    ap.add_argument("--bundle-count", type=int, default=None,
+                    help="bundles taken from the 4096-bundle list (default 4096 for --workload bundles, "
+                         "128 for the sample in the camera line)")
+    ap.add_argument("--precision", choices=["fp64", "fp32_mixed"], default="fp32_mixed",
+                    help="precision of the bundles and serving workloads")
+    ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="req/s for --workload serving")
+    ap.add_argument("--requests", type=int, default=64, help="requests per rate for --workload serving")
+    ap.add_argument("--no-extras", action="store_true", help="camera line without the bundles/serving samples")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -232,6 +611,9 @@ def main():
         return
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.workload != "camera":
+        run_workload(args)
         return
 
     import numpy as np
@@ -342,15 +724,21 @@ def main():
                         "the rays are built on the device from the camera description passed by value"},
         "fp32_mixed": {"value": value32, "unit": UNIT, "ms_per_step": 1e3 * t32 / args.steps,
                        "speedup_vs_fp64": value32 / value, "fate_agreement_vs_fp64": agree,
-                       "escaped_theta_max_abs_err": float(dth.max().item()) if dth.numel() else None,
-                       "escaped_phi_max_abs_err": float(dph.max().item()) if dph.numel() else None,
-                       "escaped_theta_median_abs_err": float(dth.median().item()) if dth.numel() else None,
+                       "escaped_error_vs_fp64": err_stats(torch, dth, dph),
                        "roofline": {"bound": "alu", "peak": peak32, "unit": "GFLOP/s (FP32)",
                                     "achieved_fp32_equiv": FLOPS_PER_STEP["kerr"] * steps32 /
                                     (statistics.mean(times32) / 1e3) / 1e9,
                                     "frac": FLOPS_PER_STEP["kerr"] * steps32 / (statistics.mean(times32) / 1e3)
                                     / 1e9 / peak32}},
     }
+    if world == 1 and not args.no_extras:
+        # samples of the uneven-bundle and serving workloads (FP32_MIXED, the
+        # serving default); full sweeps: --workload bundles / serving
+        line["bundles_sample"] = run_bundles_case(mb, torch, stream, flush, args.bundle_count or 128,
+                                                  args.precision, K=2, warmup=1)
+        line["serving_sample"] = run_serving_case(mb, torch, rate=200.0, n_req=32, precision=args.precision)
+        line["gpu_launches_note"] = ("gpu_launches counts the timed FP64 renders; the samples report their own "
+                                     "launch counts")
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()

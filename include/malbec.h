@@ -260,7 +260,10 @@ typedef struct {
 int malbec_camera_out_layout(const malbec_camera* cam, malbec_camera_layout* layout);
 
 /* Render one camera image: trace every pixel's ray.  m.a_per_ray must be
- * NULL.  out: device, layout.total bytes. */
+ * NULL.  out: device, layout.total bytes.  Rays are started centre columns
+ * first (smallest |alpha|, i.e. smallest |L_z|: the rays that pass closest to
+ * the polar axis and take the most steps); the order is a schedule only, every
+ * pixel's output is the same as in any other order. */
 int malbec_trace_camera(malbec_metric m, const malbec_camera* cam, malbec_term t,
                         malbec_precision prec, void* out, malbec_stream stream);
 

@@ -341,15 +341,21 @@ int malbec_plan_launch(malbec_plan* plan, malbec_stream stream) {
 
 int malbec_plan_autotune(malbec_plan* plan, malbec_stream stream, malbec_launch_config* best) {
   if (!plan) return MALBEC_EINVAL;
+  // Candidates: block size x blocks per SM (4 or 8 resident warps per SM,
+  // plus 16 for the FP32 path), refill granularity (dead lanes a warp waits
+  // for before it claims new rays) and, for FP32_MIXED, the FP64-zone batch.
   std::vector<malbec_launch_config> cand;
   if (!plan->mixed) {
-    for (uint32_t bps : {1u, 2u})
-      for (uint32_t rm : {1u, 4u}) cand.push_back({128u, bps, rm, 0u, 0u});
+    for (uint32_t rm : {1u, 4u}) cand.push_back({128u, 1u, rm, 0u, 0u});
     cand.push_back({64u, 2u, 1u, 0u, 0u});
+    cand.push_back({128u, 2u, 1u, 0u, 0u});
+    cand.push_back({256u, 1u, 1u, 0u, 0u});
+    cand.push_back({32u, 4u, 1u, 0u, 0u});
   } else {
-    for (uint32_t bps : {1u, 2u})
-      for (uint32_t zb : {8u, 16u})
-        for (uint32_t zw : {64u, 256u}) cand.push_back({128u, bps, 1u, zb, zw});
+    const uint32_t shapes[4][2] = {{128u, 2u}, {256u, 1u}, {128u, 1u}, {128u, 4u}};
+    for (const auto& sh : shapes)
+      for (uint32_t z = 0; z < 2; ++z) cand.push_back({sh[0], sh[1], 1u, z ? 16u : 8u, z ? 256u : 64u});
+    cand.push_back({128u, 2u, 4u, 8u, 64u});
   }
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;

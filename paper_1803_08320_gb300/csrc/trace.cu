@@ -174,8 +174,13 @@ __device__ __forceinline__ void split_pair(const double y[8], float hi[8], float
   }
 }
 
+// Launch bounds: at most kMaxTPB threads, one block per SM guaranteed.  The
+// kernel runs one to eight warps per SM (see choose_shape), so the register
+// budget is not the occupancy limit; without the minimum-blocks argument the
+// compiler capped some instantiations (the request-loop ones) at 128
+// registers and spilled.
 template <bool kKerr, bool kMixed, int kSrc, int kSink>
-__global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
+__global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const float k6h = (float)(1.0 / 6.0), k6l = (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0));
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(kMaxTPB) trace_kernel(const TraceParams p) {
         if (base + (unsigned long long)idle >= p.n) drained = true;
         const unsigned long long my = base + __popc(~act & lt_mask);
         if (!active && my < p.n) {
-          id = my;
+          id = kSrc == kSrcCamera ? camera_claim_pixel(p.cam, my) : my;
           got = true;
         }
       } else if (kSrc == kSrcServe) {

@@ -150,7 +150,7 @@ def test_plan_replays_and_autotunes(mb):
         for v, r in zip(views, ref):
             assert torch.equal(v["fate"], r["fate"]) and torch.equal(v["steps"], r["steps"])
     best = plan.autotune()
-    assert best["threads_per_block"] in (64, 128)
+    assert best["threads_per_block"] in (32, 64, 128, 256)
     for v in views:
         v["buffer"].zero_()
     plan.launch()

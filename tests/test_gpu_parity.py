@@ -259,6 +259,38 @@ def test_camera_small_image_parity(mb, orc, W):
     assert_states_close(got["phi"][esc], ref["y"][3][esc], what="phi")
 
 
+@pytest.mark.parametrize("nx,ny,precision", [(37, 23, "fp64"), (48, 5, "fp64"), (1, 9, "fp64"), (2, 3, "fp64"),
+                                              (37, 23, "fp32_mixed"), (48, 5, "fp32_mixed")])
+def test_camera_claim_order_is_a_schedule_only(mb, W, nx, ny, precision):
+    """The camera kernel starts the centre columns first; its per-pixel
+    output equals the trace of the same pixels' initial states in index order
+    (odd and even widths, one and two columns): bitwise in FP64; in
+    FP32_MIXED (two kernel instantiations may round an FP32 operation
+    differently) fates and steps on >= 99% of pixels, angles within 1e-6."""
+    import torch
+
+    cw = W.camera(nx=nx, ny=ny)
+    cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, nx, ny)
+    img = mb.trace_camera(cw.M, cw.a, cam, cw.term, precision)
+    ics = mb.ic_camera(cw.M, cw.a, cam, np.arange(nx * ny))
+    ref = mb.trace(cw.M, cw.a, ics, cw.term, precision=precision)
+    torch.cuda.synchronize()
+    steps_ref = ref["steps"].to(img["steps"].dtype)
+    if precision == "fp64":
+        assert torch.equal(img["fate"], ref["fate"]) and torch.equal(img["steps"], steps_ref)
+        for k, c in (("theta", 2), ("phi", 3)):
+            x, y = img[k], ref["y"][c]
+            assert torch.equal(torch.isnan(x), torch.isnan(y)), k
+            assert torch.equal(torch.nan_to_num(x), torch.nan_to_num(y)), k
+    else:
+        same = (img["fate"] == ref["fate"]) & (img["steps"] == steps_ref)
+        assert same.float().mean().item() >= 0.99
+        for k, c in (("theta", 2), ("phi", 3)):
+            x, y = np_(img[k][same]), np_(ref["y"][c][same])
+            fin = np.isfinite(y) & (np.abs(y) < 1e3)
+            assert_states_close(x[fin], y[fin], rtol=1e-6, what=k)
+
+
 def test_camera_full_size_sampled_parity(mb, orc, W):
     """The full 1024 x 1024 render in the benchmark's launch configuration,
     checked on 3000 seeded sample pixels: >= 99.99% fate agreement away from
