@@ -44,8 +44,11 @@ def kernel_source_hash() -> str:
 
 
 # algorithmic flops per RK4 step, counted from the kernel source expressions
-# (FMA = 2, add/mul = 1); divisions and sincos are listed separately (4 each)
-FLOPS_PER_STEP = {"kerr": 4 * 131 + 96, "schw": 4 * 42 + 96}
+# (FMA = 2, add/mul = 1, a product or sum written once and reused counted
+# once): 128 per Kerr right-hand side, 42 per Schwarzschild one, 86 for the
+# RK4 stages and combination; divisions and sincos are listed separately
+# (4 each per step)
+FLOPS_PER_STEP = {"kerr": 4 * 128 + 86, "schw": 4 * 42 + 86}
 DIV_PER_STEP, SINCOS_PER_STEP = 4, 4
 
 

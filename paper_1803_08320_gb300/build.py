@@ -20,7 +20,12 @@ LIB = os.path.join(OUT, "libmalbec.so")
 SOURCES = ["api.cu", "trace.cu", "ic.cu", "peaks.cu", "noalloc.cu", "bundles.cu", "server.cu"]
 HEADERS = ["geodesic.cuh", "camera.cuh", "bound.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+# -fmad=false: no implicit multiply-add contraction, so every kernel that
+# evaluates the same source expression rounds it the same way (results of a
+# ray do not depend on the entry point that traced it); the hot expressions
+# are written with explicit fma().  Host code: no contraction either.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 

@@ -93,7 +93,7 @@ __device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T th, T ut, T u
   const T q = bh.twoM * r * irho2;
   const T dq_r = fma(T(-2) * r, q, bh.twoM) * irho2;
   const T dq_th = T(2) * a2 * sc * q * irho2;
-  const T r2a2 = r2 + a2;
+  const T r2a2 = fma(r, r, a2);
   const T s4 = s2 * s2;
   // d_r and d_theta of g_tt, g_tph, g_phph, g_rr, g_thth
   const T dtp_r = -a * s2 * dq_r;
@@ -162,8 +162,8 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
   const T h6 = h * T(1.0 / 6.0);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const T dx = y[4 + j] + T(2) * u2[j] + T(2) * u3[j] + u4[j];
-    const T du = a1[j] + T(2) * a2[j] + T(2) * a3[j] + a4[j];
+    const T dx = fma(T(2), u2[j] + u3[j], y[4 + j] + u4[j]);
+    const T du = fma(T(2), a2[j] + a3[j], a1[j] + a4[j]);
     y[j] = fma(h6, dx, y[j]);
     y[4 + j] = fma(h6, du, y[4 + j]);
   }
@@ -183,7 +183,7 @@ __device__ __forceinline__ void invariants64(double M, double a, const double y[
   const double q = 2.0 * M * r / rho2;
   const double gtt = q - 1.0;
   const double gtp = -a * s2 * q;
-  const double gpp = s2 * fma(a2 * s2, q, r * r + a2);
+  const double gpp = s2 * fma(a2 * s2, q, fma(r, r, a2));
   const double pt = fma(gtt, y[4], gtp * y[7]);
   const double pp = fma(gtp, y[4], gpp * y[7]);
   const double pr = rho2 / Delta * y[5];
@@ -192,7 +192,7 @@ __device__ __forceinline__ void invariants64(double M, double a, const double y[
   const double E = -pt;
   inv[0] = E;
   inv[1] = pp;
-  inv[2] = fma(pth, pth, c * c * fma(a2, -norm - E * E, pp * pp / s2));
+  inv[2] = fma(pth, pth, c * c * fma(a2, fma(-E, E, -norm), pp * pp / s2));
   inv[3] = norm;
 }
 

@@ -130,9 +130,9 @@ __device__ __forceinline__ float rk4_step_mixed(const BH<float>& bh, float hf, f
     const float sx = fmaf(2.f, u2[j] + u3[j], hi[4 + j] + u4[j]);
     const float su = fmaf(2.f, a2[j] + a3[j], a1[j] + a4[j]);
     const float dx = h6h * sx;
-    const float dxe = fmaf(h6h, sx, -dx) + h6l * sx;
+    const float dxe = fmaf(h6l, sx, fmaf(h6h, sx, -dx));
     const float du = h6h * su;
-    const float due = fmaf(h6h, su, -du) + h6l * su;
+    const float due = fmaf(h6l, su, fmaf(h6h, su, -du));
     comp_add(hi[j], lo[j], dx, dxe);
     comp_add(hi[4 + j], lo[4 + j], du, due);
   }
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         if (dl_scale > 0.0) {
           hf = scale_f * hi[1];
           h6h = hf * k6h;
-          h6l = fmaf(hf, k6h, -h6h) + hf * k6l;
+          h6l = fmaf(hf, k6l, fmaf(hf, k6h, -h6h));
           lam += (double)hf;
         } else {
           hf = h_fix;
