@@ -392,6 +392,11 @@ def run_bound_case(mb, torch, stream, flush, n: int, n_steps: int, precisions, w
                "fates": {k: int((r["fate"] == v).sum().item()) for k, v in
                          (("captured", 1), ("escaped", 2), ("capped", 3), ("nonfinite", 4))},
                "drift_all_particles": drift_stats(r["inv0"].cpu().numpy(), r["inv1"].cpu().numpy())}
+        capped = (r["fate"] == mb.FATE_CAPPED).cpu().numpy()
+        ent["drift_capped_particles"] = drift_stats(r["inv0"].cpu().numpy()[:, capped],
+                                                    r["inv1"].cpu().numpy()[:, capped])
+        ent["drift_note"] = ("particles that end before the cap are orbits that pass next to the polar axis, where "
+                             "fixed-step RK4 in Boyer-Lindquist coordinates is ill-conditioned in any precision")
         if ref is not None:
             y = r["y"].cpu().numpy()[:, idx]
             with np.errstate(invalid="ignore"):

@@ -145,9 +145,16 @@ int malbec_get_mixed_zone(malbec_mixed_zone* zone);
  *   refill_min         a warp takes new rays once this many lanes are idle
  *                      (automatic: 1);
  *   zone_batch         FP32_MIXED: an FP64-zone warp step waits for this many
- *                      lanes (automatic: 8) ...
+ *                      lanes (automatic: 8 with the exchange below, 32
+ *                      without) ...
  *   zone_wait          ... or until a waiting lane sat out this many warp
- *                      steps (automatic: 64).
+ *                      steps (automatic: 64);
+ *   exchange           FP32_MIXED: 1 = the warps of a block hand FP64-zone
+ *                      rays to one zone warp per block and take FP32 rays
+ *                      back (zone steps run with fuller warps), 2 = every
+ *                      ray stays in its warp (automatic: 2 for whole-image
+ *                      cameras, whose rays spend few steps in the zone, 1
+ *                      otherwise).
  * The choice changes speed only: every ray's arithmetic is the same.
  * NULL restores all-automatic.  Thread-safe. */
 typedef struct {
@@ -156,6 +163,7 @@ typedef struct {
   uint32_t refill_min;
   uint32_t zone_batch;
   uint32_t zone_wait;
+  uint32_t exchange;
 } malbec_launch_config;
 
 int malbec_set_launch_config(const malbec_launch_config* cfg);

@@ -67,7 +67,7 @@ int device_sms(int* sms) {
 
 namespace {
 std::mutex g_launch_mu;
-malbec_launch_config g_launch = {0, 0, 0, 0, 0};
+malbec_launch_config g_launch = {0, 0, 0, 0, 0, 0};
 
 malbec_launch_config launch_config() {
   std::lock_guard<std::mutex> lk(g_launch_mu);
@@ -146,8 +146,9 @@ void fill_zone(TraceParams& p) {
     p.zone_pole = g_zone.pole_sin;
   }
   const malbec_launch_config cfg = launch_config();
-  p.zone_batch = cfg.zone_batch ? (int)cfg.zone_batch : 8;
+  p.zone_batch = cfg.zone_batch ? (int)cfg.zone_batch : -1;  // -1: the launcher decides
   p.zone_wait = cfg.zone_wait ? (int)cfg.zone_wait : 64;
+  p.exchange = cfg.exchange ? (cfg.exchange == 1 ? 1 : 0) : -1;  // -1: the launcher decides
 }
 
 int set_cuda_error(cudaError_t e) {
@@ -216,11 +217,12 @@ int malbec_set_mixed_zone(const malbec_mixed_zone* z) {
 }
 
 int malbec_set_launch_config(const malbec_launch_config* cfg) {
-  malbec_launch_config v = {0, 0, 0, 0, 0};
+  malbec_launch_config v = {0, 0, 0, 0, 0, 0};
   if (cfg) {
     if (cfg->threads_per_block && (cfg->threads_per_block % 32 != 0 || cfg->threads_per_block > 256))
       return MALBEC_EINVAL;
-    if (cfg->blocks_per_sm > 64 || cfg->refill_min > 32 || cfg->zone_batch > 32 || cfg->zone_wait > 1000000)
+    if (cfg->blocks_per_sm > 64 || cfg->refill_min > 32 || cfg->zone_batch > 32 || cfg->zone_wait > 1000000 ||
+        cfg->exchange > 2)
       return MALBEC_EINVAL;
     v = *cfg;
   }

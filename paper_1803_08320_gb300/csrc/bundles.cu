@@ -200,7 +200,7 @@ struct malbec_plan {
   bool mixed = false;
   void* block = nullptr;
   BlockLayout bl;
-  malbec_launch_config cfg = {0, 0, 0, 0, 0};
+  malbec_launch_config cfg = {0, 0, 0, 0, 0, 0};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -219,6 +219,7 @@ int record_plan(malbec_plan* P, const malbec_launch_config& cfg) {
   p.refill_min = refill_min;
   if (cfg.zone_batch) p.zone_batch = (int)cfg.zone_batch;
   if (cfg.zone_wait) p.zone_wait = (int)cfg.zone_wait;
+  if (cfg.exchange) p.exchange = cfg.exchange == 1 ? 1 : 0;
   cudaStream_t s = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (e != cudaSuccess) return set_cuda_error(e);
@@ -341,21 +342,23 @@ int malbec_plan_launch(malbec_plan* plan, malbec_stream stream) {
 
 int malbec_plan_autotune(malbec_plan* plan, malbec_stream stream, malbec_launch_config* best) {
   if (!plan) return MALBEC_EINVAL;
-  // Candidates: block size x blocks per SM (4 or 8 resident warps per SM,
-  // plus 16 for the FP32 path), refill granularity (dead lanes a warp waits
-  // for before it claims new rays) and, for FP32_MIXED, the FP64-zone batch.
+  // Candidates: block size x blocks per SM (4 or 8 resident warps per SM for
+  // FP64; 8 or 12 for the FP32 path), refill granularity (dead lanes a warp
+  // waits for before it claims new rays) and, for FP32_MIXED, the FP64-zone
+  // batch and the block ray exchange on or off.
   std::vector<malbec_launch_config> cand;
   if (!plan->mixed) {
-    for (uint32_t rm : {1u, 4u}) cand.push_back({128u, 1u, rm, 0u, 0u});
-    cand.push_back({64u, 2u, 1u, 0u, 0u});
-    cand.push_back({128u, 2u, 1u, 0u, 0u});
-    cand.push_back({256u, 1u, 1u, 0u, 0u});
-    cand.push_back({32u, 4u, 1u, 0u, 0u});
+    for (uint32_t rm : {1u, 4u}) cand.push_back({128u, 1u, rm, 0u, 0u, 0u});
+    cand.push_back({64u, 2u, 1u, 0u, 0u, 0u});
+    cand.push_back({128u, 2u, 1u, 0u, 0u, 0u});
+    cand.push_back({256u, 1u, 1u, 0u, 0u, 0u});
+    cand.push_back({32u, 4u, 1u, 0u, 0u, 0u});
   } else {
-    const uint32_t shapes[4][2] = {{128u, 2u}, {256u, 1u}, {128u, 1u}, {128u, 4u}};
+    const uint32_t shapes[3][2] = {{128u, 2u}, {256u, 1u}, {128u, 3u}};
     for (const auto& sh : shapes)
-      for (uint32_t z = 0; z < 2; ++z) cand.push_back({sh[0], sh[1], 1u, z ? 16u : 8u, z ? 256u : 64u});
-    cand.push_back({128u, 2u, 4u, 8u, 64u});
+      for (uint32_t z = 0; z < 2; ++z)
+        for (uint32_t x = 1; x <= 2; ++x) cand.push_back({sh[0], sh[1], 1u, z ? 16u : 8u, z ? 256u : 64u, x});
+    cand.push_back({128u, 2u, 4u, 8u, 64u, 1u});
   }
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;

@@ -137,37 +137,60 @@ __device__ __forceinline__ void accel(const BH<T>& bh, T r, T th, T ut, T ur, T 
 // ---------------------------------------------------------------------------
 // One classical RK4 step (tableau c = (0, 1/2, 1/2, 1), b = (1, 2, 2, 1)/6)
 // of y = (x, u).  t and phi never enter the right-hand side, so their stage
-// values are not formed.  Returns the smallest radius among the three
+// values are not formed.  The weighted sums k1 + 2 k2 + 2 k3 + k4 of the
+// stage velocities and accelerations are accumulated stage by stage (the same
+// operations in the same order whether the stage loop is unrolled or not, so
+// both forms give the same bits).  kRolled keeps one copy of the right-hand
+// side in the code (the FP32_MIXED kernels, whose size otherwise costs
+// instruction-cache misses).  Returns the smallest radius among the three
 // intermediate stage points (used by the capture test).
-template <bool kKerr, typename T>
+template <bool kKerr, typename T, bool kRolled = false>
 __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
   const T hh = T(0.5) * h;
-  T a1[4], a2[4], a3[4], a4[4];
-  accel<kKerr, T>(bh, y[1], y[2], y[4], y[5], y[6], y[7], a1);
-  T u2[4];
+  T r = y[1], th = y[2];
+  T u[4] = {y[4], y[5], y[6], y[7]};
+  T sx[4], su[4];
+  T rmin = T(0);
+  auto stage = [&](int s) {
+    T acc[4];
+    accel<kKerr, T>(bh, r, th, u[0], u[1], u[2], u[3], acc);
+    if (s == 0) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) u2[j] = fma(hh, a1[j], y[4 + j]);
-  const T r2 = fma(hh, y[5], y[1]), th2 = fma(hh, y[6], y[2]);
-  accel<kKerr, T>(bh, r2, th2, u2[0], u2[1], u2[2], u2[3], a2);
-  T u3[4];
+      for (int j = 0; j < 4; ++j) {
+        sx[j] = u[j];
+        su[j] = acc[j];
+      }
+    } else {
+      const T w = s == 3 ? T(1) : T(2);
 #pragma unroll
-  for (int j = 0; j < 4; ++j) u3[j] = fma(hh, a2[j], y[4 + j]);
-  const T r3 = fma(hh, u2[1], y[1]), th3 = fma(hh, u2[2], y[2]);
-  accel<kKerr, T>(bh, r3, th3, u3[0], u3[1], u3[2], u3[3], a3);
-  T u4[4];
+      for (int j = 0; j < 4; ++j) {
+        sx[j] = fma(w, u[j], sx[j]);
+        su[j] = fma(w, acc[j], su[j]);
+      }
+    }
+    if (s < 3) {
+      const T c = s < 2 ? hh : h;
+      r = fma(c, u[1], y[1]);
+      th = fma(c, u[2], y[2]);
 #pragma unroll
-  for (int j = 0; j < 4; ++j) u4[j] = fma(h, a3[j], y[4 + j]);
-  const T r4 = fma(h, u3[1], y[1]), th4 = fma(h, u3[2], y[2]);
-  accel<kKerr, T>(bh, r4, th4, u4[0], u4[1], u4[2], u4[3], a4);
+      for (int j = 0; j < 4; ++j) u[j] = fma(c, acc[j], y[4 + j]);
+      rmin = s == 0 ? r : fmin(rmin, r);
+    }
+  };
+  if constexpr (kRolled) {
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) stage(s);
+  } else {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) stage(s);
+  }
   const T h6 = h * T(1.0 / 6.0);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const T dx = fma(T(2), u2[j] + u3[j], y[4 + j] + u4[j]);
-    const T du = fma(T(2), a2[j] + a3[j], a1[j] + a4[j]);
-    y[j] = fma(h6, dx, y[j]);
-    y[4 + j] = fma(h6, du, y[4 + j]);
+    y[j] = fma(h6, sx[j], y[j]);
+    y[4 + j] = fma(h6, su[j], y[4 + j]);
   }
-  return fmin(fmin(r2, r3), r4);
+  return rmin;
 }
 
 // ---------------------------------------------------------------------------

@@ -73,6 +73,7 @@ struct TraceParams {
   // FP32_MIXED FP64 zone (malbec_mixed_zone) and the batching of zone steps
   double zone_horizon, zone_photon, zone_pole;
   int zone_batch, zone_wait;
+  int exchange;       // FP32_MIXED: block ray exchange on (1) / off (0)
   // work queue (scratch, zeroed before launch)
   unsigned long long* head;
   // multi-job source: job table, per-job counters (zeroed), longest-first

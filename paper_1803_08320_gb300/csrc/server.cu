@@ -6,14 +6,16 @@
 //  - job descriptors live in a device ring of kRing slots (slot = id % kRing);
 //    the host writes a slot (descriptor + zeroed counters) on its control
 //    stream and waits for that copy before publishing the id;
-//  - the active list (ids, smallest estimated job first) and its length are
-//    in mapped host memory; the kernel reads them with volatile loads and
-//    validates every id against the slot's descriptor, so a list the host is
-//    rewriting can at worst hide a job for one look;
+//  - the active list (ids, smallest estimated job first), its length and the
+//    stop flag live in device memory: the host builds them in pinned memory
+//    and copies them on its control stream, so the kernel's look at the list
+//    never leaves the GPU; it reads them with volatile loads and validates
+//    every id against the slot's descriptor, so a list being rewritten can at
+//    worst hide a job for one look;
 //  - the last ray of a job writes the job id into done_flags[slot] (mapped
 //    host memory) after a system-scope fence;
-//  - a stop flag in mapped memory ends claiming; the kernel also leaves by
-//    itself after idle_timeout_s without work (bounded wait on %globaltimer).
+//  - the stop flag ends claiming; the kernel also leaves by itself after
+//    idle_timeout_s without work (bounded wait on %globaltimer).
 #include <math.h>
 #include <string.h>
 
@@ -42,12 +44,6 @@ struct Job {
   int state = kPending;
 };
 
-struct Control {
-  // mapped host memory; the kernel sees it through the device aliases
-  uint32_t active_count;
-  uint32_t stop;
-};
-
 }  // namespace
 }  // namespace malbec
 
@@ -63,12 +59,14 @@ struct malbec_server {
   cudaMemPool_t pool = nullptr;
   JobDesc* d_ring = nullptr;
   JobCounter* d_ctr = nullptr;
-  // mapped host memory
-  void* h_block = nullptr;
-  uint64_t* h_active = nullptr;
-  Control* h_ctl = nullptr;
+  // active list: [count, stop] then the ids; built in pinned host memory,
+  // copied to the device
+  uint64_t* h_list = nullptr;
+  uint64_t* d_list = nullptr;
+  uint32_t stop = 0;
+  // done flags, one per ring slot, in mapped host memory
   uint64_t* h_done = nullptr;
-  void* d_block = nullptr;  // device alias of h_block
+  uint64_t* d_done = nullptr;  // device alias of h_done
   uint64_t next_id = 1;
   std::unordered_map<uint64_t, Job> jobs;
   std::deque<uint64_t> pending;
@@ -79,20 +77,21 @@ struct malbec_server {
 
 namespace {
 
-size_t host_block_bytes(uint32_t max_active) {
-  return (size_t)max_active * sizeof(uint64_t) + sizeof(Control) + (size_t)kRing * sizeof(uint64_t) + 64;
-}
-
-// Republish the active list, smallest estimated job first.
-void publish_active(malbec_server* S) {
+// Republish the active list, smallest estimated job first, with the stop
+// flag: build it in pinned memory, copy it to the device and wait for the
+// copy (the pinned buffer is reused by the next publish).
+int publish_active(malbec_server* S) {
   std::stable_sort(S->active.begin(), S->active.end(),
                    [&](uint64_t x, uint64_t y) { return S->jobs[x].cost < S->jobs[y].cost; });
   const uint32_t k = (uint32_t)S->active.size();
-  volatile uint64_t* ids = S->h_active;
-  for (uint32_t i = 0; i < k; ++i) ids[i] = S->active[i];
-  std::atomic_thread_fence(std::memory_order_seq_cst);
-  reinterpret_cast<volatile uint32_t*>(&S->h_ctl->active_count)[0] = k;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
+  uint32_t* hdr = reinterpret_cast<uint32_t*>(S->h_list);
+  hdr[0] = k;
+  hdr[1] = S->stop;
+  for (uint32_t i = 0; i < k; ++i) S->h_list[1 + i] = S->active[i];
+  cudaError_t e = cudaMemcpyAsync(S->d_list, S->h_list, (size_t)(k + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                                  S->control);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S->control);
+  return e == cudaSuccess ? MALBEC_OK : set_cuda_error(e);
 }
 
 int launch_kernel(malbec_server* S) {
@@ -104,12 +103,10 @@ int launch_kernel(malbec_server* S) {
   p.jobs = S->d_ring;
   p.job_ctr = S->d_ctr;
   p.n_jobs = kRing;
-  char* d = static_cast<char*>(S->d_block);
-  const size_t ids_bytes = (size_t)S->cfg.max_active * sizeof(uint64_t);
-  p.active_ids = reinterpret_cast<const volatile uint64_t*>(d);
-  p.active_count = reinterpret_cast<const volatile uint32_t*>(d + ids_bytes + offsetof(Control, active_count));
-  p.stop_flag = reinterpret_cast<const volatile uint32_t*>(d + ids_bytes + offsetof(Control, stop));
-  p.done_flags = reinterpret_cast<volatile uint64_t*>(d + ids_bytes + sizeof(Control));
+  p.active_ids = reinterpret_cast<const volatile uint64_t*>(S->d_list + 1);
+  p.active_count = reinterpret_cast<const volatile uint32_t*>(S->d_list);
+  p.stop_flag = reinterpret_cast<const volatile uint32_t*>(S->d_list) + 1;
+  p.done_flags = reinterpret_cast<volatile uint64_t*>(S->d_done);
   p.max_active = S->cfg.max_active;
   p.idle_ns = (uint64_t)(S->cfg.idle_timeout_s * 1e9);
   fill_zone(p);
@@ -162,12 +159,12 @@ int admit(malbec_server* S) {
     S->stats.admitted++;
     changed = true;
   }
-  if (changed) publish_active(S);
+  if (changed) return publish_active(S);
   return MALBEC_OK;
 }
 
 // Move jobs whose completion flag is set from the active list to done.
-void reap(malbec_server* S) {
+int reap(malbec_server* S) {
   bool changed = false;
   for (size_t i = 0; i < S->active.size();) {
     const uint64_t id = S->active[i];
@@ -181,7 +178,8 @@ void reap(malbec_server* S) {
       ++i;
     }
   }
-  if (changed) publish_active(S);
+  if (changed) return publish_active(S);
+  return MALBEC_OK;
 }
 
 }  // namespace
@@ -218,27 +216,33 @@ int malbec_server_create(const malbec_server_config* cfg, malbec_server** server
   if (e == cudaSuccess) e = cudaMalloc(&S->d_ctr, (size_t)kRing * sizeof(JobCounter));
   if (e == cudaSuccess) e = cudaMemset(S->d_ring, 0, (size_t)kRing * sizeof(JobDesc));
   if (e == cudaSuccess) e = cudaMemset(S->d_ctr, 0, (size_t)kRing * sizeof(JobCounter));
-  if (e == cudaSuccess) e = cudaHostAlloc(&S->h_block, host_block_bytes(cfg->max_active), cudaHostAllocMapped);
-  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&S->d_block, S->h_block, 0);
+  const size_t list_bytes = (size_t)(cfg->max_active + 1) * sizeof(uint64_t);
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_list, list_bytes);
+  if (e == cudaSuccess) e = cudaMemset(S->d_list, 0, list_bytes);
+  if (e == cudaSuccess) e = cudaHostAlloc(&S->h_list, list_bytes, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(&S->h_done, (size_t)kRing * sizeof(uint64_t), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&S->d_done, S->h_done, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     int rc = set_cuda_error(e);
     malbec_server_destroy(S);
     return rc;
   }
-  memset(S->h_block, 0, host_block_bytes(cfg->max_active));
-  char* h = static_cast<char*>(S->h_block);
-  S->h_active = reinterpret_cast<uint64_t*>(h);
-  S->h_ctl = reinterpret_cast<Control*>(h + (size_t)cfg->max_active * sizeof(uint64_t));
-  S->h_done = reinterpret_cast<uint64_t*>(h + (size_t)cfg->max_active * sizeof(uint64_t) + sizeof(Control));
+  memset(S->h_list, 0, list_bytes);
+  memset(S->h_done, 0, (size_t)kRing * sizeof(uint64_t));
   *server = S;
   return MALBEC_OK;
 }
 
 int malbec_server_destroy(malbec_server* S) {
   if (!S) return MALBEC_EINVAL;
-  if (S->h_ctl) {
-    reinterpret_cast<volatile uint32_t*>(&S->h_ctl->stop)[0] = 1u;
-    std::atomic_thread_fence(std::memory_order_seq_cst);
+  if (S->h_list && S->d_list && S->control) {
+    // stop claiming: copy the list header with the stop flag set
+    S->stop = 1u;
+    uint32_t* hdr = reinterpret_cast<uint32_t*>(S->h_list);
+    hdr[1] = 1u;
+    if (cudaMemcpyAsync(S->d_list, S->h_list, sizeof(uint64_t), cudaMemcpyHostToDevice, S->control) == cudaSuccess)
+      cudaStreamSynchronize(S->control);
   }
   if (S->compute) cudaStreamSynchronize(S->compute);
   if (S->control) cudaStreamSynchronize(S->control);
@@ -248,7 +252,9 @@ int malbec_server_destroy(malbec_server* S) {
   if (S->pool) cudaMemPoolDestroy(S->pool);
   if (S->d_ring) cudaFree(S->d_ring);
   if (S->d_ctr) cudaFree(S->d_ctr);
-  if (S->h_block) cudaFreeHost(S->h_block);
+  if (S->d_list) cudaFree(S->d_list);
+  if (S->h_list) cudaFreeHost(S->h_list);
+  if (S->h_done) cudaFreeHost(S->h_done);
   if (S->kernel_done) cudaEventDestroy(S->kernel_done);
   if (S->compute) cudaStreamDestroy(S->compute);
   if (S->control) cudaStreamDestroy(S->control);
@@ -283,8 +289,9 @@ int malbec_poll(malbec_server* S, uint64_t job_id, int* done) {
   std::lock_guard<std::mutex> lk(S->mu);
   auto it = S->jobs.find(job_id);
   if (it == S->jobs.end()) return MALBEC_ENOTFOUND;
-  reap(S);
-  int rc = admit(S);
+  int rc = reap(S);
+  if (rc) return rc;
+  rc = admit(S);
   if (rc) return rc;
   rc = ensure_kernel(S);
   if (rc) return rc;

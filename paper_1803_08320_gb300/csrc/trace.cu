@@ -12,13 +12,16 @@
 // Precision: FP64 (every operation in double), or FP32_MIXED: the state is
 // kept as a compensated pair (hi, lo) of floats, the RHS and RK4 stages run in
 // FP32, and the increments h/6 (k1 + 2k2 + 2k3 + k4) -- with h/6 as a float
-// pair -- are added with TwoSum.  lambda is accumulated in FP64 and the
-// invariants are evaluated in FP64; a step whose start lies inside the FP64
-// zone (near the horizon, near the photon orbits for null rays, or near the
-// polar axis where the BL Christoffel symbols diverge) runs entirely in FP64.  An FP32 step costs one FP64 add (lambda): on a part
-// whose FP64 rate is 1/64 of its FP32 rate every FP64 operation in the bulk
-// path counts.  FP32 steps test termination on the hi words against the
-// thresholds rounded to float.
+// pair -- are added with TwoSum.  lambda is accumulated in FP64 (the h of
+// FP32 steps through an error-free float-pair partial sum flushed every 32
+// steps) and the invariants are evaluated in FP64; a step whose start lies
+// inside the FP64 zone (near the horizon, near the photon orbits for null
+// rays, or near the polar axis where the BL Christoffel symbols diverge) runs
+// entirely in FP64, and the warps of a block exchange rays so that zone steps
+// run with full warps (see the block banks below).  On a part whose FP64 rate
+// is 1/64 of its FP32 rate every FP64 operation in the bulk path counts: an
+// FP32 step has none.  FP32 steps test termination on the hi words against
+// the thresholds rounded to float.
 #include <math.h>
 
 #include "bound.cuh"
@@ -103,40 +106,53 @@ __device__ __forceinline__ void store_nan_samples(const TraceParams& p, uint64_t
 // One FP32 RK4 step on the compensated state (hi, lo).  The stage points are
 // hi + (lo + c h k), so the low words enter the right-hand side; the
 // increments h/6 (k1 + 2k2 + 2k3 + k4) use h/6 as a float pair (h6h, h6l) and
-// are added with TwoSum.  Returns the smallest stage radius.
+// are added with TwoSum.  One copy of the right-hand side (stage loop not
+// unrolled).  Returns the smallest stage radius.
 template <bool kKerr>
 __device__ __forceinline__ float rk4_step_mixed(const BH<float>& bh, float hf, float h6h, float h6l, float hi[8],
                                                 float lo[8]) {
   const float hh = 0.5f * hf;
-  float a1[4], a2[4], a3[4], a4[4], u2[4], u3[4], u4[4];
-  accel<kKerr, float>(bh, hi[1], hi[2], hi[4], hi[5], hi[6], hi[7], a1);
+  float r = hi[1], th = hi[2];
+  float u[4] = {hi[4], hi[5], hi[6], hi[7]};
+  float sx[4], su[4];
+  float rmin = 0.f;
+#pragma unroll 1
+  for (int s = 0; s < 4; ++s) {
+    float acc[4];
+    accel<kKerr, float>(bh, r, th, u[0], u[1], u[2], u[3], acc);
+    if (s == 0) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) u2[j] = hi[4 + j] + fmaf(hh, a1[j], lo[4 + j]);
-  const float r2 = hi[1] + fmaf(hh, hi[5], lo[1]);
-  const float th2 = hi[2] + fmaf(hh, hi[6], lo[2]);
-  accel<kKerr, float>(bh, r2, th2, u2[0], u2[1], u2[2], u2[3], a2);
+      for (int j = 0; j < 4; ++j) {
+        sx[j] = u[j];
+        su[j] = acc[j];
+      }
+    } else {
+      const float w = s == 3 ? 1.f : 2.f;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) u3[j] = hi[4 + j] + fmaf(hh, a2[j], lo[4 + j]);
-  const float r3 = hi[1] + fmaf(hh, u2[1], lo[1]);
-  const float th3 = hi[2] + fmaf(hh, u2[2], lo[2]);
-  accel<kKerr, float>(bh, r3, th3, u3[0], u3[1], u3[2], u3[3], a3);
+      for (int j = 0; j < 4; ++j) {
+        sx[j] = fmaf(w, u[j], sx[j]);
+        su[j] = fmaf(w, acc[j], su[j]);
+      }
+    }
+    if (s < 3) {
+      const float c = s < 2 ? hh : hf;
+      r = hi[1] + fmaf(c, u[1], lo[1]);
+      th = hi[2] + fmaf(c, u[2], lo[2]);
 #pragma unroll
-  for (int j = 0; j < 4; ++j) u4[j] = hi[4 + j] + fmaf(hf, a3[j], lo[4 + j]);
-  const float r4 = hi[1] + fmaf(hf, u3[1], lo[1]);
-  const float th4 = hi[2] + fmaf(hf, u3[2], lo[2]);
-  accel<kKerr, float>(bh, r4, th4, u4[0], u4[1], u4[2], u4[3], a4);
+      for (int j = 0; j < 4; ++j) u[j] = hi[4 + j] + fmaf(c, acc[j], lo[4 + j]);
+      rmin = s == 0 ? r : fminf(rmin, r);
+    }
+  }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const float sx = fmaf(2.f, u2[j] + u3[j], hi[4 + j] + u4[j]);
-    const float su = fmaf(2.f, a2[j] + a3[j], a1[j] + a4[j]);
-    const float dx = h6h * sx;
-    const float dxe = fmaf(h6l, sx, fmaf(h6h, sx, -dx));
-    const float du = h6h * su;
-    const float due = fmaf(h6l, su, fmaf(h6h, su, -du));
+    const float dx = h6h * sx[j];
+    const float dxe = fmaf(h6l, sx[j], fmaf(h6h, sx[j], -dx));
+    const float du = h6h * su[j];
+    const float due = fmaf(h6l, su[j], fmaf(h6h, su[j], -du));
     comp_add(hi[j], lo[j], dx, dxe);
     comp_add(hi[4 + j], lo[4 + j], du, due);
   }
-  return fminf(fminf(r2, r3), r4);
+  return rmin;
 }
 
 __device__ __forceinline__ void step_consts(double dl, double dl_scale, double r_esc, float& h_fix, float& h6h,
@@ -174,13 +190,109 @@ __device__ __forceinline__ void split_pair(const double y[8], float hi[8], float
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32_MIXED: exchange of rays between the warps of a block.
+//
+// The FP64 unit costs the same per warp instruction whatever the number of
+// active lanes, and few rays of a warp are in the FP64 zone at a time, so
+// zone steps taken where the rays happen to be run with a handful of lanes.
+// One warp of each block (the zone warp) therefore collects them: the other
+// warps hand a zone ray that would otherwise wait (fewer than zone_batch
+// zone lanes in the warp) to the block's zone bank, and take rays the zone
+// warp has handed back to the FP32 bank into idle lanes before they claim new
+// ones; the zone warp fills its idle lanes from the zone bank and hands its
+// FP32 rays to the FP32 bank while zone rays wait.  A ray carries its whole
+// state; where it runs changes when its steps run, never their arithmetic.
+// Every bank operation holds the block's lock (a bounded try: a warp that
+// does not get it simply skips the exchange this time).
+constexpr int kBankSlots = 32;
+
+struct RayBank {
+  float hi[8][kBankSlots], lo[8][kBankSlots];
+  double lam[kBankSlots], M[kBankSlots], a[kBankSlots], dl[kBankSlots], dls[kBankSlots], r_esc[kBankSlots],
+      r_cap[kBankSlots];
+  unsigned long long id[kBankSlots];
+  uint32_t job[kBankSlots], nst[kBankSlots], cap[kBankSlots];
+  float r_zone[kBankSlots], pole[kBankSlots], lam_h[kBankSlots], lam_l[kBankSlots];
+  uint32_t lam_fix[kBankSlots];
+};
+
+struct BlockBanks {
+  RayBank zone, fp32;
+  int n_zone, n_fp32;  // records [0, n) of each bank are valid
+  int lock;
+  int open;            // the zone warp still takes zone rays
+  int alive;           // warps of the block other than the zone warp still running
+};
+struct NoBanks {
+  int unused;
+};
+template <bool kMixed>
+struct BanksFor {
+  using type = NoBanks;
+};
+template <>
+struct BanksFor<true> {
+  using type = BlockBanks;
+};
+
+// Lane 0 only: take the block's lock, at most 64 tries.
+__device__ __forceinline__ bool bank_try_lock(int* lock) {
+  for (int k = 0; k < 64; ++k) {
+    if (atomicCAS(lock, 0, 1) == 0) {
+      __threadfence_block();
+      return true;
+    }
+    __nanosleep(32);
+  }
+  return false;
+}
+__device__ __forceinline__ void bank_unlock(int* lock) {
+  __threadfence_block();
+  atomicExch(lock, 0);
+}
+// The whole warp: lane 0 tries the lock, every lane learns the outcome; the
+// warp barrier orders lane 0's acquire before the other lanes' accesses.
+__device__ __forceinline__ bool warp_lock(int* lock, int lane) {
+  int got = 0;
+  if (lane == 0) got = bank_try_lock(lock);
+  got = __shfl_sync(kFull, got, 0);
+  __syncwarp();
+  return got != 0;
+}
+__device__ __forceinline__ void warp_unlock(int* lock, int lane) {
+  __syncwarp();
+  if (lane == 0) bank_unlock(lock);
+  __syncwarp();
+}
+__device__ __forceinline__ int shared_load(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+__device__ __forceinline__ void shared_store(int* p, int v) { *reinterpret_cast<volatile int*>(p) = v; }
+// Lane 0's view of a bank counter, for every lane (a warp-uniform hint).
+__device__ __forceinline__ int warp_peek(const int* p, int lane) {
+  int v = 0;
+  if (lane == 0) v = shared_load(p);
+  return __shfl_sync(kFull, v, 0);
+}
+
+__device__ __forceinline__ unsigned nsmid() {
+  unsigned n;
+  asm("mov.u32 %0, %%nsmid;" : "=r"(n));
+  return n;
+}
+
+// Longest wait of a zone warp for the other warps of its block: after it the
+// zone warp closes its bank and leaves (the others then run their zone steps
+// in place).
+constexpr unsigned long long kZoneWarpWaitNs = 600ull * 1000000000ull;
+
 // Launch bounds: at most kMaxTPB threads, one block per SM guaranteed.  The
 // kernel runs one to eight warps per SM (see choose_shape), so the register
 // budget is not the occupancy limit; without the minimum-blocks argument the
 // compiler capped some instantiations (the request-loop ones) at 128
 // registers and spilled.
-template <bool kKerr, bool kMixed, int kSrc, int kSink>
+template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks>
 __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) {
+  static_assert(!kBanks || kMixed, "block banks exist for FP32_MIXED only");
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const float k6h = (float)(1.0 / 6.0), k6l = (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0));
@@ -204,18 +316,183 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
   BH<double> bh64 = make_bh<double>(M, p.a);
   BH<float> bh32 = make_bh<float>(M, p.a);
   int zone_waited = 0;
-  unsigned long long idle_since = 0ull;
+  unsigned long long idle_since = 0ull, nap_since = 0ull;
   int claim_backoff = 0;
   bool active = false, drained = false;
+  // FP32 steps add their h to a float pair (TwoSum), flushed into the FP64
+  // lambda after every 32nd step of the ray, before an FP64 step and at the
+  // end (a fixed step only counts): no FP64 operation in the FP32 bulk step,
+  // and the flush points depend on the ray's own steps alone.
+  float lam_h = 0.f, lam_l = 0.f;
+  uint32_t lam_fix = 0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     y[c] = 0.0;
     hi[c] = 0.f;
     lo[c] = 0.f;
   }
+  auto flush_lam = [&]() {
+    lam += ((double)lam_h + (double)lam_l) + (double)lam_fix * dl;
+    lam_h = lam_l = 0.f;
+    lam_fix = 0;
+  };
+
+  // Block banks (FP32_MIXED with at least two warps per block).
+  __shared__ typename BanksFor<kBanks>::type banks;
+  const int n_warps = (int)(blockDim.x >> 5);
+  const bool use_banks = kBanks && n_warps >= 2;
+  const int zone_warp_index = use_banks ? (int)((blockIdx.x / nsmid()) % (unsigned)n_warps) : -1;
+  const bool zone_warp = (int)(threadIdx.x >> 5) == zone_warp_index;
+  if constexpr (kBanks) {
+    if (threadIdx.x == 0) {
+      banks.n_zone = 0;
+      banks.n_fp32 = 0;
+      banks.lock = 0;
+      banks.open = use_banks ? 1 : 0;
+      banks.alive = n_warps - 1;
+    }
+    __syncthreads();
+  }
+  // Move this lane's ray into / out of bank slot s (FP32_MIXED only).
+  auto save_ray = [&](RayBank& b, int s) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      b.hi[c][s] = hi[c];
+      b.lo[c][s] = lo[c];
+    }
+    b.lam[s] = lam;
+    b.M[s] = M;
+    b.a[s] = a;
+    b.dl[s] = dl;
+    b.dls[s] = dl_scale;
+    b.r_esc[s] = r_esc;
+    b.r_cap[s] = r_cap;
+    b.id[s] = id;
+    b.job[s] = job;
+    b.nst[s] = nst;
+    b.cap[s] = cap;
+    b.r_zone[s] = r_zone_f;
+    b.pole[s] = pole_lane;
+    b.lam_h[s] = lam_h;
+    b.lam_l[s] = lam_l;
+    b.lam_fix[s] = lam_fix;
+    active = false;
+  };
+  auto load_ray = [&](const RayBank& b, int s) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      hi[c] = b.hi[c][s];
+      lo[c] = b.lo[c][s];
+    }
+    lam = b.lam[s];
+    M = b.M[s];
+    a = b.a[s];
+    dl = b.dl[s];
+    dl_scale = b.dls[s];
+    r_esc = b.r_esc[s];
+    r_cap = b.r_cap[s];
+    id = b.id[s];
+    job = b.job[s];
+    nst = b.nst[s];
+    cap = b.cap[s];
+    r_zone_f = b.r_zone[s];
+    pole_lane = b.pole[s];
+    step_consts(dl, dl_scale, r_esc, h_fix, h6_fix_h, h6_fix_l, scale_f, r_esc_f);
+    bh64 = make_bh<double>(M, a);
+    bh32 = make_bh<float>(M, a);
+    r_cap_f = (float)r_cap;
+    zone_waited = 0;
+    lam_h = b.lam_h[s];
+    lam_l = b.lam_l[s];
+    lam_fix = b.lam_fix[s];
+    active = true;
+  };
+  auto zone_test = [&]() -> bool {
+    return active && nst < cap && (hi[1] < r_zone_f || fabsf(__sinf(hi[2])) < pole_lane);
+  };
+  // A warp with no ray left asks to leave (banks in use).  The zone warp
+  // leaves once its bank is empty and every other warp of the block has left
+  // (it naps meanwhile, at most kZoneWarpWaitNs, then closes its bank); the
+  // others leave once the FP32 bank is empty.  Returns false to loop again.
+  auto leave_block_banks = [&](auto& bk) -> bool {
+    if (!warp_lock(&bk.lock, lane)) return false;
+    int leave = 0;
+    if (lane == 0) {
+      if (zone_warp) {
+        const int nz = shared_load(&bk.n_zone), alive = shared_load(&bk.alive);
+        if (nz == 0) {
+          const unsigned long long now = global_ns();
+          if (nap_since == 0ull) nap_since = now;
+          if (alive == 0 || now - nap_since > kZoneWarpWaitNs) {
+            shared_store(&bk.open, 0);
+            leave = 1;
+          }
+        }
+      } else if (shared_load(&bk.n_fp32) == 0) {
+        shared_store(&bk.alive, shared_load(&bk.alive) - 1);
+        leave = 1;
+      }
+    }
+    leave = __shfl_sync(kFull, leave, 0);
+    warp_unlock(&bk.lock, lane);
+    if (!leave && zone_warp) __nanosleep(1000);
+    return leave != 0;
+  };
 
   while (true) {
-    const unsigned act = __ballot_sync(kFull, active);
+    unsigned act = __ballot_sync(kFull, active);
+    if constexpr (kBanks) {
+      if (use_banks) {
+        if (zone_warp) {
+          // ---- zone warp: take waiting zone rays into idle lanes, handing
+          // FP32 rays to the FP32 bank to make room for them
+          if (warp_peek(&banks.n_zone, lane) > 0 && warp_lock(&banks.lock, lane)) {
+            const unsigned cand = __ballot_sync(kFull, active && !zone_test());
+            int nz = 0, nf = 0, alive = 0;
+            if (lane == 0) {
+              nz = shared_load(&banks.n_zone);
+              nf = shared_load(&banks.n_fp32);
+              alive = shared_load(&banks.alive);
+            }
+            nz = __shfl_sync(kFull, nz, 0);
+            nf = __shfl_sync(kFull, nf, 0);
+            alive = __shfl_sync(kFull, alive, 0);
+            const int n_idle = 32 - __popc(act);
+            unsigned evict = 0u;
+            if (nz > n_idle && alive > 0) {
+              int k = min(nz - n_idle, __popc(cand));
+              k = min(k, kBankSlots - nf);
+              const unsigned rank = __popc(cand & lt_mask);
+              evict = __ballot_sync(kFull, ((cand >> lane) & 1u) && (int)rank < k);
+              if ((evict >> lane) & 1u) save_ray(banks.fp32, nf + (int)rank);
+              nf += __popc(evict);
+            }
+            const unsigned free_lanes = ~act | evict;
+            const int take = min(nz, __popc(free_lanes));
+            const unsigned frank = __popc(free_lanes & lt_mask);
+            if (((free_lanes >> lane) & 1u) && (int)frank < take) load_ray(banks.zone, nz - 1 - (int)frank);
+            if (lane == 0) {
+              shared_store(&banks.n_zone, nz - take);
+              shared_store(&banks.n_fp32, nf);
+            }
+            warp_unlock(&banks.lock, lane);
+            act = __ballot_sync(kFull, active);
+          }
+        } else if (act != kFull && warp_peek(&banks.n_fp32, lane) > 0 && warp_lock(&banks.lock, lane)) {
+          // ---- other warps: rays the zone warp handed back go first
+          int nf = 0;
+          if (lane == 0) nf = shared_load(&banks.n_fp32);
+          nf = __shfl_sync(kFull, nf, 0);
+          const unsigned free_lanes = ~act;
+          const int take = min(nf, __popc(free_lanes));
+          const unsigned frank = __popc(free_lanes & lt_mask);
+          if (((free_lanes >> lane) & 1u) && (int)frank < take) load_ray(banks.fp32, nf - 1 - (int)frank);
+          if (lane == 0) shared_store(&banks.n_fp32, nf - take);
+          warp_unlock(&banks.lock, lane);
+          act = __ballot_sync(kFull, active);
+        }
+      }
+    }
     const int idle = 32 - __popc(act);
     if (kSrc == kSrcServe && claim_backoff > 0) --claim_backoff;
     if (!drained && idle > 0 && (idle >= p.refill_min || act == 0) && (act == 0 || claim_backoff == 0)) {
@@ -233,43 +510,56 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         }
       } else if (kSrc == kSrcServe) {
         // ---- claim rays from the active jobs, in the order the host
-        // publishes (smallest first), until every idle lane has one or no
-        // job has rays left; no new claims once the host asked to stop
+        // publishes (smallest first): the warp reads 32 entries of the list
+        // at a time and lane 0 claims from the first job that has rays left,
+        // until every idle lane has a ray or no listed job has rays left; no
+        // new claims once the host asked to stop.  A job whose last rays went
+        // to another warp meanwhile is seen exhausted on the next look.
         unsigned need = ~act;
-        while (need != 0u) {
-          const int cnt = __popc(need);
-          int slot = -1;
-          unsigned long long base = 0, nj = 0;
-          if (lane == 0 && *p.stop_flag == 0u) {
-            uint32_t na = *p.active_count;
-            if (na > p.max_active) na = p.max_active;
-            for (uint32_t i = 0; i < na; ++i) {
-              const uint64_t jid = p.active_ids[i];
-              if (jid == 0) continue;
-              const uint32_t s = (uint32_t)(jid % p.n_jobs);
-              if (__ldcg(reinterpret_cast<const unsigned long long*>(&p.jobs[s].job_id)) != jid) continue;
-              const unsigned long long ns = __ldcg(reinterpret_cast<const unsigned long long*>(&p.jobs[s].n));
-              if (*reinterpret_cast<volatile unsigned long long*>(&p.job_ctr[s].next) >= ns) continue;
-              const unsigned long long b = atomicAdd(&p.job_ctr[s].next, (unsigned long long)cnt);
-              if (b < ns) {
-                slot = (int)s;
-                base = b;
-                nj = ns;
-                break;
+        uint32_t na = 0, stop = 0;
+        if (lane == 0) {
+          na = *p.active_count;
+          stop = *p.stop_flag;
+        }
+        na = __shfl_sync(kFull, na, 0);
+        stop = __shfl_sync(kFull, stop, 0);
+        if (na > p.max_active) na = p.max_active;
+        uint32_t i0 = 0;
+        while (need != 0u && stop == 0u && i0 < na) {
+          const uint32_t i = i0 + (uint32_t)lane;
+          uint32_t s = 0;
+          unsigned long long ns = 0;
+          bool avail = false;
+          if (i < na) {
+            const uint64_t jid = p.active_ids[i];
+            if (jid != 0) {
+              s = (uint32_t)(jid % p.n_jobs);
+              if (__ldcg(reinterpret_cast<const unsigned long long*>(&p.jobs[s].job_id)) == jid) {
+                ns = __ldcg(reinterpret_cast<const unsigned long long*>(&p.jobs[s].n));
+                avail = *reinterpret_cast<volatile unsigned long long*>(&p.job_ctr[s].next) < ns;
               }
             }
           }
-          slot = __shfl_sync(kFull, slot, 0);
-          base = __shfl_sync(kFull, base, 0);
-          nj = __shfl_sync(kFull, nj, 0);
-          if (slot < 0) break;
-          const unsigned long long avail = nj - base < (unsigned long long)cnt ? nj - base : (unsigned long long)cnt;
+          const unsigned m = __ballot_sync(kFull, avail);
+          if (m == 0u) {
+            i0 += 32u;
+            continue;
+          }
+          const int first = __ffs(m) - 1;
+          s = __shfl_sync(kFull, s, first);
+          ns = __shfl_sync(kFull, ns, first);
+          const int cnt = __popc(need);
+          unsigned long long b = 0;
+          if (lane == 0) b = atomicAdd(&p.job_ctr[s].next, (unsigned long long)cnt);
+          b = __shfl_sync(kFull, b, 0);
+          if (b >= ns) continue;
+          const unsigned long long n_take = ns - b < (unsigned long long)cnt ? ns - b : (unsigned long long)cnt;
           const bool mine = (need >> lane) & 1u;
           const unsigned rank = __popc(need & lt_mask);
-          const bool take_it = mine && rank < avail;
+          const bool take_it = mine && rank < n_take;
           if (take_it) {
-            job = (uint32_t)slot;
-            id = base + rank;
+            job = s;
+            id = b + rank;
             got = true;
           }
           need &= ~__ballot_sync(kFull, take_it);
@@ -317,7 +607,13 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
             if (idle_since == 0ull) idle_since = now;
             quit = *p.stop_flag != 0u || now - idle_since > p.idle_ns;
           }
-          if (__shfl_sync(kFull, quit, 0)) break;
+          if (__shfl_sync(kFull, quit, 0)) {
+            if constexpr (kBanks) {
+              if (!use_banks || leave_block_banks(banks)) break;
+            } else {
+              break;
+            }
+          }
           __nanosleep(2000);
           continue;
         }
@@ -358,6 +654,8 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         const double rp = dev_r_plus(M, a);
         r_cap = (1.0 + eps_hor) * rp;
         lam = 0.0;
+        lam_h = lam_l = 0.f;
+        lam_fix = 0;
         nst = 0;
         zone_waited = 0;
         const bool from_jobs = kSrc == kSrcJobs || kSrc == kSrcServe;
@@ -390,17 +688,47 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
       }
       continue;
     }
-    if (act == 0) break;  // queue drained and no lane busy
+    if (act == 0) {  // queue drained and no lane busy
+      if constexpr (kBanks) {
+        if (!use_banks || leave_block_banks(banks)) break;
+        continue;
+      } else {
+        break;
+      }
+    }
+    if (zone_warp) nap_since = 0ull;
     // FP32_MIXED: one warp step is either an FP64-zone step (for every lane
     // that wants one) or an FP32 step (for the others), never both.  FP64
     // steps are deferred until zone_batch lanes want one, no lane wants an
     // FP32 step, or a waiting lane has sat out zone_wait warp steps.  Only the
     // timing of a ray's steps changes, never their arithmetic.
     bool in_zone = false, take = true;
-    if (kMixed) {
-      in_zone = active && nst < cap && (hi[1] < r_zone_f || fabsf(__sinf(hi[2])) < pole_lane);
+    if constexpr (kMixed) {
+      in_zone = zone_test();
+      unsigned m64 = __ballot_sync(kFull, in_zone);
+      if constexpr (kBanks) {
+        // too few zone rays here for an FP64 step: hand them to the zone warp
+        if (use_banks && !zone_warp && m64 != 0u && __popc(m64) < p.zone_batch && warp_peek(&banks.open, lane) != 0 &&
+            warp_peek(&banks.n_zone, lane) < kBankSlots && warp_lock(&banks.lock, lane)) {
+          int nz = 0, open = 0;
+          if (lane == 0) {
+            nz = shared_load(&banks.n_zone);
+            open = shared_load(&banks.open);
+          }
+          nz = __shfl_sync(kFull, nz, 0);
+          open = __shfl_sync(kFull, open, 0);
+          const int k = open ? min(__popc(m64), kBankSlots - nz) : 0;
+          const unsigned rank = __popc(m64 & lt_mask);
+          if (in_zone && (int)rank < k) {
+            save_ray(banks.zone, nz + (int)rank);
+            in_zone = false;
+          }
+          if (lane == 0) shared_store(&banks.n_zone, nz + k);
+          warp_unlock(&banks.lock, lane);
+          m64 = __ballot_sync(kFull, in_zone);
+        }
+      }
       const bool want32 = active && nst < cap && !in_zone;
-      const unsigned m64 = __ballot_sync(kFull, in_zone);
       const unsigned m32 = __ballot_sync(kFull, want32);
       const unsigned urgent = __ballot_sync(kFull, in_zone && zone_waited >= p.zone_wait);
       const bool do64 = m32 == 0 || urgent != 0 || __popc(m64) >= p.zone_batch;
@@ -426,7 +754,8 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
 #pragma unroll
         for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
         const double h = dl_scale > 0.0 ? dl_scale * y[1] : dl;
-        const double rmin = rk4_step<kKerr, double>(bh64, h, y);
+        const double rmin = rk4_step<kKerr, double, true>(bh64, h, y);
+        flush_lam();
         lam += h;
         split_pair(y, hi, lo);
         captured = (y[1] <= r_cap) | (rmin <= r_cap);
@@ -434,17 +763,21 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         finite = finite8(y);
       } else {
         float hf, h6h, h6l;
-        if (dl_scale > 0.0) {
+        if (scale_f > 0.f) {
           hf = scale_f * hi[1];
           h6h = hf * k6h;
           h6l = fmaf(hf, k6l, fmaf(hf, k6h, -h6h));
-          lam += (double)hf;
+          float s, e;
+          two_sum(lam_h, hf, s, e);
+          lam_h = s;
+          lam_l += e;
         } else {
           hf = h_fix;
           h6h = h6_fix_h;
           h6l = h6_fix_l;
-          lam += dl;
+          ++lam_fix;
         }
+        if ((nst & 31u) == 31u) flush_lam();
         const float rmin = rk4_step_mixed<kKerr>(bh32, hf, h6h, h6l, hi, lo);
         captured = (hi[1] <= r_cap_f) | (rmin <= r_cap_f);
         escaped = hi[1] >= r_esc_f;
@@ -467,6 +800,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
 
     if (fate != 0) {
       if (kMixed) {
+        flush_lam();
 #pragma unroll
         for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
       }
@@ -518,14 +852,20 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
   }
 }
 
-template <bool kKerr, bool kMixed, int kSrc, int kSink>
+template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks>
 const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&trace_kernel<kKerr, kMixed, kSrc, kSink>);
+  return reinterpret_cast<const void*>(&trace_kernel<kKerr, kMixed, kSrc, kSink, kBanks>);
 }
 
-const void* pick(bool kerr, bool mixed, Source src, Sink sink) {
-#define MALBEC_PICK(K, X, S, T) \
-  if (kerr == K && mixed == X && src == S && sink == T) return kernel_ptr<K, X, S, T>();
+// The kernel for a launch; FP32_MIXED kernels come with and without the
+// block ray exchange (two instantiations, so that the one without carries
+// none of its code).
+const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks) {
+#define MALBEC_PICK(K, X, S, T)                                                        \
+  if (kerr == K && mixed == X && src == S && sink == T) {                              \
+    if (X && banks) return kernel_ptr<K, X, S, T, X>();                               \
+    return kernel_ptr<K, X, S, T, false>();                                            \
+  }
   MALBEC_PICK(true, false, kSrcJobs, kSinkJobs)
   MALBEC_PICK(true, true, kSrcJobs, kSinkJobs)
   MALBEC_PICK(true, false, kSrcServe, kSinkJobs)
@@ -549,7 +889,7 @@ const void* pick(bool kerr, bool mixed, Source src, Sink sink) {
 }  // namespace
 
 int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, int threads_per_block) {
-  const void* k = pick(kerr, mixed, src, sink);
+  const void* k = pick(kerr, mixed, src, sink, mixed);  // the larger of the two kernels
   if (!k) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads_per_block, 0) != cudaSuccess) return 0;
@@ -558,12 +898,22 @@ int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, int th
 
 cudaError_t launch_trace(const TraceParams& p, bool kerr, bool mixed, Source src, Sink sink,
                          const LaunchShape& shape, cudaStream_t stream) {
-  const void* k = pick(kerr, mixed, src, sink);
+  // automatic block exchange: on for job tables, the request loop and state
+  // arrays (mixes of long timelike orbits spend many steps in the polar FP64
+  // zone), off for whole-image cameras (too few steps in their zone to pay
+  // for a zone warp)
+  const int exchange = p.exchange >= 0 ? p.exchange : (src == kSrcCamera ? 0 : 1);
+  const void* k = pick(kerr, mixed, src, sink, mixed && exchange == 1);
   if (!k) return cudaErrorInvalidValue;
+  // automatic FP64-zone batch: 8 lanes with the exchange (a warp hands fewer
+  // zone rays to the zone warp), a full warp without it (a zone step then
+  // waits for 32 lanes, zone_wait warp steps, or a warp with no FP32 lane)
+  TraceParams q = p;
+  if (q.zone_batch < 0) q.zone_batch = exchange == 1 ? 8 : 32;
   if (shape.threads_per_block <= 0 || shape.threads_per_block > kMaxTPB ||
       shape.threads_per_block % 32 != 0 || shape.blocks <= 0)
     return cudaErrorInvalidConfiguration;
-  void* args[] = {const_cast<TraceParams*>(&p)};
+  void* args[] = {&q};
   return cudaLaunchKernel(k, dim3(shape.blocks), dim3(shape.threads_per_block), args, 0, stream);
 }
 

@@ -64,7 +64,7 @@ class Bundle(ctypes.Structure):
 
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("threads_per_block", _U32), ("blocks_per_sm", _U32), ("refill_min", _U32),
-                ("zone_batch", _U32), ("zone_wait", _U32)]
+                ("zone_batch", _U32), ("zone_wait", _U32), ("exchange", _U32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -522,14 +522,14 @@ def set_mixed_zone(horizon_factor=None, photon_margin=None, pole_sin=None, reset
     return z
 
 
-def set_launch_config(threads_per_block=0, blocks_per_sm=0, refill_min=0, zone_batch=0, zone_wait=0,
+def set_launch_config(threads_per_block=0, blocks_per_sm=0, refill_min=0, zone_batch=0, zone_wait=0, exchange=0,
                       reset=False) -> LaunchConfig:
     """Process-wide launch configuration of the trace kernels (0 = automatic)."""
     if reset:
         _check(lib().malbec_set_launch_config(None), "malbec_set_launch_config")
     else:
         c = LaunchConfig(int(threads_per_block), int(blocks_per_sm), int(refill_min), int(zone_batch),
-                         int(zone_wait))
+                         int(zone_wait), int(exchange))
         _check(lib().malbec_set_launch_config(ctypes.byref(c)), "malbec_set_launch_config")
     return get_launch_config()
 

@@ -163,10 +163,11 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
 def test_launch_config_setting(mb):
     c = mb.get_launch_config()
     assert c.as_dict() == {"threads_per_block": 0, "blocks_per_sm": 0, "refill_min": 0, "zone_batch": 0,
-                           "zone_wait": 0}
-    c2 = mb.set_launch_config(threads_per_block=64, blocks_per_sm=2, refill_min=4, zone_batch=8, zone_wait=32)
+                           "zone_wait": 0, "exchange": 0}
+    c2 = mb.set_launch_config(threads_per_block=64, blocks_per_sm=2, refill_min=4, zone_batch=8, zone_wait=32,
+                              exchange=2)
     assert c2.as_dict() == {"threads_per_block": 64, "blocks_per_sm": 2, "refill_min": 4, "zone_batch": 8,
-                            "zone_wait": 32}
+                            "zone_wait": 32, "exchange": 2}
     bad = mb.LaunchConfig(48, 0, 0, 0, 0)
     assert mb.lib().malbec_set_launch_config(ctypes.byref(bad)) == mb.EINVAL
     bad = mb.LaunchConfig(512, 0, 0, 0, 0)
