@@ -344,9 +344,11 @@ int malbec_plan_destroy(malbec_plan* plan);
  *    (max_active) and its output fits in hbm_budget minus the bytes held by
  *    admitted, not yet released jobs; otherwise it waits in a FIFO of at most
  *    max_pending jobs (malbec_submit returns MALBEC_EBUSY when that is full).
- *  - The kernel leaves by itself after idle_timeout_s without work (a bounded
- *    wait on the device clock), and is relaunched by the next submit or poll
- *    that finds work.  Job slots form a ring of 65536 descriptors.
+ *  - The kernel leaves by itself once every one of its warps has been
+ *    without work for idle_timeout_s (measured on the device clock; the
+ *    whole grid leaves at once, so a job never runs on a partly exited
+ *    kernel), and is relaunched by the next submit or poll that finds work.
+ *    Job slots form a ring of 65536 descriptors.
  *  - Completion is signalled by the device in mapped host memory; polling
  *    never synchronises the device.
  * All calls are thread-safe.  malbec_server_destroy waits for running rays

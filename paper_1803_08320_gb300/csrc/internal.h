@@ -92,6 +92,10 @@ struct TraceParams {
   volatile uint64_t* done_flags;
   uint32_t max_active;
   uint64_t idle_ns;
+  // request loop: warps that have been idle for idle_ns park here (low 32
+  // bits count them); the kernel leaves only when every warp is parked (the
+  // warp that sees it sets bit 63, closing), never part of it
+  unsigned long long* park;
   // launch shape
   int refill_min;  // refill when at least this many lanes of a warp are idle
 };

@@ -14,8 +14,10 @@
 //    worst hide a job for one look;
 //  - the last ray of a job writes the job id into done_flags[slot] (mapped
 //    host memory) after a system-scope fence;
-//  - the stop flag ends claiming; the kernel also leaves by itself after
-//    idle_timeout_s without work (bounded wait on %globaltimer).
+//  - the stop flag ends claiming; the kernel also leaves by itself when all
+//    its warps have been idle for idle_timeout_s (each idle warp parks in a
+//    device word; the warp that sees every warp parked closes the kernel and
+//    all leave, so a job is never left to a partly exited grid).
 #include <math.h>
 #include <string.h>
 
@@ -67,6 +69,7 @@ struct malbec_server {
   // done flags, one per ring slot, in mapped host memory
   uint64_t* h_done = nullptr;
   uint64_t* d_done = nullptr;  // device alias of h_done
+  unsigned long long* d_park = nullptr;  // park word of the running kernel
   uint64_t next_id = 1;
   std::unordered_map<uint64_t, Job> jobs;
   std::deque<uint64_t> pending;
@@ -107,6 +110,7 @@ int launch_kernel(malbec_server* S) {
   p.active_count = reinterpret_cast<const volatile uint32_t*>(S->d_list);
   p.stop_flag = reinterpret_cast<const volatile uint32_t*>(S->d_list) + 1;
   p.done_flags = reinterpret_cast<volatile uint64_t*>(S->d_done);
+  p.park = S->d_park;
   p.max_active = S->cfg.max_active;
   p.idle_ns = (uint64_t)(S->cfg.idle_timeout_s * 1e9);
   fill_zone(p);
@@ -116,7 +120,8 @@ int launch_kernel(malbec_server* S) {
   int rc = choose_shape(true, mixed, kSrcServe, kSinkJobs, p.n, &shape, &refill_min);
   if (rc) return rc;
   p.refill_min = 1;
-  cudaError_t e = launch_trace(p, true, mixed, kSrcServe, kSinkJobs, shape, S->compute);
+  cudaError_t e = cudaMemsetAsync(S->d_park, 0, sizeof(unsigned long long), S->compute);
+  if (e == cudaSuccess) e = launch_trace(p, true, mixed, kSrcServe, kSinkJobs, shape, S->compute);
   if (e == cudaSuccess) e = cudaEventRecord(S->kernel_done, S->compute);
   if (e != cudaSuccess) return set_cuda_error(e);
   S->launched = true;
@@ -218,6 +223,7 @@ int malbec_server_create(const malbec_server_config* cfg, malbec_server** server
   if (e == cudaSuccess) e = cudaMemset(S->d_ctr, 0, (size_t)kRing * sizeof(JobCounter));
   const size_t list_bytes = (size_t)(cfg->max_active + 1) * sizeof(uint64_t);
   if (e == cudaSuccess) e = cudaMalloc(&S->d_list, list_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_park, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(S->d_list, 0, list_bytes);
   if (e == cudaSuccess) e = cudaHostAlloc(&S->h_list, list_bytes, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaHostAlloc(&S->h_done, (size_t)kRing * sizeof(uint64_t), cudaHostAllocMapped);
@@ -253,6 +259,7 @@ int malbec_server_destroy(malbec_server* S) {
   if (S->d_ring) cudaFree(S->d_ring);
   if (S->d_ctr) cudaFree(S->d_ctr);
   if (S->d_list) cudaFree(S->d_list);
+  if (S->d_park) cudaFree(S->d_park);
   if (S->h_list) cudaFreeHost(S->h_list);
   if (S->h_done) cudaFreeHost(S->h_done);
   if (S->kernel_done) cudaEventDestroy(S->kernel_done);

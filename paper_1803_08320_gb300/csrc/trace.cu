@@ -274,6 +274,17 @@ __device__ __forceinline__ int warp_peek(const int* p, int lane) {
   return __shfl_sync(kFull, v, 0);
 }
 
+// Request loop: a parked warp that found work leaves the park count, unless
+// the kernel is closing (lane 0; bounded number of tries).
+__device__ __forceinline__ bool serve_unpark(unsigned long long* park) {
+  for (int t = 0; t < 64; ++t) {
+    const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(park);
+    if (w >> 63) return false;
+    if (atomicCAS(park, w, w - 1ull) == w) return true;
+  }
+  return false;
+}
+
 __device__ __forceinline__ unsigned nsmid() {
   unsigned n;
   asm("mov.u32 %0, %%nsmid;" : "=r"(n));
@@ -318,7 +329,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
   int zone_waited = 0;
   unsigned long long idle_since = 0ull, nap_since = 0ull;
   int claim_backoff = 0;
-  bool active = false, drained = false;
+  bool active = false, drained = false, parked = false;
   // FP32 steps add their h to a float pair (TwoSum), flushed into the FP64
   // lambda after every 32nd step of the ray, before an FP64 step and at the
   // end (a fixed step only counts): no FP64 operation in the FP32 bulk step,
@@ -545,6 +556,12 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
             i0 += 32u;
             continue;
           }
+          if (parked) {
+            int ok = 0;
+            if (lane == 0) ok = serve_unpark(p.park);
+            if (__shfl_sync(kFull, ok, 0) == 0) break;  // closing: claim nothing
+            parked = false;
+          }
           const int first = __ffs(m) - 1;
           s = __shfl_sync(kFull, s, first);
           ns = __shfl_sync(kFull, ns, first);
@@ -598,15 +615,35 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         }
       }
       if (kSrc == kSrcServe) {
-        // no ray for any lane of this warp: nap, and leave after idle_ns of
-        // idleness or once the host asks to stop (bounded wait; lane 0 decides)
+        // no ray for any lane of this warp: nap.  After idle_ns of idleness
+        // the warp parks; the kernel leaves once every warp is parked (all
+        // at once: the first to see it closes, and a parked warp that finds
+        // work unparks before it claims), or when the host asks to stop.
+        // Lane 0 decides; every wait is a bounded nap of the loop.
         if (act == 0 && __ballot_sync(kFull, got) == 0u) {
           bool quit = false;
           if (lane == 0) {
             const unsigned long long now = global_ns();
             if (idle_since == 0ull) idle_since = now;
-            quit = *p.stop_flag != 0u || now - idle_since > p.idle_ns;
+            volatile unsigned long long* pk = p.park;
+            if ((*pk >> 63) != 0ull || *p.stop_flag != 0u) {
+              quit = true;
+            } else {
+              if (!parked && now - idle_since > p.idle_ns) {
+                atomicAdd(p.park, 1ull);
+                parked = true;
+              }
+              if (parked) {
+                const unsigned long long w = *pk;
+                const unsigned long long total = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+                if ((w >> 63) != 0ull)
+                  quit = true;
+                else if ((w & 0xffffffffull) == total && atomicCAS(p.park, w, w | (1ull << 63)) == w)
+                  quit = true;
+              }
+            }
           }
+          parked = __shfl_sync(kFull, parked, 0);
           if (__shfl_sync(kFull, quit, 0)) {
             if constexpr (kBanks) {
               if (!use_banks || leave_block_banks(banks)) break;
