@@ -301,7 +301,8 @@ def run_bundles_case(mb, torch, stream, flush, count: int, precision: str, K: in
             for b in bundles:
                 mb.trace_bundles([b], precision, stream=stream)
 
-        per_bundle()
+        # the kernel is already warm: one small launch before the timed passes
+        mb.trace_bundles([min(bundles, key=lambda b: b.n)], precision, stream=stream)
         stream.synchronize()
         t_each = timed(per_bundle, K)
         steps_each = steps_of(views)

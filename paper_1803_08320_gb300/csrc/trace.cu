@@ -737,8 +737,9 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
     // FP32_MIXED: one warp step is either an FP64-zone step (for every lane
     // that wants one) or an FP32 step (for the others), never both.  FP64
     // steps are deferred until zone_batch lanes want one, no lane wants an
-    // FP32 step, or a waiting lane has sat out zone_wait warp steps.  Only the
-    // timing of a ray's steps changes, never their arithmetic.
+    // FP32 step, a waiting lane has sat out zone_wait warp steps, or (queue
+    // drained) zone rays are a quarter of the live rays.  Only the timing of
+    // a ray's steps changes, never their arithmetic.
     bool in_zone = false, take = true;
     if constexpr (kMixed) {
       in_zone = zone_test();
@@ -768,7 +769,10 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
       const bool want32 = active && nst < cap && !in_zone;
       const unsigned m32 = __ballot_sync(kFull, want32);
       const unsigned urgent = __ballot_sync(kFull, in_zone && zone_waited >= p.zone_wait);
-      const bool do64 = m32 == 0 || urgent != 0 || __popc(m64) >= p.zone_batch;
+      // once this warp's queue is drained no new ray will join a batch:
+      // step the zone rays when they are a quarter of the warp's live rays
+      const bool do64 = m32 == 0 || urgent != 0 || __popc(m64) >= p.zone_batch ||
+                        (drained && 4 * __popc(m64) >= __popc(m64 | m32));
       take = do64 ? in_zone : want32;
       if (in_zone) zone_waited = do64 ? 0 : zone_waited + 1;
     }
