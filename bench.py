@@ -119,6 +119,23 @@ def camera_setup():
     return cw, cam
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (Linux /proc/cpuinfo; 'unknown' elsewhere)."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
 def cpu_baseline(seconds: float = 12.0, max_seconds: float = 30.0) -> dict:
     """The oracle, untuned, on this host's cores: seeded random pixels of the
     same camera traced until about `seconds` of wall time have been spent."""
@@ -146,9 +163,16 @@ def cpu_baseline(seconds: float = 12.0, max_seconds: float = 30.0) -> dict:
             break
         del t1
     el = time.perf_counter() - t0
+    # one host core, for comparison with the paper's sequential C (Sec. 6.4)
+    pix = rng.choice(cw.n, 256, replace=False)
+    ics = oracle.camera_ics(cw.M, cw.a, cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny, pix)
+    t1 = time.perf_counter()
+    out1 = oracle.trace_many(cw.M, cw.a, ics, t_term, nthreads=1)
+    single = int(out1["steps"].sum()) / (time.perf_counter() - t1)
     return {"value": steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{rays} seeded random pixels of the {cw.nx}x{cw.ny} camera ({steps} RK4 steps, "
-                      f"{el:.1f} s incl. initial-data construction), OpenMP over rays"}
+                      f"{el:.1f} s incl. initial-data construction), OpenMP over rays",
+            "single_thread_value": single, "cpu_model": cpu_model()}
 
 
 REFERENCE_PIXELS_PER_STEP = 16384
@@ -185,7 +209,7 @@ def run_reference(args) -> None:
         steps += s
         secs += t
     value = steps / secs
-    cb = {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+    cb = {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
           "sample": f"{args.steps} x {REFERENCE_PIXELS_PER_STEP} seeded random pixels of the {cw.nx}x{cw.ny} camera "
                     f"({steps} RK4 steps in {secs:.1f} s incl. initial data), OpenMP over rays"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -417,6 +441,67 @@ def run_bound_case(mb, torch, stream, flush, n: int, n_steps: int, precisions, w
     return res
 
 
+# The paper's timing experiment (Sec. 6.4, its two tables of GPU and CPU
+# run times): Kerr a = 0.5M, RK4 with h = 0.1, t_f = 1000 (10^4 steps, t_f
+# read as proper time), N random timelike geodesics; its GPU run times in
+# seconds, without and with per-step output to disk.
+PAPER_N = (10, 100, 500, 1000, 5000, 10000, 50000)
+PAPER_GPU_S_NO_OUTPUT = {10: 2.16987, 100: 2.301033, 500: 4.628749, 1000: 4.63499, 5000: 13.598218,
+                         10000: 27.066675}
+PAPER_GPU_S_WITH_OUTPUT = {10: 60 * 0.0545956, 100: 60 * 0.11868735, 500: 60 * 0.3829293, 1000: 60 * 0.66657395,
+                           5000: 60 * 3.543259, 10000: 60 * 7.14927418, 50000: 60 * 35.6253648}
+
+
+def run_paper_case(mb, torch, stream, stride: int = 10) -> dict:
+    """The paper's timing experiment on this GPU, FP64: for each N, the
+    generic bound-orbit sampler with the spin fixed at 0.5 gives the N
+    initial states (the paper's are unspecified random timelike geodesics),
+    traced 10^4 steps of h = 0.1 (a) with the final state only and (b) with
+    the trajectory every `stride` steps copied to pinned host memory (the
+    paper writes ASCII at every step).  CUDA events on the launching stream;
+    (b) includes the device-to-host copy."""
+    from paper_1803_08320_gb300 import workloads as W
+
+    term = W.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=10_000, dl=0.1)
+    n_max = max(PAPER_N)
+    ics_all, _, _ = mb.ic_bound(1.0, 0.5, W.SEED_BASE + 6, n_max, spin_fixed=True)
+    Lmax = mb.out_layout(mb.OUT_STRIDED, "fp64", n_max, term.n_steps_cap, stride)
+    out = torch.empty(Lmax.total, dtype=torch.uint8, device="cuda")
+    host = torch.empty(Lmax.total, dtype=torch.uint8, pin_memory=True)
+    rows = []
+    with torch.cuda.stream(stream):
+        mb.trace(1.0, 0.5, ics_all[:, :10].contiguous(), term, precision="fp64", stream=stream, out=out)
+        for n in PAPER_N:
+            ics = ics_all[:, :n].contiguous()
+            row = {"n": n}
+            for mode in ("final", "strided"):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                stream.synchronize()
+                e0.record(stream)
+                if mode == "final":
+                    r = mb.trace(1.0, 0.5, ics, term, precision="fp64", stream=stream, out=out)
+                    nbytes = 0
+                else:
+                    L = mb.out_layout(mb.OUT_STRIDED, "fp64", n, term.n_steps_cap, stride)
+                    r = mb.trace(1.0, 0.5, ics, term, mode=mb.OUT_STRIDED, stride=stride, precision="fp64",
+                                 stream=stream, out=out)
+                    host[:L.total].copy_(out[:L.total], non_blocking=True)
+                    nbytes = int(L.total)
+                e1.record(stream)
+                stream.synchronize()
+                sec = e0.elapsed_time(e1) / 1e3
+                steps = int(r["steps"].to(torch.int64).sum().item())
+                row[mode] = {"seconds": sec, "steps_per_s": steps / sec, "d2h_bytes": nbytes}
+            p0, p1 = PAPER_GPU_S_NO_OUTPUT.get(n), PAPER_GPU_S_WITH_OUTPUT.get(n)
+            row["paper_gpu_seconds"] = {"no_output": p0, "with_ascii_output": p1}
+            row["speedup_vs_paper_gpu"] = {"no_output": p0 / row["final"]["seconds"] if p0 else None,
+                                           "with_output": p1 / row["strided"]["seconds"] if p1 else None}
+            rows.append(row)
+    return {"a": 0.5, "h": 0.1, "rk4_steps_per_ray": 10_000, "trajectory_stride": stride, "precision": "fp64",
+            "rows": rows,
+            "paper_hardware": "GTX 960M (Maxwell), CUDA 7.5; the paper's numbers are context, not a target"}
+
+
 def serving_bundle(mb, r):
     return bundle_of(mb, r.kind, r.n, r.a, r.cap, r.incl, r.seed, side=r.side)
 
@@ -561,6 +646,14 @@ def run_workload(args) -> None:
                          "config": {"workload": f"uneven_bundles_{count}_of_4096_size64-65536_cap1e3-1e5",
                                     "l2": res["l2"]},
                          "gpu_launches": args.steps, "bundles": res})
+        elif args.workload == "paper":
+            res = run_paper_case(mb, torch, stream)
+            big = res["rows"][-1]
+            line.update({"value": big["final"]["steps_per_s"], "ms_per_step": 1e3 * big["final"]["seconds"],
+                         "dtype": "f64",
+                         "config": {"workload": "paper_sec6.4_kerr_a0.5_h0.1_1e4steps_N10-50000",
+                                    "l2": "one launch per N; the inputs fit in L2 for small N"},
+                         "gpu_launches": 2 * len(res["rows"]) + 1, "paper": res})
         elif args.workload == "bound":
             res = run_bound_case(mb, torch, stream, flush, args.particles, args.bound_steps,
                                  ["fp64", "fp32_mixed"])
@@ -596,7 +689,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", choices=["camera_fp64", "camera_mixed"], default=None,
                     help="small case for ncu: a 512x512 render of the same camera, --steps times")
-    ap.add_argument("--workload", choices=["camera", "bundles", "serving", "bound"], default="camera",
+    ap.add_argument("--workload", choices=["camera", "bundles", "serving", "bound", "paper"], default="camera",
                     help="camera: the headline line (with a bundles and a serving sample); bundles: uneven "
                          "bundles, persistent graph launch vs one launch per bundle; serving: Poisson "
                          "arrivals at several rates, continuous batching vs one launch per request; bound: "

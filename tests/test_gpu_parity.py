@@ -348,6 +348,26 @@ def test_edge_cases(mb, orc):
     assert np.array_equal(got["y"], base) and np.all(got["lambda"] == 0)
 
 
+def test_self_convergence_is_fourth_order(mb, W):
+    """The GPU integrator is fourth order (the paper's self-convergence test,
+    Sec. 6.3): for generic bound Kerr orbits (a = 0.5) integrated to the same
+    proper time with h, h/2 and h/4, Q = |y_h - y_h/2| / |y_h/2 - y_h/4| is
+    close to 2^4 = 16."""
+    wl = W.bound()
+    ics, _, _ = mb.ic_bound(1.0, 0.5, wl.seed, 128, spin_fixed=True)
+    finals = []
+    for h in (0.2, 0.1, 0.05):
+        t = W.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=int(round(200.0 / h)), dl=h)
+        finals.append(gpu_trace(mb, 1.0, 0.5, ics, t)["y"])
+    d1 = np.abs(finals[0] - finals[1]).max(axis=0)
+    d2 = np.abs(finals[1] - finals[2]).max(axis=0)
+    ok = np.isfinite(d1) & np.isfinite(d2) & (d2 > 1e-12)
+    q = d1[ok] / d2[ok]
+    assert ok.mean() > 0.95
+    assert 15.0 < np.median(q) < 17.0, np.median(q)
+    assert np.mean((q > 13.0) & (q < 19.0)) > 0.9
+
+
 def test_strided_trajectories_match_oracle(mb, orc):
     from paper_1803_08320_gb300.malbec import Termination
 
