@@ -40,6 +40,7 @@ class Term(ctypes.Structure):
         ("n_steps_cap", _U32),
         ("dl", _D),
         ("dl_r_scale", _D),
+        ("form", _U32),
     ]
 
 
@@ -122,8 +123,9 @@ def _vp(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
 
 
-def make_term(eps_hor=0.01, r_esc=1e30, n_steps_cap=1000, dl=0.01, dl_r_scale=0.0) -> Term:
-    return Term(float(eps_hor), float(r_esc), int(n_steps_cap), float(dl), float(dl_r_scale))
+def make_term(eps_hor=0.01, r_esc=1e30, n_steps_cap=1000, dl=0.01, dl_r_scale=0.0, form=0) -> Term:
+    """form 0: geodesic equation (eq. geo); 1: canonical equations (eq. Ham)."""
+    return Term(float(eps_hor), float(r_esc), int(n_steps_cap), float(dl), float(dl_r_scale), int(form))
 
 
 # ---------------------------------------------------------------- geometry

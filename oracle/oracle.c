@@ -255,6 +255,18 @@ static int all_finite(const double y[8]) {
  * is fixed (dl) or dl_r_scale * r at the start of the step, held for all four
  * stages.  traj (optional) receives sample k (k*stride steps) at
  * traj[k*8 ...]; samples after termination are NaN. */
+/* (x, p) -> (x, u): u^m = g^{mn} p_n. */
+static void canonical_to_state(double M, double a, const double z[8], double y[8]) {
+  double gi[16];
+  orc_inverse_metric(M, a, z[1], z[2], gi);
+  for (int m = 0; m < 4; ++m) {
+    double acc = 0.0;
+    for (int n = 0; n < 4; ++n) acc += gi[IDX2(m, n)] * z[4 + n];
+    y[m] = z[m];
+    y[4 + m] = acc;
+  }
+}
+
 int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, double y[8],
                   double* lambda, uint32_t* steps, double* traj, uint32_t stride) {
   double r_cap = (1.0 + t->eps_hor) * orc_r_plus(M, a);
@@ -262,20 +274,36 @@ int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, dou
   int fate = ORC_FATE_CAPPED;
   uint32_t n = 0;
   double lam = 0.0;
+  /* the integrated state: (x, u), or (x, p) with p = g u in the canonical
+   * form; inputs, samples and the result are (x, u) in both */
+  const int canonical = t->form == 1;
+  double z[8];
   memcpy(y, y0, 8 * sizeof(double));
+  memcpy(z, y0, 8 * sizeof(double));
+  if (canonical) orc_state_to_momenta(M, a, y0, z + 4);
   if (ns) memcpy(traj, y, 8 * sizeof(double));
+  orc_bh bh = {M, a};
   while (n < t->n_steps_cap) {
-    double h = (t->dl_r_scale > 0.0) ? t->dl_r_scale * y[1] : t->dl;
+    double h = (t->dl_r_scale > 0.0) ? t->dl_r_scale * z[1] : t->dl;
     double r_stage_min;
-    orc_bh bh = {M, a};
-    rk4_generic(geo_fn, &bh, 8, h, y, 1, &r_stage_min);
+    rk4_generic(canonical ? ham_fn : geo_fn, &bh, 8, h, z, 1, &r_stage_min);
     lam += h;
     ++n;
-    if (ns && n % stride == 0) memcpy(traj + (size_t)(n / stride) * 8, y, 8 * sizeof(double));
-    if (y[1] <= r_cap || r_stage_min <= r_cap) { fate = ORC_FATE_CAPTURED; break; }
-    if (!all_finite(y)) { fate = ORC_FATE_NONFINITE; break; }
-    if (y[1] >= t->r_esc) { fate = ORC_FATE_ESCAPED; break; }
+    if (ns && n % stride == 0) {
+      double* s = traj + (size_t)(n / stride) * 8;
+      if (canonical)
+        canonical_to_state(M, a, z, s);
+      else
+        memcpy(s, z, 8 * sizeof(double));
+    }
+    if (z[1] <= r_cap || r_stage_min <= r_cap) { fate = ORC_FATE_CAPTURED; break; }
+    if (!all_finite(z)) { fate = ORC_FATE_NONFINITE; break; }
+    if (z[1] >= t->r_esc) { fate = ORC_FATE_ESCAPED; break; }
   }
+  if (canonical)
+    canonical_to_state(M, a, z, y);
+  else
+    memcpy(y, z, 8 * sizeof(double));
   if (ns)
     for (uint32_t k = n / stride + 1; k < ns; ++k)
       for (int c = 0; c < 8; ++c) traj[(size_t)k * 8 + c] = NAN;

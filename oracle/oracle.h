@@ -39,6 +39,8 @@ typedef struct {
   uint32_t n_steps_cap;/* capped after this many steps */
   double dl;           /* fixed step, used when dl_r_scale == 0 */
   double dl_r_scale;   /* if > 0: h_n = dl_r_scale * r_n (r at the step start) */
+  uint32_t form;       /* 0: the geodesic equation in (x, u) (Sec. 2, eq. geo);
+                          1: the canonical equations in (x, p) (Sec. 2, eq. Ham) */
 } orc_term;
 
 /* -------- geometry (Sec. 2, eq. kerr) -------- */

@@ -760,3 +760,54 @@ def test_trace_many_matches_trace_one(orc):
         assert np.array_equal(many["y"][:, i], one["y"])
         assert many["steps"][i] == one["steps"] and many["fate"][i] == one["fate"]
         np.testing.assert_array_equal(many["inv0"][:, i], orc.invariants(1.0, spins[i], ys[:, i]))
+
+
+# --------------------------------------------------------------------------- canonical form (eq. Ham)
+def test_canonical_trace_conserves_E_and_Lz_exactly(orc):
+    """Sec. 2 eq. Ham: H does not depend on t or phi, so p_t = -E and p_phi =
+    L_z never change along the canonical RK4 trace; the only error left in E
+    and L_z is the conversion (x, u) <-> (x, p) at the two ends, while the
+    geodesic form drifts by the RK4 truncation error."""
+    ys, spins, _ = orc.bound_samples(1.0, 0.9, 11, np.arange(24), spin_fixed=True)
+    geo = orc.make_term(n_steps_cap=4000, dl=0.25)
+    can = orc.make_term(n_steps_cap=4000, dl=0.25, form=1)
+    worst_can, worst_geo = 0.0, 0.0
+    for i in range(ys.shape[1]):
+        i0 = orc.invariants(1.0, 0.9, ys[:, i])
+        a = orc.trace_one(1.0, 0.9, ys[:, i], geo)
+        b = orc.trace_one(1.0, 0.9, ys[:, i], can)
+        if a["fate"] != 3 or b["fate"] != 3:
+            continue
+        ig, ic = orc.invariants(1.0, 0.9, a["y"]), orc.invariants(1.0, 0.9, b["y"])
+        worst_geo = max(worst_geo, np.abs(ig[:2] - i0[:2]).max())
+        worst_can = max(worst_can, np.abs(ic[:2] - i0[:2]).max())
+    assert worst_can < 1e-12
+    assert worst_geo > 1e3 * worst_can
+
+
+def test_canonical_and_geodesic_forms_agree_to_fourth_order(orc):
+    """The two forms are exact rewritings of one flow; their RK4 maps differ by
+    the truncation error, which falls as h^4 (ratio 16 when h halves)."""
+    y0 = orc.circular_state(1.0, 0.6, 9.0, 1)
+    y0[5] = 0.05  # perturb into an eccentric, inclined orbit
+    y0[6] = 0.01
+    diffs = []
+    for h in (0.4, 0.2, 0.1):
+        n = int(round(200.0 / h))
+        a = orc.trace_one(1.0, 0.6, y0, orc.make_term(n_steps_cap=n, dl=h))
+        b = orc.trace_one(1.0, 0.6, y0, orc.make_term(n_steps_cap=n, dl=h, form=1))
+        diffs.append(np.abs(a["y"] - b["y"]).max())
+    assert 12.0 < diffs[0] / diffs[1] < 20.0 and 12.0 < diffs[1] / diffs[2] < 20.0, diffs
+
+
+def test_canonical_circular_orbit_stays_closed(orc):
+    """Sec. 4 circular orbits in the canonical form: r stays at r0 and phi
+    advances at the analytic angular frequency (eq. omega), as in the geodesic
+    form."""
+    for a, r0 in ((0.0, 8.0), (0.7, 7.0)):
+        y0 = orc.circular_state(1.0, a, r0, 1)
+        t = orc.make_term(n_steps_cap=5000, dl=0.02, form=1)
+        res = orc.trace_one(1.0, a, y0, t)
+        assert abs(res["y"][1] - r0) < 1e-9
+        om = y0[7] / y0[4]
+        assert res["y"][3] == pytest.approx(om * res["y"][0], rel=1e-10)
