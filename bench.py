@@ -15,6 +15,7 @@ data-path collective); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -45,10 +46,12 @@ def kernel_source_hash() -> str:
 
 # algorithmic flops per RK4 step, counted from the kernel source expressions
 # (FMA = 2, add/mul = 1, a product or sum written once and reused counted
-# once): 128 per Kerr right-hand side, 42 per Schwarzschild one, 86 for the
-# RK4 stages and combination; divisions and sincos are listed separately
-# (4 each per step)
-FLOPS_PER_STEP = {"kerr": 4 * 128 + 86, "schw": 4 * 42 + 86}
+# once): 128 per Kerr right-hand side of the geodesic form, 42 per
+# Schwarzschild one, 102 for the RK4 stage points and weighted sums; the
+# canonical form (eq. Ham): 72 per Kerr right-hand side, 74 for its RK4
+# (p_t, p_ph fixed).  Divisions and sincos are listed separately (4 each per
+# step).
+FLOPS_PER_STEP = {"kerr": 4 * 128 + 102, "schw": 4 * 42 + 102, "kerr_canonical": 4 * 72 + 74}
 DIV_PER_STEP, SINCOS_PER_STEP = 4, 4
 
 
@@ -605,6 +608,14 @@ def err_stats(torch, dth, dph) -> dict:
     return out
 
 
+@dataclasses.dataclass(frozen=True)
+class CameraRun:
+    """What `timed_renders` needs of a camera workload."""
+    M: float
+    a: float
+    term: object
+
+
 def timed_renders(mb, cw, cam, precision, K, stream, flush, out=None, host_out=None):
     """K renders, each bracketed by CUDA events on the launching stream; the L2
     is flushed (256 MB write) before each, outside the events."""
@@ -774,6 +785,36 @@ def main():
         value = world * steps_per_render * args.steps / t_total
         ms_per_step = 1e3 * t_total / args.steps
 
+        # ---------------- FP64, canonical form (eq. Ham), same protocol
+        term_c = mb.term_from(cw.term, form=mb.FORM_HAMILTONIAN)
+        cwc = CameraRun(cw.M, cw.a, term_c)
+        for _ in range(args.warmup):
+            mb.trace_camera(cw.M, cw.a, cam, term_c, "fp64", stream=stream, out=out)
+        barrier()
+        torch.cuda.synchronize()
+        times_c, res_c = timed_renders(mb, cwc, cam, "fp64", args.steps, stream, flush, out=out)
+        torch.cuda.synchronize()
+        barrier()
+        steps_c = int(res_c["steps"].to(torch.int64).sum().item())
+        t_c = max_over_ranks(sum(times_c) / 1e3)
+        value_c = world * steps_c * args.steps / t_c
+        agree_c = float((res_c["fate"] == fate64).float().mean().item())
+        esc_c = (fate64 == mb.FATE_ESCAPED) & (res_c["fate"] == mb.FATE_ESCAPED)
+        dth_c = (res_c["theta"][esc_c] - theta64[esc_c]).abs()
+        dph_c = (res_c["phi"][esc_c] - phi64[esc_c]).abs()
+        dth_c, dph_c = dth_c[torch.isfinite(dth_c)], dph_c[torch.isfinite(dph_c)]
+        canonical = {"value": value_c, "unit": UNIT, "ms_per_step": 1e3 * t_c / args.steps,
+                     "speedup_vs_geodesic_form": value_c / value, "fate_agreement_vs_geodesic_form": agree_c,
+                     "escaped_difference_vs_geodesic_form": err_stats(torch, dth_c, dph_c),
+                     "roofline": {"bound": "alu", "peak": peak64, "unit": "GFLOP/s (FP64)",
+                                  "flops_per_rk4_step": FLOPS_PER_STEP["kerr_canonical"],
+                                  "achieved": FLOPS_PER_STEP["kerr_canonical"] * steps_c /
+                                  (statistics.mean(times_c) / 1e3) / 1e9,
+                                  "frac": FLOPS_PER_STEP["kerr_canonical"] * steps_c /
+                                  (statistics.mean(times_c) / 1e3) / 1e9 / peak64},
+                     "note": "RK4 on (x, p) with p = g u (Sec. 2, eq. Ham); same camera, inputs and outputs (x, u); "
+                             "the two forms are different discrete maps of the same flow"}
+
         # ---------------- FP32_MIXED, same protocol
         for _ in range(args.warmup):
             mb.trace_camera(cw.M, cw.a, cam, cw.term, "fp32_mixed", stream=stream, out=out)
@@ -824,6 +865,7 @@ def main():
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(L.total),
                 "note": "malbec_trace_camera + copy of the image (fate, steps, theta, phi) to pinned host memory; "
                         "the rays are built on the device from the camera description passed by value"},
+        "canonical_form": canonical,
         "fp32_mixed": {"value": value32, "unit": UNIT, "ms_per_step": 1e3 * t32 / args.steps,
                        "speedup_vs_fp64": value32 / value, "fate_agreement_vs_fp64": agree,
                        "escaped_error_vs_fp64": err_stats(torch, dth, dph),

@@ -84,13 +84,26 @@ typedef struct {
 /* Step rule and termination.  The step is h = dl, or h = dl_r_scale * r_n
  * (r at the start of the step, held for all four stages) when
  * dl_r_scale > 0.  The paper uses a fixed h (Sec. 6).  Requires eps_hor >= 0,
- * r_esc > (1+eps_hor) r_+, and a finite positive step. */
+ * r_esc > (1+eps_hor) r_+, and a finite positive step.
+ * form: the equations RK4 integrates --
+ *   MALBEC_FORM_GEODESIC     (0) the geodesic equation in (x^mu, u^mu),
+ *                            du/dl = -Gamma u u (Sec. 2, eq. geo);
+ *   MALBEC_FORM_HAMILTONIAN  (1) the canonical equations in (x^mu, p_mu),
+ *                            p = g u, H = g^{ab} p_a p_b / 2 (Sec. 2, eq. Ham):
+ *                            the paper's own form; p_t and p_ph (-E and L_z)
+ *                            stay exactly constant.  FP64, malbec_trace and
+ *                            malbec_trace_camera only (MALBEC_EINVAL elsewhere).
+ * Inputs and outputs are (x, u) states in both forms; the two discrete maps
+ * agree to O(h^4) per unit lambda. */
+#define MALBEC_FORM_GEODESIC 0
+#define MALBEC_FORM_HAMILTONIAN 1
 typedef struct {
   double eps_hor;
   double r_esc;
   uint32_t n_steps_cap;
   double dl;
   double dl_r_scale;
+  uint32_t form;
 } malbec_term;
 
 typedef enum {

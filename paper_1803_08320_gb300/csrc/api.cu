@@ -33,6 +33,7 @@ int check_metric(const malbec_metric& m) {
 // escape radius must clear that worst case.
 int check_term(const malbec_term& t, const malbec_metric& m) {
   if (!isfinite(t.eps_hor) || t.eps_hor < 0.0) return MALBEC_EINVAL;
+  if (t.form != MALBEC_FORM_GEODESIC && t.form != MALBEC_FORM_HAMILTONIAN) return MALBEC_EINVAL;
   const bool scaled = t.dl_r_scale != 0.0;
   if (scaled && !finite_pos(t.dl_r_scale)) return MALBEC_EINVAL;
   if (!scaled && !finite_pos(t.dl)) return MALBEC_EINVAL;
@@ -292,6 +293,7 @@ int malbec_trace(malbec_metric m, const double* ics, uint64_t n, malbec_term t, 
   if (rc) return rc;
   rc = check_term(t, m);
   if (rc) return rc;
+  if (t.form == MALBEC_FORM_HAMILTONIAN && prec != MALBEC_FP64) return MALBEC_EINVAL;
   if (!ics || !out) return MALBEC_EINVAL;
   malbec_layout L;
   rc = malbec_out_layout(mode, prec, n, t.n_steps_cap, stride, &L);
@@ -307,6 +309,7 @@ int malbec_trace(malbec_metric m, const double* ics, uint64_t n, malbec_term t, 
   p.r_esc = t.r_esc;
   p.dl = t.dl;
   p.dl_r_scale = t.dl_r_scale;
+  p.form = t.form;
   p.cap = t.n_steps_cap;
   p.ics = ics;
   p.n = n;
@@ -366,6 +369,7 @@ int malbec_trace_camera(malbec_metric m, const malbec_camera* cam, malbec_term t
   if (rc) return rc;
   rc = check_term(t, m);
   if (rc) return rc;
+  if (t.form == MALBEC_FORM_HAMILTONIAN && prec != MALBEC_FP64) return MALBEC_EINVAL;
   rc = check_camera(m, cam, &t);
   if (rc) return rc;
   if (!out || ((uintptr_t)out & 255u) != 0) return MALBEC_EINVAL;
@@ -382,6 +386,7 @@ int malbec_trace_camera(malbec_metric m, const malbec_camera* cam, malbec_term t
   p.r_esc = t.r_esc;
   p.dl = t.dl;
   p.dl_r_scale = t.dl_r_scale;
+  p.form = t.form;
   p.cap = t.n_steps_cap;
   p.n = (uint64_t)cam->nx * cam->ny;
   p.cam = make_camera_const(m.M, m.a, *cam);

@@ -194,6 +194,125 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
 }
 
 // ---------------------------------------------------------------------------
+// Canonical form (Sec. 2, eq. Ham): state z = (x^mu, p_mu), dx^mu/dl =
+// dH/dp_mu, dp_mu/dl = -dH/dx^mu with H = g^{ab} p_a p_b / 2.  For Kerr in BL
+// coordinates, with P = (r^2 + a^2) p_t + a p_ph and T = p_ph + a s^2 p_t,
+//   2 rho^2 H = F = Delta p_r^2 + p_th^2 - P^2 / Delta + T^2 / s^2,
+// so dx/dl follows from dF/dp and dp_r/dl = -(dF/dr - F d(rho^2)/dr / rho^2)
+// / (2 rho^2), dp_th/dl likewise; p_t and p_ph are constant (H does not
+// depend on t, ph) and are not integrated.  f = (dt, dr, dth, dph, dp_r,
+// dp_th)/dl.  One division, as in the geodesic form.
+template <typename T>
+__device__ __forceinline__ void ham_kerr(const BH<T>& bh, T r, T th, T pt, T pr, T pth, T pph, T f[6]) {
+  T s, c;
+  Trig<T>::sc(th, &s, &c);
+  const T a = bh.a, a2 = bh.a2;
+  const T s2 = s * s, sc = s * c;
+  const T rho2 = fma(a2, c * c, r * r);
+  const T Delta = fma(r, r - bh.twoM, a2);
+  const T rD = rho2 * Delta;
+  const T inv = T(1) / (rD * s2);
+  const T irho2 = Delta * s2 * inv;
+  const T iDelta = rho2 * s2 * inv;
+  const T is2 = rD * inv;
+  const T r2a2 = fma(r, r, a2);
+  const T P = fma(r2a2, pt, a * pph);
+  const T Tq = fma(a * s2, pt, pph);
+  const T PiD = P * iDelta;
+  const T TiS = Tq * is2;
+  f[0] = fma(-r2a2, PiD, a * Tq) * irho2;
+  f[1] = Delta * pr * irho2;
+  f[2] = pth * irho2;
+  f[3] = fma(-a, PiD, TiS) * irho2;
+  const T pr2 = pr * pr;
+  const T F = fma(Tq, TiS, fma(-P, PiD, fma(pth, pth, Delta * pr2)));
+  const T dFr = fma(T(2) * (r - bh.M), fma(PiD, PiD, pr2), T(-4) * r * pt * PiD);
+  const T dFth = T(2) * (sc * is2) * Tq * fma(T(2) * a, pt, -TiS);
+  const T mh = T(-0.5) * irho2;
+  f[4] = mh * fma(T(-2) * r * F, irho2, dFr);
+  f[5] = mh * fma(T(2) * a2 * sc * F, irho2, dFth);
+}
+
+// One classical RK4 step of the canonical state z (same tableau and the same
+// stage-by-stage sums as rk4_step); p_t = z[4] and p_ph = z[7] stay fixed.
+// Returns the smallest radius among the three intermediate stage points.
+template <typename T, bool kRolled = false>
+__device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
+  const T hh = T(0.5) * h;
+  T r = z[1], th = z[2], pr = z[5], pth = z[6];
+  T sx[6];
+  T rmin = T(0);
+  auto stage = [&](int s) {
+    T f[6];
+    ham_kerr<T>(bh, r, th, z[4], pr, pth, z[7], f);
+    if (s == 0) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) sx[j] = f[j];
+    } else {
+      const T w = s == 3 ? T(1) : T(2);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) sx[j] = fma(w, f[j], sx[j]);
+    }
+    if (s < 3) {
+      const T c = s < 2 ? hh : h;
+      r = fma(c, f[1], z[1]);
+      th = fma(c, f[2], z[2]);
+      pr = fma(c, f[4], z[5]);
+      pth = fma(c, f[5], z[6]);
+      rmin = s == 0 ? r : fmin(rmin, r);
+    }
+  };
+  if constexpr (kRolled) {
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) stage(s);
+  } else {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) stage(s);
+  }
+  const T h6 = h * T(1.0 / 6.0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) z[j] = fma(h6, sx[j], z[j]);
+  z[5] = fma(h6, sx[4], z[5]);
+  z[6] = fma(h6, sx[5], z[6]);
+  return rmin;
+}
+
+// p_mu = g_{mu nu} u^nu (Kerr, BL): the canonical momenta of a state.
+__device__ __forceinline__ void lower_velocity(double M, double a, const double y[8], double p[4]) {
+  double s, c;
+  sincos(y[2], &s, &c);
+  const double r = y[1], a2 = a * a, s2 = s * s;
+  const double rho2 = fma(a2, c * c, r * r);
+  const double Delta = fma(r, r - 2.0 * M, a2);
+  const double q = 2.0 * M * r / rho2;
+  const double gtp = -a * s2 * q;
+  const double gpp = s2 * fma(a2 * s2, q, fma(r, r, a2));
+  p[0] = fma(q - 1.0, y[4], gtp * y[7]);
+  p[1] = rho2 / Delta * y[5];
+  p[2] = rho2 * y[6];
+  p[3] = fma(gtp, y[4], gpp * y[7]);
+}
+
+// u^mu = g^{mu nu} p_nu (Kerr, BL); the (t, ph) block inverse has
+// determinant -Delta sin^2.
+__device__ __forceinline__ void raise_momentum(double M, double a, const double z[8], double u[4]) {
+  double s, c;
+  sincos(z[2], &s, &c);
+  const double r = z[1], a2 = a * a, s2 = s * s;
+  const double rho2 = fma(a2, c * c, r * r);
+  const double Delta = fma(r, r - 2.0 * M, a2);
+  const double q = 2.0 * M * r / rho2;
+  const double gtt = q - 1.0;
+  const double gtp = -a * s2 * q;
+  const double gpp = s2 * fma(a2 * s2, q, fma(r, r, a2));
+  const double det = -Delta * s2;
+  u[0] = fma(gpp, z[4], -gtp * z[7]) / det;
+  u[1] = Delta / rho2 * z[5];
+  u[2] = z[6] / rho2;
+  u[3] = fma(gtt, z[7], -gtp * z[4]) / det;
+}
+
+// ---------------------------------------------------------------------------
 // Conserved quantities in FP64: p = g u; E = -p_t, L_z = p_ph,
 // Q = p_th^2 + cos^2 (a^2 (mu^2 - E^2) + L_z^2 / sin^2) with mu^2 = -g(u,u),
 // norm = g(u,u).

@@ -74,6 +74,7 @@ struct TraceParams {
   double zone_horizon, zone_photon, zone_pole;
   int zone_batch, zone_wait;
   int exchange;       // FP32_MIXED: block ray exchange on (1) / off (0)
+  uint32_t form;      // MALBEC_FORM_*
   // work queue (scratch, zeroed before launch)
   unsigned long long* head;
   // multi-job source: job table, per-job counters (zeroed), longest-first

@@ -301,9 +301,10 @@ constexpr unsigned long long kZoneWarpWaitNs = 600ull * 1000000000ull;
 // budget is not the occupancy limit; without the minimum-blocks argument the
 // compiler capped some instantiations (the request-loop ones) at 128
 // registers and spilled.
-template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks>
+template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, bool kHam>
 __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) {
   static_assert(!kBanks || kMixed, "block banks exist for FP32_MIXED only");
+  static_assert(!kHam || (!kMixed && kKerr), "the canonical form runs in FP64 with the Kerr Hamiltonian");
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const float k6h = (float)(1.0 / 6.0), k6l = (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0));
@@ -722,6 +723,13 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
           }
         }
         if (kSink == kSinkStrided) store_sample<kMixed>(p, id, 0, y, hi);
+        if constexpr (kHam) {
+          // canonical form: integrate (x, p) with p = g u
+          double pz[4];
+          lower_velocity(M, a, y, pz);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) y[4 + c] = pz[c];
+        }
       }
       continue;
     }
@@ -785,7 +793,11 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
       bool captured, escaped, finite;
       if (!kMixed) {
         const double h = dl_scale > 0.0 ? dl_scale * y[1] : dl;
-        const double rmin = rk4_step<kKerr, double>(bh64, h, y);
+        double rmin;
+        if constexpr (kHam)
+          rmin = rk4_step_ham<double>(bh64, h, y);
+        else
+          rmin = rk4_step<kKerr, double>(bh64, h, y);
         lam += h;
         captured = (y[1] <= r_cap) | (rmin <= r_cap);
         escaped = y[1] >= r_esc;
@@ -825,7 +837,17 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         finite = finite8f(hi) & finite8f(lo);
       }
       ++nst;
-      if (kSink == kSinkStrided && (nst % p.stride) == 0) store_sample<kMixed>(p, id, nst / p.stride, y, hi);
+      if (kSink == kSinkStrided && (nst % p.stride) == 0) {
+        if constexpr (kHam) {
+          double yu[8];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) yu[c] = y[c];
+          raise_momentum(M, a, y, yu + 4);
+          store_sample<kMixed>(p, id, nst / p.stride, yu, hi);
+        } else {
+          store_sample<kMixed>(p, id, nst / p.stride, y, hi);
+        }
+      }
       // ---- termination tests, in the documented order
       if (captured)
         fate = MALBEC_FATE_CAPTURED;
@@ -840,6 +862,13 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
     }
 
     if (fate != 0) {
+      if constexpr (kHam) {
+        // back to (x, u) for the outputs and the invariants
+        double u[4];
+        raise_momentum(M, a, y, u);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) y[4 + c] = u[c];
+      }
       if (kMixed) {
         flush_lam();
 #pragma unroll
@@ -893,15 +922,24 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
   }
 }
 
-template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks>
+template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, bool kHam = false>
 const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&trace_kernel<kKerr, kMixed, kSrc, kSink, kBanks>);
+  return reinterpret_cast<const void*>(&trace_kernel<kKerr, kMixed, kSrc, kSink, kBanks, kHam>);
 }
 
 // The kernel for a launch; FP32_MIXED kernels come with and without the
 // block ray exchange (two instantiations, so that the one without carries
 // none of its code).
-const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks) {
+const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, bool ham) {
+  // canonical form (Sec. 2, eq. Ham): FP64, state arrays and cameras
+  if (ham) {
+    if (mixed) return nullptr;
+    if (src == kSrcStates && sink == kSinkFinal) return kernel_ptr<true, false, kSrcStates, kSinkFinal, false, true>();
+    if (src == kSrcStates && sink == kSinkStrided)
+      return kernel_ptr<true, false, kSrcStates, kSinkStrided, false, true>();
+    if (src == kSrcCamera && sink == kSinkCamera) return kernel_ptr<true, false, kSrcCamera, kSinkCamera, false, true>();
+    return nullptr;
+  }
 #define MALBEC_PICK(K, X, S, T)                                                        \
   if (kerr == K && mixed == X && src == S && sink == T) {                              \
     if (X && banks) return kernel_ptr<K, X, S, T, X>();                               \
@@ -930,7 +968,7 @@ const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks) {
 }  // namespace
 
 int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, int threads_per_block) {
-  const void* k = pick(kerr, mixed, src, sink, mixed);  // the larger of the two kernels
+  const void* k = pick(kerr, mixed, src, sink, mixed, false);  // the larger of the two kernels
   if (!k) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads_per_block, 0) != cudaSuccess) return 0;
@@ -944,7 +982,7 @@ cudaError_t launch_trace(const TraceParams& p, bool kerr, bool mixed, Source src
   // zone), off for whole-image cameras (too few steps in their zone to pay
   // for a zone warp)
   const int exchange = p.exchange >= 0 ? p.exchange : (src == kSrcCamera ? 0 : 1);
-  const void* k = pick(kerr, mixed, src, sink, mixed && exchange == 1);
+  const void* k = pick(kerr, mixed, src, sink, mixed && exchange == 1, p.form == MALBEC_FORM_HAMILTONIAN);
   if (!k) return cudaErrorInvalidValue;
   // automatic FP64-zone batch: 8 lanes with the exchange (a warp hands fewer
   // zone rays to the zone warp), a full warp without it (a zone step then

@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmalbec.so")
 
 FP64, FP32_MIXED = 0, 1
+FORM_GEODESIC, FORM_HAMILTONIAN = 0, 1
 OUT_FINAL, OUT_STRIDED = 0, 1
 FATE_CAPTURED, FATE_ESCAPED, FATE_CAPPED, FATE_NONFINITE = 1, 2, 3, 4
 OK, EINVAL, ENOMEM, EBUSY, ETIMEDOUT, ECUDA, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
@@ -34,7 +35,8 @@ class Metric(ctypes.Structure):
 
 
 class Term(ctypes.Structure):
-    _fields_ = [("eps_hor", _D), ("r_esc", _D), ("n_steps_cap", _U32), ("dl", _D), ("dl_r_scale", _D)]
+    _fields_ = [("eps_hor", _D), ("r_esc", _D), ("n_steps_cap", _U32), ("dl", _D), ("dl_r_scale", _D),
+                ("form", _U32)]
 
 
 class Camera(ctypes.Structure):
@@ -198,16 +200,18 @@ class Termination:
     n_steps_cap: int = 10_000
     dl: float = 0.01
     dl_r_scale: float = 0.0
+    form: int = 0  # FORM_GEODESIC or FORM_HAMILTONIAN
 
     def c(self) -> Term:
         return Term(float(self.eps_hor), float(self.r_esc), int(self.n_steps_cap), float(self.dl),
-                    float(self.dl_r_scale))
+                    float(self.dl_r_scale), int(self.form))
 
 
-def term_from(t) -> Termination:
-    if isinstance(t, Termination):
+def term_from(t, form=None) -> Termination:
+    if isinstance(t, Termination) and form is None:
         return t
-    return Termination(t.eps_hor, t.r_esc, t.n_steps_cap, t.dl, t.dl_r_scale)
+    f = getattr(t, "form", 0) if form is None else form
+    return Termination(t.eps_hor, t.r_esc, t.n_steps_cap, t.dl, t.dl_r_scale, int(f))
 
 
 def _prec(p) -> int:

@@ -101,6 +101,7 @@ def test_trace_validation_rejects_before_any_cuda_call(mb):
         (mb.Metric(1.0, 0.5, None), _term(dl=0.0, dl_r_scale=-0.05)),
         (mb.Metric(1.0, 0.5, None), _term(r_esc=1.5)),  # escape inside the capture radius
         (mb.Metric(1.0, 0.5, None), _term(eps_hor=-0.1)),
+        (mb.Metric(1.0, 0.5, None), _term(form=2)),   # no such form
     ]
     for m, t in cases:
         assert lib.malbec_trace(m, fake, 10, t, mb.OUT_FINAL, 0, mb.FP64, fake, None) == mb.EINVAL
@@ -109,6 +110,10 @@ def test_trace_validation_rejects_before_any_cuda_call(mb):
     assert lib.malbec_trace(m, fake, 0, good, mb.OUT_FINAL, 0, mb.FP64, fake, None) == mb.EINVAL
     assert lib.malbec_trace(m, fake, 10, good, mb.OUT_STRIDED, 0, mb.FP64, fake, None) == mb.EINVAL
     assert lib.malbec_trace(m, fake, 10, good, mb.OUT_FINAL, 0, mb.FP64, ctypes.c_void_p(257), None) == mb.EINVAL
+    # the canonical form runs in FP64 only
+    canon = _term(eps_hor=0.01, r_esc=1000.0, n_steps_cap=10, dl=0.01, form=mb.FORM_HAMILTONIAN)
+    assert lib.malbec_trace(m, fake, 10, canon, mb.OUT_FINAL, 0, mb.FP32_MIXED, fake, None) == mb.EINVAL
+    assert lib.malbec_trace_noalloc(m, fake, 10, canon, mb.OUT_FINAL, 0, mb.FP32_MIXED, fake, None) == mb.EINVAL
 
 
 def test_camera_validation(mb):

@@ -108,8 +108,9 @@ def gpu_trace(mb, M, a, ics, term, **kw):
     return {k: (np_(v) if hasattr(v, "detach") else v) for k, v in res.items() if k not in ("buffer", "_keep")}
 
 
-def oracle_term(orc, t):
-    return orc.make_term(t.eps_hor, t.r_esc, t.n_steps_cap, t.dl, t.dl_r_scale)
+def oracle_term(orc, t, form=None):
+    f = getattr(t, "form", 0) if form is None else form
+    return orc.make_term(t.eps_hor, t.r_esc, t.n_steps_cap, t.dl, t.dl_r_scale, f)
 
 
 # --------------------------------------------------------------------------- initial data
@@ -222,10 +223,10 @@ def _pixel_ab(cw, pix):
     return al, be
 
 
-def _camera_compare(mb, orc, cw, got, pix, exclusion=0.098):
+def _camera_compare(mb, orc, cw, got, pix, exclusion=0.098, form=0):
     """Per-pixel comparison with the oracle on the pixels `pix`."""
     ics = orc.camera_ics(cw.M, cw.a, cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny, pix)
-    ref, kappa = oracle_kappa(orc, cw.M, cw.a, ics, oracle_term(orc, cw.term))
+    ref, kappa = oracle_kappa(orc, cw.M, cw.a, ics, oracle_term(orc, cw.term, form))
     near = np.array([orc.critical_curve_distance(cw.M, cw.a, cw.incl, *_pixel_ab(cw, p)) < exclusion for p in pix])
     fate_g = got["fate"][pix]
     agree = fate_g == ref["fate"]
