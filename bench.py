@@ -46,12 +46,12 @@ def kernel_source_hash() -> str:
 
 # algorithmic flops per RK4 step, counted from the kernel source expressions
 # (FMA = 2, add/mul = 1, a product or sum written once and reused counted
-# once): 128 per Kerr right-hand side of the geodesic form, 42 per
+# once): 120 per Kerr right-hand side of the geodesic form, 42 per
 # Schwarzschild one, 102 for the RK4 stage points and weighted sums; the
 # canonical form (eq. Ham): 72 per Kerr right-hand side, 74 for its RK4
 # (p_t, p_ph fixed).  Divisions and sincos are listed separately (4 each per
 # step).
-FLOPS_PER_STEP = {"kerr": 4 * 128 + 102, "schw": 4 * 42 + 102, "kerr_canonical": 4 * 72 + 74}
+FLOPS_PER_STEP = {"kerr": 4 * 120 + 102, "schw": 4 * 42 + 102, "kerr_canonical": 4 * 72 + 74}
 DIV_PER_STEP, SINCOS_PER_STEP = 4, 4
 
 

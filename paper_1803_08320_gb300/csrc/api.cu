@@ -439,7 +439,7 @@ int malbec_invariants(malbec_metric m, const double* states, uint64_t n, double*
 const char* malbec_build_info(void) {
 #define MALBEC_S2(x) #x
 #define MALBEC_S(x) MALBEC_S2(x)
-  return "libmalbec: sm_103a, nvcc " MALBEC_S(__CUDACC_VER_MAJOR__) "." MALBEC_S(__CUDACC_VER_MINOR__) ", -O3, no fast-math, FMA contraction on";
+  return "libmalbec: sm_103a, nvcc " MALBEC_S(__CUDACC_VER_MAJOR__) "." MALBEC_S(__CUDACC_VER_MINOR__) ", -O3, no fast-math, no implicit FMA contraction (explicit fma only)";
 }
 
 }  // extern "C"

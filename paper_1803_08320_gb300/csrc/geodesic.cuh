@@ -33,7 +33,7 @@ struct Trig<float> {
 
 template <typename T>
 struct BH {
-  T M, a, a2, twoM;
+  T M, a, a2, twoM, two_a2;
 };
 
 template <typename T>
@@ -43,6 +43,7 @@ __device__ __forceinline__ BH<T> make_bh(double M, double a) {
   b.a = T(a);
   b.a2 = T(a * a);
   b.twoM = T(2.0 * M);
+  b.two_a2 = T(2.0 * a * a);
   return b;
 }
 
@@ -88,22 +89,26 @@ __device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T th, T ut, T u
   const T Ds2 = Delta * s2;
   const T inv = T(1) / (rho2 * Ds2);
   const T irho2 = Ds2 * inv;
-  const T iDelta = rho2 * s2 * inv;
-  const T is2 = rho2 * Delta * inv;
+  const T iDs2 = rho2 * inv;  // 1 / (Delta sin^2)
+  const T iDelta = iDs2 * s2;
+  const T r_2 = T(2) * r;
   const T q = bh.twoM * r * irho2;
-  const T dq_r = fma(T(-2) * r, q, bh.twoM) * irho2;
-  const T dq_th = T(2) * a2 * sc * q * irho2;
+  const T qi = q * irho2;
+  const T dq_r = fma(-r_2, q, bh.twoM) * irho2;
+  const T a2sc_2 = bh.two_a2 * sc;  // 2 a^2 sin cos
+  const T dq_th = a2sc_2 * qi;
   const T r2a2 = fma(r, r, a2);
   const T s4 = s2 * s2;
+  const T as2 = a * s2;
   // d_r and d_theta of g_tt, g_tph, g_phph, g_rr, g_thth
-  const T dtp_r = -a * s2 * dq_r;
+  const T dtp_r = -as2 * dq_r;
   const T dtp_th = -a * fma(T(2) * sc, q, s2 * dq_th);
-  const T dpp_r = fma(a2 * s4, dq_r, T(2) * r * s2);
+  const T dpp_r = fma(a2 * s4, dq_r, r_2 * s2);
   const T dpp_th = fma(T(2) * sc, r2a2, a2 * fma(T(4) * s2 * sc, q, s4 * dq_th));
-  const T drr_r = fma(-rho2 * T(2) * (r - bh.M), iDelta, T(2) * r) * iDelta;
-  const T drr_th = T(-2) * a2 * sc * iDelta;
-  const T dhh_r = T(2) * r;
-  const T dhh_th = T(-2) * a2 * sc;
+  const T drr_r = fma(-rho2 * T(2) * (r - bh.M), iDelta, r_2) * iDelta;
+  const T drr_th = -a2sc_2 * iDelta;
+  const T dhh_r = r_2;
+  const T dhh_th = -a2sc_2;
   // derivatives along u: D = u^r d_r + u^th d_th
   const T Dtt = fma(ur, dq_r, uth * dq_th);
   const T Dtp = fma(ur, dtp_r, uth * dtp_th);
@@ -121,9 +126,9 @@ __device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T th, T ut, T u
   // raise with g^{mu nu}: (t, phi) block inverse has det = -Delta sin^2
   acc[1] = -Wr * Delta * irho2;
   acc[2] = -Wth * irho2;
-  const T gpp_s2 = fma(a2 * s2, q, r2a2);
+  const T gpp_s2 = fma(a * as2, q, r2a2);
   acc[0] = fma(gpp_s2, Wt, a * q * Wp) * iDelta;
-  acc[3] = fma(q - T(1), Wp, a * s2 * q * Wt) * iDelta * is2;
+  acc[3] = fma(q - T(1), Wp, as2 * q * Wt) * iDs2;
 }
 
 template <bool kKerr, typename T>
