@@ -814,6 +814,20 @@ def main():
                                   (statistics.mean(times_c) / 1e3) / 1e9 / peak64},
                      "note": "RK4 on (x, p) with p = g u (Sec. 2, eq. Ham); same camera, inputs and outputs (x, u); "
                              "the two forms are different discrete maps of the same flow"}
+        fate_c = res_c["fate"].clone()
+        for _ in range(args.warmup):
+            mb.trace_camera(cw.M, cw.a, cam, term_c, "fp32_mixed", stream=stream, out=out)
+        barrier()
+        torch.cuda.synchronize()
+        times_cm, res_cm = timed_renders(mb, cwc, cam, "fp32_mixed", args.steps, stream, flush, out=out)
+        torch.cuda.synchronize()
+        barrier()
+        steps_cm = int(res_cm["steps"].to(torch.int64).sum().item())
+        t_cm = max_over_ranks(sum(times_cm) / 1e3)
+        canonical["fp32_mixed"] = {"value": world * steps_cm * args.steps / t_cm, "unit": UNIT,
+                                   "ms_per_step": 1e3 * t_cm / args.steps,
+                                   "fate_agreement_vs_fp64_canonical": float((res_cm["fate"] == fate_c).float().mean()
+                                                                             .item())}
 
         # ---------------- FP32_MIXED, same protocol
         for _ in range(args.warmup):

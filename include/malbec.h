@@ -91,8 +91,10 @@ typedef struct {
  *   MALBEC_FORM_HAMILTONIAN  (1) the canonical equations in (x^mu, p_mu),
  *                            p = g u, H = g^{ab} p_a p_b / 2 (Sec. 2, eq. Ham):
  *                            the paper's own form; p_t and p_ph (-E and L_z)
- *                            stay exactly constant.  FP64, malbec_trace and
- *                            malbec_trace_camera only (MALBEC_EINVAL elsewhere).
+ *                            stay exactly constant.  FP64 and FP32_MIXED
+ *                            (same FP64 zones); malbec_trace, malbec_trace_noalloc
+ *                            and malbec_trace_camera only (MALBEC_EINVAL for
+ *                            bundles and server jobs).
  * Inputs and outputs are (x, u) states in both forms; the two discrete maps
  * agree to O(h^4) per unit lambda. */
 #define MALBEC_FORM_GEODESIC 0

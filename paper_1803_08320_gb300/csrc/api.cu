@@ -293,7 +293,6 @@ int malbec_trace(malbec_metric m, const double* ics, uint64_t n, malbec_term t, 
   if (rc) return rc;
   rc = check_term(t, m);
   if (rc) return rc;
-  if (t.form == MALBEC_FORM_HAMILTONIAN && prec != MALBEC_FP64) return MALBEC_EINVAL;
   if (!ics || !out) return MALBEC_EINVAL;
   malbec_layout L;
   rc = malbec_out_layout(mode, prec, n, t.n_steps_cap, stride, &L);
@@ -369,7 +368,6 @@ int malbec_trace_camera(malbec_metric m, const malbec_camera* cam, malbec_term t
   if (rc) return rc;
   rc = check_term(t, m);
   if (rc) return rc;
-  if (t.form == MALBEC_FORM_HAMILTONIAN && prec != MALBEC_FP64) return MALBEC_EINVAL;
   rc = check_camera(m, cam, &t);
   if (rc) return rc;
   if (!out || ((uintptr_t)out & 255u) != 0) return MALBEC_EINVAL;

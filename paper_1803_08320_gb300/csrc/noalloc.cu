@@ -62,7 +62,6 @@ extern "C" int malbec_trace_noalloc(malbec_metric m, const double* ics, uint64_t
   if (rc) return rc;
   rc = check_term(t, m);
   if (rc) return rc;
-  if (t.form == MALBEC_FORM_HAMILTONIAN && prec != MALBEC_FP64) return MALBEC_EINVAL;
   if (!ics || !out) return MALBEC_EINVAL;
   malbec_layout L;
   rc = malbec_out_layout(mode, prec, n, t.n_steps_cap, stride, &L);

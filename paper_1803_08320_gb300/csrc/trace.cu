@@ -155,6 +155,46 @@ __device__ __forceinline__ float rk4_step_mixed(const BH<float>& bh, float hf, f
   return rmin;
 }
 
+// The canonical form of rk4_step_mixed: z = (x, p) as compensated pairs,
+// p_t = z[4] and p_ph = z[7] fixed (their float hi words enter the right-hand
+// side); t, r, theta, phi, p_r, p_theta are integrated.
+__device__ __forceinline__ float rk4_step_mixed_ham(const BH<float>& bh, float hf, float h6h, float h6l, float hi[8],
+                                                    float lo[8]) {
+  const float hh = 0.5f * hf;
+  float r = hi[1], th = hi[2], pr = hi[5], pth = hi[6];
+  float sx[6];
+  float rmin = 0.f;
+#pragma unroll 1
+  for (int s = 0; s < 4; ++s) {
+    float f[6];
+    ham_kerr<float>(bh, r, th, hi[4], pr, pth, hi[7], f);
+    if (s == 0) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) sx[j] = f[j];
+    } else {
+      const float w = s == 3 ? 1.f : 2.f;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) sx[j] = fmaf(w, f[j], sx[j]);
+    }
+    if (s < 3) {
+      const float c = s < 2 ? hh : hf;
+      r = hi[1] + fmaf(c, f[1], lo[1]);
+      th = hi[2] + fmaf(c, f[2], lo[2]);
+      pr = hi[5] + fmaf(c, f[4], lo[5]);
+      pth = hi[6] + fmaf(c, f[5], lo[6]);
+      rmin = s == 0 ? r : fminf(rmin, r);
+    }
+  }
+  const int comp[6] = {0, 1, 2, 3, 5, 6};
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float d = h6h * sx[j];
+    const float de = fmaf(h6l, sx[j], fmaf(h6h, sx[j], -d));
+    comp_add(hi[comp[j]], lo[comp[j]], d, de);
+  }
+  return rmin;
+}
+
 __device__ __forceinline__ void step_consts(double dl, double dl_scale, double r_esc, float& h_fix, float& h6h,
                                             float& h6l, float& scale_f, float& r_esc_f) {
   h_fix = (float)dl;
@@ -304,7 +344,7 @@ constexpr unsigned long long kZoneWarpWaitNs = 600ull * 1000000000ull;
 template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, bool kHam>
 __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) {
   static_assert(!kBanks || kMixed, "block banks exist for FP32_MIXED only");
-  static_assert(!kHam || (!kMixed && kKerr), "the canonical form runs in FP64 with the Kerr Hamiltonian");
+  static_assert(!kHam || kKerr, "the canonical form uses the Kerr Hamiltonian (a = 0 included)");
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const float k6h = (float)(1.0 / 6.0), k6l = (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0));
@@ -729,6 +769,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
           lower_velocity(M, a, y, pz);
 #pragma unroll
           for (int c = 0; c < 4; ++c) y[4 + c] = pz[c];
+          if constexpr (kMixed) split_pair(y, hi, lo);
         }
       }
       continue;
@@ -807,7 +848,11 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
 #pragma unroll
         for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
         const double h = dl_scale > 0.0 ? dl_scale * y[1] : dl;
-        const double rmin = rk4_step<kKerr, double, true>(bh64, h, y);
+        double rmin;
+        if constexpr (kHam)
+          rmin = rk4_step_ham<double, true>(bh64, h, y);
+        else
+          rmin = rk4_step<kKerr, double, true>(bh64, h, y);
         flush_lam();
         lam += h;
         split_pair(y, hi, lo);
@@ -831,7 +876,11 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
           ++lam_fix;
         }
         if ((nst & 31u) == 31u) flush_lam();
-        const float rmin = rk4_step_mixed<kKerr>(bh32, hf, h6h, h6l, hi, lo);
+        float rmin;
+        if constexpr (kHam)
+          rmin = rk4_step_mixed_ham(bh32, hf, h6h, h6l, hi, lo);
+        else
+          rmin = rk4_step_mixed<kKerr>(bh32, hf, h6h, h6l, hi, lo);
         captured = (hi[1] <= r_cap_f) | (rmin <= r_cap_f);
         escaped = hi[1] >= r_esc_f;
         finite = finite8f(hi) & finite8f(lo);
@@ -839,11 +888,16 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
       ++nst;
       if (kSink == kSinkStrided && (nst % p.stride) == 0) {
         if constexpr (kHam) {
-          double yu[8];
+          double yz[8], yu[8];
+          float hu[8];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) yu[c] = y[c];
-          raise_momentum(M, a, y, yu + 4);
-          store_sample<kMixed>(p, id, nst / p.stride, yu, hi);
+          for (int c = 0; c < 8; ++c) yz[c] = kMixed ? (double)hi[c] + (double)lo[c] : y[c];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) yu[c] = yz[c];
+          raise_momentum(M, a, yz, yu + 4);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) hu[c] = (float)yu[c];
+          store_sample<kMixed>(p, id, nst / p.stride, yu, hu);
         } else {
           store_sample<kMixed>(p, id, nst / p.stride, y, hi);
         }
@@ -862,17 +916,17 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
     }
 
     if (fate != 0) {
+      if (kMixed) {
+        flush_lam();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
+      }
       if constexpr (kHam) {
         // back to (x, u) for the outputs and the invariants
         double u[4];
         raise_momentum(M, a, y, u);
 #pragma unroll
         for (int c = 0; c < 4; ++c) y[4 + c] = u[c];
-      }
-      if (kMixed) {
-        flush_lam();
-#pragma unroll
-        for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
       }
       if (kSink == kSinkJobs) {
         const JobDesc J = load_job(&p.jobs[job]);
@@ -933,11 +987,15 @@ const void* kernel_ptr() {
 const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, bool ham) {
   // canonical form (Sec. 2, eq. Ham): FP64, state arrays and cameras
   if (ham) {
-    if (mixed) return nullptr;
-    if (src == kSrcStates && sink == kSinkFinal) return kernel_ptr<true, false, kSrcStates, kSinkFinal, false, true>();
-    if (src == kSrcStates && sink == kSinkStrided)
-      return kernel_ptr<true, false, kSrcStates, kSinkStrided, false, true>();
-    if (src == kSrcCamera && sink == kSinkCamera) return kernel_ptr<true, false, kSrcCamera, kSinkCamera, false, true>();
+#define MALBEC_PICK_HAM(S, T)                                                   \
+  if (src == S && sink == T) {                                                  \
+    if (!mixed) return kernel_ptr<true, false, S, T, false, true>();            \
+    return banks ? kernel_ptr<true, true, S, T, true, true>() : kernel_ptr<true, true, S, T, false, true>(); \
+  }
+    MALBEC_PICK_HAM(kSrcStates, kSinkFinal)
+    MALBEC_PICK_HAM(kSrcStates, kSinkStrided)
+    MALBEC_PICK_HAM(kSrcCamera, kSinkCamera)
+#undef MALBEC_PICK_HAM
     return nullptr;
   }
 #define MALBEC_PICK(K, X, S, T)                                                        \

@@ -110,10 +110,7 @@ def test_trace_validation_rejects_before_any_cuda_call(mb):
     assert lib.malbec_trace(m, fake, 0, good, mb.OUT_FINAL, 0, mb.FP64, fake, None) == mb.EINVAL
     assert lib.malbec_trace(m, fake, 10, good, mb.OUT_STRIDED, 0, mb.FP64, fake, None) == mb.EINVAL
     assert lib.malbec_trace(m, fake, 10, good, mb.OUT_FINAL, 0, mb.FP64, ctypes.c_void_p(257), None) == mb.EINVAL
-    # the canonical form runs in FP64 only
-    canon = _term(eps_hor=0.01, r_esc=1000.0, n_steps_cap=10, dl=0.01, form=mb.FORM_HAMILTONIAN)
-    assert lib.malbec_trace(m, fake, 10, canon, mb.OUT_FINAL, 0, mb.FP32_MIXED, fake, None) == mb.EINVAL
-    assert lib.malbec_trace_noalloc(m, fake, 10, canon, mb.OUT_FINAL, 0, mb.FP32_MIXED, fake, None) == mb.EINVAL
+
 
 
 def test_camera_validation(mb):
