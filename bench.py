@@ -691,6 +691,46 @@ def run_workload(args) -> None:
     print(json.dumps(line))
 
 
+class Ranks:
+    """One process per GPU under torchrun: RANK / LOCAL_RANK / WORLD_SIZE from
+    the environment; host-side barrier and max over ranks through gloo (the
+    timings are host numbers; the traced rays never cross ranks)."""
+
+    def __init__(self, world: int, rank: int, local: int):
+        self.world, self.rank, self.local = world, rank, local
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group("gloo")
+
+    @classmethod
+    def from_env(cls) -> "Ranks":
+        return cls(int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+                   int(os.environ.get("LOCAL_RANK", "0")))
+
+    def barrier(self) -> None:
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self) -> None:
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -731,16 +771,12 @@ def main():
 
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     from paper_1803_08320_gb300 import build as _b
     from paper_1803_08320_gb300 import malbec as mb
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("gloo")
+    ranks = Ranks.from_env()
+    world, rank, local = ranks.world, ranks.rank, ranks.local
     torch.cuda.set_device(local)
     _b.build()
     stream = torch.cuda.Stream()
@@ -748,17 +784,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     peak64 = mb.measure_fma_peak("fp64")
     peak32 = mb.measure_fma_peak("fp32_mixed")
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     with torch.cuda.stream(stream):
         L = mb.camera_layout(cam)
@@ -901,8 +927,7 @@ def main():
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
-    if world > 1:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 if __name__ == "__main__":

@@ -44,3 +44,56 @@ def test_drift_and_error_summaries():
     dth = torch.tensor([0.0, 1e-9, 1e-3, 2.0], dtype=torch.float64)
     e = bench.err_stats(torch, dth, dth)
     assert e["rays"] == 4 and e["theta"]["max"] == 2.0 and e["theta"]["above_1e-6"] == 2
+
+
+def _free_port() -> int:
+    import socket
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _ranks_worker(rank, port, q):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "WORLD_SIZE": "2",
+                       "RANK": str(rank), "LOCAL_RANK": str(rank)})
+    sys.path.insert(0, ROOT)
+    import bench
+
+    r = bench.Ranks.from_env()
+    r.barrier()
+    q.put((rank, r.max(1.5 + rank)))
+    r.close()
+
+
+def test_ranks_barrier_and_max_over_gloo():
+    """The bench's multi-rank plumbing (one process per GPU under torchrun):
+    two gloo ranks on the host agree on the maximum of their timings."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_ranks_worker, args=(r, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in ps)
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    assert got == [(0, 2.5), (1, 2.5)]
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """--impl reference launched the way the driver launches N > 1: rank 0
+    prints one JSON line, the other rank exits 0 without work."""
+    port = _free_port()
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2
