@@ -292,6 +292,32 @@ def test_camera_claim_order_is_a_schedule_only(mb, W, nx, ny, precision):
             assert_states_close(x[fin], y[fin], rtol=1e-6, what=k)
 
 
+def test_schwarzschild_camera_parity(mb, orc, W):
+    """The a = 0 camera runs the Schwarzschild kernel: 48 x 48 pixels, fates
+    and steps equal to the oracle away from the critical curve (b = 3 sqrt(3)
+    M, Sec. 4), escaped angles within 1e-9; the shadow is the disc of that
+    radius."""
+    import torch
+
+    cw = W.camera(nx=48, ny=48, a=0.0)
+    cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
+    res = mb.trace_camera(cw.M, 0.0, cam, cw.term, "fp64")
+    torch.cuda.synchronize()
+    got = {k: np_(v) for k, v in res.items() if k != "buffer"}
+    pix = np.arange(cw.n)
+    ref, near, agree, far = _camera_compare(mb, orc, cw, got, pix)
+    good = ref["kappa"] <= KAPPA_MAX
+    assert agree[far & good].all()
+    assert np.array_equal(got["steps"][far & good].astype(np.uint32), ref["steps"][far & good])
+    esc = far & good & (ref["fate"] == mb.FATE_ESCAPED)
+    assert_states_close(got["theta"][esc], ref["y"][2][esc], what="theta")
+    al, be = _pixel_ab(cw, pix)
+    b = np.hypot(al, be)
+    crit = 3.0 * math.sqrt(3.0)
+    assert np.all(got["fate"][b < crit - 0.2] == mb.FATE_CAPTURED)
+    assert np.all(got["fate"][b > crit + 0.2] == mb.FATE_ESCAPED)
+
+
 def test_camera_full_size_sampled_parity(mb, orc, W):
     """The full 1024 x 1024 render in the benchmark's launch configuration,
     checked on 3000 seeded sample pixels: >= 99.99% fate agreement away from
