@@ -280,7 +280,7 @@ def steps_of(views) -> int:
 
 
 def run_bundles_case(mb, torch, stream, flush, count: int, precision: str, K: int, warmup: int,
-                     autotune_every: int = 8) -> dict:
+                     autotune_every: int = 8, per_bundle_arm: bool = True) -> dict:
     """Uneven bundles (the first `count` of the 4096-bundle list): one
     persistent launch replayed from a CUDA graph after autotuning, against
     one launch per bundle on the same stream.  Each timed pass is bracketed
@@ -328,23 +328,25 @@ def run_bundles_case(mb, torch, stream, flush, count: int, precision: str, K: in
             for b in bundles:
                 mb.trace_bundles([b], precision, stream=stream)
 
-        # the kernel is already warm: one small launch before the timed passes
-        mb.trace_bundles([min(bundles, key=lambda b: b.n)], precision, stream=stream)
-        stream.synchronize()
-        t_each = timed(per_bundle, K)
-        steps_each = steps_of(views)
-        agree = sum(int((v["fate"] == f).sum().item()) for v, f in zip(views, fates_plan)) / rays
+        if per_bundle_arm:
+            # the kernel is already warm: one small launch before the timed passes
+            mb.trace_bundles([min(bundles, key=lambda b: b.n)], precision, stream=stream)
+            stream.synchronize()
+            t_each = timed(per_bundle, K)
+            steps_each = steps_of(views)
+            agree = sum(int((v["fate"] == f).sum().item()) for v, f in zip(views, fates_plan)) / rays
     plan.close()
     v_plan = steps_plan / statistics.mean(t_plan)
-    v_each = steps_each / statistics.mean(t_each)
-    return {"bundles": count, "rays": rays, "precision": precision,
-            "rk4_steps_per_pass": steps_plan, "rk4_steps_per_pass_one_launch_each": steps_each,
-            "fate_agreement_between_arms": agree,
+    each = None
+    if per_bundle_arm:
+        v_each = steps_each / statistics.mean(t_each)
+        each = {"value": v_each, "unit": UNIT, "ms_per_pass": 1e3 * statistics.mean(t_each),
+                "gpu_launches_per_pass": count, "rk4_steps_per_pass": steps_each, "fate_agreement_with_graph": agree}
+    return {"bundles": count, "rays": rays, "precision": precision, "rk4_steps_per_pass": steps_plan,
             "persistent_graph": {"value": v_plan, "unit": UNIT, "ms_per_pass": 1e3 * statistics.mean(t_plan),
                                  "gpu_launches_per_pass": 1},
-            "one_launch_per_bundle": {"value": v_each, "unit": UNIT, "ms_per_pass": 1e3 * statistics.mean(t_each),
-                                      "gpu_launches_per_pass": count},
-            "speedup": v_plan / v_each,
+            "one_launch_per_bundle": each,
+            "speedup": v_plan / each["value"] if each else None,
             "autotune": {"best": best, "on_bundles": len(sub), "seconds": t_at},
             "l2": "flushed before every timed pass (outside the events)"}
 
@@ -650,8 +652,10 @@ def run_workload(args) -> None:
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
         if args.workload == "bundles":
             count = args.bundle_count or 4096
+            # a pass of the full list takes tens of seconds: one warm-up replay
             res = run_bundles_case(mb, torch, stream, flush, count, args.precision, K=args.steps,
-                                   warmup=args.warmup)
+                                   warmup=args.warmup if count < 1024 else 1, autotune_every=max(8, count // 128),
+                                   per_bundle_arm=not args.no_per_bundle_arm)
             line.update({"value": res["persistent_graph"]["value"],
                          "ms_per_step": res["persistent_graph"]["ms_per_pass"],
                          "config": {"workload": f"uneven_bundles_{count}_of_4096_size64-65536_cap1e3-1e5",
@@ -756,6 +760,9 @@ def main():
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="req/s for --workload serving")
     ap.add_argument("--requests", type=int, default=64, help="requests per rate for --workload serving")
     ap.add_argument("--no-extras", action="store_true", help="camera line without the bundles/serving samples")
+    ap.add_argument("--no-per-bundle-arm", action="store_true",
+                    help="--workload bundles: time the persistent graph launch only (the full 4096-bundle list "
+                         "takes about ten minutes with one launch per bundle)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
