@@ -84,6 +84,13 @@ def _declare(L):
     sig("orc_adm", None, _D, _D, _D, _D, _PD, _PD, _PD)
     sig("orc_rhs", None, _D, _D, _PD, _PD)
     sig("orc_rhs_hamiltonian", None, _D, _D, _PD, _PD)
+    sig("orc_adm_derivs", None, _D, _D, _D, _D, _PD, _PD, _PD)
+    sig("orc_adm_metric", None, _D, _D, _D, _D, _PD)
+    sig("orc_adm_metric_derivs", None, _D, _D, _D, _D, _PD)
+    sig("orc_invert4", None, _PD, _PD)
+    sig("orc_rhs_adm", None, _D, _D, _PD, _PD)
+    sig("orc_hamiltonian_adm", _D, _D, _D, _PD)
+    sig("orc_rk4_step_adm", None, _D, _D, _D, _PD)
     sig("orc_rk4_linear_test", None, _D, _D, ctypes.c_int, _PD)
     sig("orc_rk4_step", None, _D, _D, _D, _PD)
     sig("orc_rk4_step_hamiltonian", None, _D, _D, _D, _PD)
@@ -124,7 +131,8 @@ def _vp(a):
 
 
 def make_term(eps_hor=0.01, r_esc=1e30, n_steps_cap=1000, dl=0.01, dl_r_scale=0.0, form=0) -> Term:
-    """form 0: geodesic equation (eq. geo); 1: canonical equations (eq. Ham)."""
+    """form 0: geodesic equation (eq. geo); 1: canonical equations (eq. Ham)
+    with g of eq. kerr; 2: the same equations with g from eq. ADM."""
     return Term(float(eps_hor), float(r_esc), int(n_steps_cap), float(dl), float(dl_r_scale), int(form))
 
 
@@ -164,6 +172,32 @@ def adm(M, a, r, th):
     return al.value, be.value, ga
 
 
+def adm_derivs(M, a, r, th):
+    """(d alpha, d beta^phi, d gamma_ii) along (r, theta): shapes (2,), (2,), (3, 2)."""
+    da, db, dg = np.zeros(2), np.zeros(2), np.zeros(6)
+    lib().orc_adm_derivs(M, a, r, th, _p(da), _p(db), _p(dg))
+    return da, db, dg.reshape(3, 2)
+
+
+def adm_metric(M, a, r, th):
+    g = np.zeros(16)
+    lib().orc_adm_metric(M, a, r, th, _p(g))
+    return g.reshape(4, 4)
+
+
+def adm_metric_derivs(M, a, r, th):
+    d = np.zeros(64)
+    lib().orc_adm_metric_derivs(M, a, r, th, _p(d))
+    return d.reshape(4, 4, 4)
+
+
+def invert4(A):
+    A = np.ascontiguousarray(A, dtype=np.float64).reshape(16)
+    Ai = np.zeros(16)
+    lib().orc_invert4(_p(A), _p(Ai))
+    return Ai.reshape(4, 4)
+
+
 # ---------------------------------------------------------------- dynamics
 def rhs(M, a, y):
     y = np.ascontiguousarray(y, dtype=np.float64)
@@ -177,6 +211,24 @@ def rhs_hamiltonian(M, a, z):
     f = np.zeros(8)
     lib().orc_rhs_hamiltonian(M, a, _p(z), _p(f))
     return f
+
+
+def rhs_adm(M, a, z):
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    f = np.zeros(8)
+    lib().orc_rhs_adm(M, a, _p(z), _p(f))
+    return f
+
+
+def hamiltonian_adm(M, a, z):
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    return lib().orc_hamiltonian_adm(M, a, _p(z))
+
+
+def rk4_step_adm(M, a, h, z):
+    z = np.array(z, dtype=np.float64)
+    lib().orc_rk4_step_adm(M, a, h, _p(z))
+    return z
 
 
 def rk4_linear(lam, h, nsteps, y0):

@@ -145,6 +145,141 @@ void orc_adm(double M, double a, double r, double th, double* alpha, double* bet
   gamma[2] = Sigma * s * s / rho2;
 }
 
+/* Partial derivatives of the ADM quantities of Kerr along r (k = 0) and
+ * theta (k = 1), by the chain and quotient rules on the expressions of
+ * orc_adm.  dgamma[i * 2 + k] = d gamma_ii / d x^k for i = rr, thth, phph. */
+void orc_adm_derivs(double M, double a, double r, double th, double dalpha[2], double dbeta_phi[2],
+                    double dgamma[6]) {
+  double s = sin(th), c = cos(th);
+  double rho2 = r * r + a * a * c * c;
+  double Delta = r * r - 2.0 * M * r + a * a;
+  double Sigma = (r * r + a * a) * (r * r + a * a) - a * a * Delta * s * s;
+  double alpha = sqrt(rho2 * Delta / Sigma);
+  double drho2[2] = {2.0 * r, -2.0 * a * a * s * c};
+  double dDelta[2] = {2.0 * r - 2.0 * M, 0.0};
+  double dSigma[2] = {4.0 * r * (r * r + a * a) - a * a * dDelta[0] * s * s,
+                      -a * a * Delta * 2.0 * s * c};
+  double ds2[2] = {0.0, 2.0 * s * c};
+  double dr[2] = {1.0, 0.0};
+  for (int k = 0; k < 2; ++k) {
+    /* alpha^2 = N / Sigma with N = rho^2 Delta; d alpha = d(alpha^2) / (2 alpha) */
+    double N = rho2 * Delta, dN = drho2[k] * Delta + rho2 * dDelta[k];
+    double dalpha2 = (dN * Sigma - N * dSigma[k]) / (Sigma * Sigma);
+    dalpha[k] = dalpha2 / (2.0 * alpha);
+    /* beta^phi = -2 M a r / Sigma */
+    dbeta_phi[k] = (-2.0 * M * a * dr[k] * Sigma + 2.0 * M * a * r * dSigma[k]) / (Sigma * Sigma);
+    /* gamma_rr = rho^2 / Delta, gamma_thth = rho^2, gamma_phph = Sigma s^2 / rho^2 */
+    dgamma[0 * 2 + k] = (drho2[k] * Delta - rho2 * dDelta[k]) / (Delta * Delta);
+    dgamma[1 * 2 + k] = drho2[k];
+    dgamma[2 * 2 + k] = ((dSigma[k] * s * s + Sigma * ds2[k]) * rho2 - Sigma * s * s * drho2[k]) / (rho2 * rho2);
+  }
+}
+
+/* The 4-metric of the line element eq. ADM, for any lapse alpha, shift
+ * beta^i and spatial metric gamma_ij (gam row-major 3x3, spatial index
+ * i = 0, 1, 2 for x^1, x^2, x^3):
+ *   g_tt = -alpha^2 + gamma_ij beta^i beta^j,  g_ti = gamma_ij beta^j,
+ *   g_ij = gamma_ij. */
+static void adm_metric(double alpha, const double beta[3], const double gam[9], double g[16]) {
+  double bb = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) bb += gam[i * 3 + j] * beta[i] * beta[j];
+  g[IDX2(0, 0)] = -alpha * alpha + bb;
+  for (int i = 0; i < 3; ++i) {
+    double bi = 0.0;
+    for (int j = 0; j < 3; ++j) bi += gam[i * 3 + j] * beta[j];
+    g[IDX2(0, i + 1)] = bi;
+    g[IDX2(i + 1, 0)] = bi;
+    for (int j = 0; j < 3; ++j) g[IDX2(i + 1, j + 1)] = gam[i * 3 + j];
+  }
+}
+
+/* Its derivative along one coordinate, by the product rule on adm_metric. */
+static void adm_metric_deriv(double alpha, double dalpha, const double beta[3], const double dbeta[3],
+                             const double gam[9], const double dgam[9], double dg[16]) {
+  double dbb = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      dbb += dgam[i * 3 + j] * beta[i] * beta[j] + gam[i * 3 + j] * dbeta[i] * beta[j] +
+             gam[i * 3 + j] * beta[i] * dbeta[j];
+  dg[IDX2(0, 0)] = -2.0 * alpha * dalpha + dbb;
+  for (int i = 0; i < 3; ++i) {
+    double dbi = 0.0;
+    for (int j = 0; j < 3; ++j) dbi += dgam[i * 3 + j] * beta[j] + gam[i * 3 + j] * dbeta[j];
+    dg[IDX2(0, i + 1)] = dbi;
+    dg[IDX2(i + 1, 0)] = dbi;
+    for (int j = 0; j < 3; ++j) dg[IDX2(i + 1, j + 1)] = dgam[i * 3 + j];
+  }
+}
+
+/* Kerr's lapse, shift and 3-metric (orc_adm, orc_adm_derivs) as full 3-vectors
+ * and 3x3 matrices, with their derivatives along all four coordinates
+ * (d/dt and d/dphi vanish: the metric is stationary and axisymmetric). */
+static void kerr_adm_full(double M, double a, double r, double th, double* alpha, double dalpha[4],
+                          double beta[3], double dbeta[12], double gam[9], double dgam[36]) {
+  double bphi, gd[3], da[2], db[2], dgd[6];
+  orc_adm(M, a, r, th, alpha, &bphi, gd);
+  orc_adm_derivs(M, a, r, th, da, db, dgd);
+  memset(dalpha, 0, 4 * sizeof(double));
+  memset(beta, 0, 3 * sizeof(double));
+  memset(dbeta, 0, 12 * sizeof(double));
+  memset(gam, 0, 9 * sizeof(double));
+  memset(dgam, 0, 36 * sizeof(double));
+  beta[2] = bphi;
+  for (int i = 0; i < 3; ++i) gam[i * 3 + i] = gd[i];
+  for (int k = 0; k < 2; ++k) {
+    int s = k + 1; /* coordinate index: r = 1, theta = 2 */
+    dalpha[s] = da[k];
+    dbeta[s * 3 + 2] = db[k];
+    for (int i = 0; i < 3; ++i) dgam[s * 9 + i * 3 + i] = dgd[i * 2 + k];
+  }
+}
+
+/* Kerr's 4-metric and its derivatives assembled from the ADM quantities
+ * (a different route to orc_metric and orc_metric_derivs). */
+void orc_adm_metric(double M, double a, double r, double th, double g[16]) {
+  double alpha, dalpha[4], beta[3], dbeta[12], gam[9], dgam[36];
+  kerr_adm_full(M, a, r, th, &alpha, dalpha, beta, dbeta, gam, dgam);
+  adm_metric(alpha, beta, gam, g);
+}
+
+void orc_adm_metric_derivs(double M, double a, double r, double th, double dg[64]) {
+  double alpha, dalpha[4], beta[3], dbeta[12], gam[9], dgam[36];
+  kerr_adm_full(M, a, r, th, &alpha, dalpha, beta, dbeta, gam, dgam);
+  for (int s = 0; s < 4; ++s)
+    adm_metric_deriv(alpha, dalpha[s], beta, dbeta + s * 3, gam, dgam + s * 9, dg + s * 16);
+}
+
+/* Inverse of a 4x4 matrix by Gauss-Jordan elimination with partial pivoting. */
+void orc_invert4(const double A[16], double Ai[16]) {
+  double w[4][8];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      w[i][j] = A[IDX2(i, j)];
+      w[i][4 + j] = (i == j) ? 1.0 : 0.0;
+    }
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+    for (int i = col + 1; i < 4; ++i)
+      if (fabs(w[i][col]) > fabs(w[piv][col])) piv = i;
+    if (piv != col)
+      for (int j = 0; j < 8; ++j) {
+        double t = w[col][j];
+        w[col][j] = w[piv][j];
+        w[piv][j] = t;
+      }
+    double d = w[col][col];
+    for (int j = 0; j < 8; ++j) w[col][j] /= d;
+    for (int i = 0; i < 4; ++i) {
+      if (i == col) continue;
+      double f = w[i][col];
+      for (int j = 0; j < 8; ++j) w[i][j] -= f * w[col][j];
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) Ai[IDX2(i, j)] = w[i][4 + j];
+}
+
 /* ------------------------------------------------------------------------ */
 /* equations of motion                                                       */
 /* ------------------------------------------------------------------------ */
@@ -191,6 +326,49 @@ void orc_rhs_hamiltonian(double M, double a, const double z[8], double f[8]) {
   }
 }
 
+/* The canonical equations (Sec. 2, eq. Ham) with the metric of the 3+1 line
+ * element eq. ADM: g_{mn} and d_s g_{mn} are assembled from Kerr's lapse,
+ * shift and 3-metric and their derivatives (orc_adm, orc_adm_derivs), g^{mn}
+ * is their numerical 4x4 inverse; then, as in orc_rhs_hamiltonian,
+ *   dx^m/dl = g^{mn} p_n,  dp_s/dl = 1/2 g^{am} (d_s g_{mn}) g^{nb} p_a p_b. */
+void orc_rhs_adm(double M, double a, const double z[8], double f[8]) {
+  double alpha, dalpha[4], beta[3], dbeta[12], gam[9], dgam[36];
+  double g[16], gi[16];
+  kerr_adm_full(M, a, z[1], z[2], &alpha, dalpha, beta, dbeta, gam, dgam);
+  adm_metric(alpha, beta, gam, g);
+  orc_invert4(g, gi);
+  for (int m = 0; m < 4; ++m) {
+    double acc = 0.0;
+    for (int n = 0; n < 4; ++n) acc += gi[IDX2(m, n)] * z[4 + n];
+    f[m] = acc;
+  }
+  for (int s = 0; s < 4; ++s) {
+    double dg[16];
+    adm_metric_deriv(alpha, dalpha[s], beta, dbeta + s * 3, gam, dgam + s * 9, dg);
+    double acc = 0.0;
+    for (int al = 0; al < 4; ++al)
+      for (int be = 0; be < 4; ++be) {
+        double dgi = 0.0;
+        for (int m = 0; m < 4; ++m)
+          for (int n = 0; n < 4; ++n) dgi -= gi[IDX2(al, m)] * dg[IDX2(m, n)] * gi[IDX2(n, be)];
+        acc += dgi * z[4 + al] * z[4 + be];
+      }
+    f[4 + s] = -0.5 * acc;
+  }
+}
+
+/* H = 1/2 g^{mn} p_m p_n with g from eq. ADM (a test handle: its finite
+ * differences must reproduce orc_rhs_adm). */
+double orc_hamiltonian_adm(double M, double a, const double z[8]) {
+  double g[16], gi[16];
+  orc_adm_metric(M, a, z[1], z[2], g);
+  orc_invert4(g, gi);
+  double H = 0.0;
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) H += 0.5 * gi[IDX2(m, n)] * z[4 + m] * z[4 + n];
+  return H;
+}
+
 typedef void (*orc_rhs_fn)(const void* ctx, const double* y, double* f);
 
 /* One classical RK4 step of size h on a dim-dimensional system.  If
@@ -222,6 +400,10 @@ static void ham_fn(const void* ctx, const double* y, double* f) {
   const orc_bh* bh = (const orc_bh*)ctx;
   orc_rhs_hamiltonian(bh->M, bh->a, y, f);
 }
+static void adm_fn(const void* ctx, const double* y, double* f) {
+  const orc_bh* bh = (const orc_bh*)ctx;
+  orc_rhs_adm(bh->M, bh->a, y, f);
+}
 static void lin_fn(const void* ctx, const double* y, double* f) { f[0] = *(const double*)ctx * y[0]; }
 
 void orc_rk4_linear_test(double lam, double h, int nsteps, double* y) {
@@ -234,6 +416,10 @@ void orc_rk4_step(double M, double a, double h, double y[8]) {
 void orc_rk4_step_hamiltonian(double M, double a, double h, double z[8]) {
   orc_bh bh = {M, a};
   rk4_generic(ham_fn, &bh, 8, h, z, 1, NULL);
+}
+void orc_rk4_step_adm(double M, double a, double h, double z[8]) {
+  orc_bh bh = {M, a};
+  rk4_generic(adm_fn, &bh, 8, h, z, 1, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -255,10 +441,17 @@ static int all_finite(const double y[8]) {
  * is fixed (dl) or dl_r_scale * r at the start of the step, held for all four
  * stages.  traj (optional) receives sample k (k*stride steps) at
  * traj[k*8 ...]; samples after termination are NaN. */
-/* (x, p) -> (x, u): u^m = g^{mn} p_n. */
-static void canonical_to_state(double M, double a, const double z[8], double y[8]) {
+/* (x, p) -> (x, u): u^m = g^{mn} p_n, with g^{mn} of eq. kerr (form 1) or the
+ * inverse of the eq. ADM metric (form 2). */
+static void canonical_to_state(double M, double a, int form, const double z[8], double y[8]) {
   double gi[16];
-  orc_inverse_metric(M, a, z[1], z[2], gi);
+  if (form == 2) {
+    double g[16];
+    orc_adm_metric(M, a, z[1], z[2], g);
+    orc_invert4(g, gi);
+  } else {
+    orc_inverse_metric(M, a, z[1], z[2], gi);
+  }
   for (int m = 0; m < 4; ++m) {
     double acc = 0.0;
     for (int n = 0; n < 4; ++n) acc += gi[IDX2(m, n)] * z[4 + n];
@@ -275,24 +468,35 @@ int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, dou
   uint32_t n = 0;
   double lam = 0.0;
   /* the integrated state: (x, u), or (x, p) with p = g u in the canonical
-   * form; inputs, samples and the result are (x, u) in both */
-  const int canonical = t->form == 1;
+   * forms (1: g of eq. kerr, 2: g of eq. ADM); inputs, samples and the
+   * result are (x, u) in all three */
+  const int form = (int)t->form;
+  const int canonical = form == 1 || form == 2;
+  orc_rhs_fn rhs = form == 2 ? adm_fn : (form == 1 ? ham_fn : geo_fn);
   double z[8];
   memcpy(y, y0, 8 * sizeof(double));
   memcpy(z, y0, 8 * sizeof(double));
-  if (canonical) orc_state_to_momenta(M, a, y0, z + 4);
+  if (form == 1) orc_state_to_momenta(M, a, y0, z + 4);
+  if (form == 2) {
+    double g[16];
+    orc_adm_metric(M, a, y0[1], y0[2], g);
+    for (int m = 0; m < 4; ++m) {
+      z[4 + m] = 0.0;
+      for (int n = 0; n < 4; ++n) z[4 + m] += g[IDX2(m, n)] * y0[4 + n];
+    }
+  }
   if (ns) memcpy(traj, y, 8 * sizeof(double));
   orc_bh bh = {M, a};
   while (n < t->n_steps_cap) {
     double h = (t->dl_r_scale > 0.0) ? t->dl_r_scale * z[1] : t->dl;
     double r_stage_min;
-    rk4_generic(canonical ? ham_fn : geo_fn, &bh, 8, h, z, 1, &r_stage_min);
+    rk4_generic(rhs, &bh, 8, h, z, 1, &r_stage_min);
     lam += h;
     ++n;
     if (ns && n % stride == 0) {
       double* s = traj + (size_t)(n / stride) * 8;
       if (canonical)
-        canonical_to_state(M, a, z, s);
+        canonical_to_state(M, a, form, z, s);
       else
         memcpy(s, z, 8 * sizeof(double));
     }
@@ -301,7 +505,7 @@ int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, dou
     if (z[1] >= t->r_esc) { fate = ORC_FATE_ESCAPED; break; }
   }
   if (canonical)
-    canonical_to_state(M, a, z, y);
+    canonical_to_state(M, a, form, z, y);
   else
     memcpy(y, z, 8 * sizeof(double));
   if (ns)

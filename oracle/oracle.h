@@ -40,7 +40,10 @@ typedef struct {
   double dl;           /* fixed step, used when dl_r_scale == 0 */
   double dl_r_scale;   /* if > 0: h_n = dl_r_scale * r_n (r at the step start) */
   uint32_t form;       /* 0: the geodesic equation in (x, u) (Sec. 2, eq. geo);
-                          1: the canonical equations in (x, p) (Sec. 2, eq. Ham) */
+                          1: the canonical equations in (x, p) (Sec. 2, eq. Ham)
+                             with g of eq. kerr;
+                          2: the same equations with g built from the lapse,
+                             shift and 3-metric of eq. ADM */
 } orc_term;
 
 /* -------- geometry (Sec. 2, eq. kerr) -------- */
@@ -50,13 +53,24 @@ void orc_metric_derivs(double M, double a, double r, double th, double dg[64]);
 void orc_inverse_metric(double M, double a, double r, double th, double gi[16]);
 void orc_christoffel(double M, double a, double r, double th, double G[64]);
 void orc_adm(double M, double a, double r, double th, double* alpha, double* beta_phi, double gamma[3]);
+/* d/dr (k = 0) and d/dtheta (k = 1) of alpha, beta^phi and gamma_ii
+ * (dgamma[i * 2 + k], i = rr, thth, phph) */
+void orc_adm_derivs(double M, double a, double r, double th, double dalpha[2], double dbeta_phi[2],
+                    double dgamma[6]);
+/* g_{mn} and d_s g_{mn} assembled from the ADM quantities (eq. ADM) */
+void orc_adm_metric(double M, double a, double r, double th, double g[16]);
+void orc_adm_metric_derivs(double M, double a, double r, double th, double dg[64]);
+void orc_invert4(const double A[16], double Ai[16]);  /* Gauss-Jordan, partial pivoting */
 
 /* -------- equations of motion -------- */
 void orc_rhs(double M, double a, const double y[8], double f[8]);          /* geodesic eq., Christoffel form */
 void orc_rhs_hamiltonian(double M, double a, const double z[8], double f[8]); /* eq. Ham, state (x^mu, p_mu) */
+void orc_rhs_adm(double M, double a, const double z[8], double f[8]);         /* eq. Ham with g from eq. ADM */
+double orc_hamiltonian_adm(double M, double a, const double z[8]);          /* H = g^{mn} p_m p_n / 2 */
 void orc_rk4_linear_test(double lam, double h, int nsteps, double* y);   /* RK4 on y' = lam*y */
 void orc_rk4_step(double M, double a, double h, double y[8]);
 void orc_rk4_step_hamiltonian(double M, double a, double h, double z[8]);
+void orc_rk4_step_adm(double M, double a, double h, double z[8]);
 
 /* -------- integration with termination (Sec. 5) -------- */
 int orc_trace_one(double M, double a, const double y0[8], const orc_term* t,

@@ -811,3 +811,131 @@ def test_canonical_circular_orbit_stays_closed(orc):
         assert abs(res["y"][1] - r0) < 1e-9
         om = y0[7] / y0[4]
         assert res["y"][3] == pytest.approx(om * res["y"][0], rel=1e-10)
+
+
+# --------------------------------------------------------------------------- 3+1 form (eq. ADM)
+def _fd4(f, x, h):
+    """Fourth-order central difference of f at x."""
+    return (-f(x + 2 * h) + 8 * f(x + h) - 8 * f(x - h) + f(x - 2 * h)) / (12 * h)
+
+
+def test_adm_derivatives_match_finite_differences(orc):
+    """Sec. 2: the r- and theta-derivatives of Kerr's lapse, shift and
+    3-metric (the expressions after eq. coord) against fourth-order finite
+    differences of the values themselves."""
+    r_ = rng(21)
+    for _ in range(40):
+        a = r_.uniform(0.0, 0.999)
+        r = r_.uniform(2.2, 40.0)
+        th = r_.uniform(0.1, math.pi - 0.1)
+        da, db, dg = orc.adm_derivs(M1, a, r, th)
+
+        def vals(rr, tt):
+            al, be, ga = orc.adm(M1, a, rr, tt)
+            return np.concatenate([[al, be], ga])
+
+        fr = _fd4(lambda x: vals(x, th), r, 1e-3 * r)
+        ft = _fd4(lambda x: vals(r, x), th, 1e-3)
+        got_r = np.concatenate([[da[0], db[0]], dg[:, 0]])
+        got_t = np.concatenate([[da[1], db[1]], dg[:, 1]])
+        scale_r = np.abs(vals(r, th)) / r + 1e-12
+        scale_t = np.abs(vals(r, th)) + 1e-12
+        assert np.all(np.abs(got_r - fr) < 1e-7 * scale_r), (got_r, fr)
+        assert np.all(np.abs(got_t - ft) < 1e-7 * scale_t), (got_t, ft)
+
+
+def test_adm_assembled_metric_is_kerr(orc):
+    """Eq. ADM assembled from alpha, beta^i, gamma_ij (full sums over i, j)
+    reproduces eq. kerr and its analytic derivatives, which have their own
+    pins above."""
+    r_ = rng(22)
+    for _ in range(40):
+        a = r_.uniform(0.0, 0.999)
+        r = r_.uniform(2.2, 60.0)
+        th = r_.uniform(0.05, math.pi - 0.05)
+        g, ga = orc.metric(M1, a, r, th), orc.adm_metric(M1, a, r, th)
+        np.testing.assert_allclose(ga, g, rtol=1e-12, atol=1e-14 * np.abs(g).max())
+        d, dga = orc.metric_derivs(M1, a, r, th), orc.adm_metric_derivs(M1, a, r, th)
+        np.testing.assert_allclose(dga, d, rtol=1e-10, atol=1e-12 * np.abs(d).max())
+
+
+def test_invert4_matches_library_inverse(orc):
+    """The oracle's Gauss-Jordan inverse against numpy's LAPACK inverse, on
+    random matrices and on Kerr metrics (indefinite, with a zero pivot in
+    the unpivoted order at a = 0)."""
+    r_ = rng(23)
+    for _ in range(50):
+        A = r_.normal(size=(4, 4)) + 3 * np.eye(4)
+        np.testing.assert_allclose(orc.invert4(A), np.linalg.inv(A), rtol=1e-10, atol=1e-12)
+    for a in (0.0, 0.5, 0.99):
+        g = orc.metric(M1, a, 6.0, 1.1)
+        np.testing.assert_allclose(orc.invert4(g) @ g, np.eye(4), atol=1e-13)
+        np.testing.assert_allclose(orc.invert4(g), orc.inverse_metric(M1, a, 6.0, 1.1), rtol=1e-12, atol=1e-15)
+
+
+def _random_canonical(r_, a):
+    y = _random_state(r_, a)
+    return np.concatenate([y[:4], orc_momenta(a, y)]), y
+
+
+def orc_momenta(a, y):
+    import oracle
+
+    return oracle.state_to_momenta(M1, a, y)
+
+
+def test_adm_rhs_is_hamiltons_equations(orc):
+    """Sec. 2 eq. Ham taken literally: dx^mu/dl = dH/dp_mu and dp_mu/dl =
+    -dH/dx^mu, with H = g^{mn} p_m p_n / 2 differentiated numerically, match
+    the 3+1 right-hand side; and H at p = g u equals g(u, u) / 2."""
+    r_ = rng(24)
+    for _ in range(30):
+        a = r_.uniform(0.0, 0.999)
+        z, y = _random_canonical(r_, a)
+        f = orc.rhs_adm(M1, a, z)
+        g = orc.metric(M1, a, y[1], y[2])
+        assert orc.hamiltonian_adm(M1, a, z) == pytest.approx(0.5 * y[4:] @ g @ y[4:], rel=1e-10, abs=1e-12)
+        grad = np.zeros(8)
+        for k in range(8):
+            e = np.zeros(8)
+            hk = 1e-4 * max(1.0, abs(z[k]))
+            e[k] = 1.0
+            grad[k] = _fd4(lambda s: orc.hamiltonian_adm(M1, a, z + s * e), 0.0, hk)
+        np.testing.assert_allclose(f[:4], grad[4:], rtol=1e-7, atol=1e-9 * np.abs(grad[4:]).max())
+        np.testing.assert_allclose(f[4:], -grad[:4], rtol=1e-6, atol=1e-8 * np.abs(grad[:4]).max() + 1e-12)
+        assert f[4] == 0.0 and f[7] == 0.0
+
+
+def test_adm_rhs_equals_kerr_canonical_rhs(orc):
+    """The 3+1 route (g assembled from alpha, beta, gamma, numerically inverted)
+    and the BL route (closed-form inverse of eq. kerr) are the same equations."""
+    r_ = rng(25)
+    for _ in range(60):
+        a = r_.uniform(0.0, 0.999)
+        z, _ = _random_canonical(r_, a)
+        fa, fh = orc.rhs_adm(M1, a, z), orc.rhs_hamiltonian(M1, a, z)
+        np.testing.assert_allclose(fa, fh, rtol=1e-10, atol=1e-12 * np.abs(fh).max())
+
+
+def test_adm_trace_matches_canonical_and_conserves(orc):
+    """Form 2 (eq. Ham with g from eq. ADM) is the same discrete RK4 map as
+    form 1 up to rounding: traces agree closely, p_t and p_phi are exact
+    constants, and a circular orbit stays at r0 with phi advancing at eq.
+    omega's rate."""
+    ys, spins, _ = orc.bound_samples(1.0, 0.9, 11, np.arange(12), spin_fixed=True)
+    can = orc.make_term(n_steps_cap=3000, dl=0.25, form=1)
+    adm = orc.make_term(n_steps_cap=3000, dl=0.25, form=2)
+    for i in range(ys.shape[1]):
+        i0 = orc.invariants(1.0, 0.9, ys[:, i])
+        a = orc.trace_one(1.0, 0.9, ys[:, i], can)
+        b = orc.trace_one(1.0, 0.9, ys[:, i], adm)
+        assert a["fate"] == b["fate"] and a["steps"] == b["steps"]
+        scale = np.maximum(np.abs(a["y"]), 1.0)
+        assert np.all(np.abs(a["y"] - b["y"]) < 1e-7 * scale), (a["y"], b["y"])
+        if b["fate"] == 3:
+            assert np.abs(orc.invariants(1.0, 0.9, b["y"])[:2] - i0[:2]).max() < 1e-12
+    for a, r0 in ((0.0, 8.0), (0.7, 7.0)):
+        y0 = orc.circular_state(1.0, a, r0, 1)
+        res = orc.trace_one(1.0, a, y0, orc.make_term(n_steps_cap=5000, dl=0.02, form=2))
+        assert abs(res["y"][1] - r0) < 1e-9
+        assert res["y"][3] == pytest.approx(y0[7] / y0[4] * res["y"][0], rel=1e-10)
