@@ -49,9 +49,12 @@ def kernel_source_hash() -> str:
 # once): 120 per Kerr right-hand side of the geodesic form, 42 per
 # Schwarzschild one, 102 for the RK4 stage points and weighted sums; the
 # canonical form (eq. Ham): 72 per Kerr right-hand side, 74 for its RK4
-# (p_t, p_ph fixed).  Divisions and sincos are listed separately (4 each per
+# (p_t, p_ph fixed); the 3+1 form: 65 for Kerr's lapse, shift, 3-metric and
+# their logarithmic derivatives plus 34 for the 3+1 right-hand side, the same
+# 74 for its RK4.  Divisions and sincos are listed separately (4 each per
 # step).
-FLOPS_PER_STEP = {"kerr": 4 * 120 + 102, "schw": 4 * 42 + 102, "kerr_canonical": 4 * 72 + 74}
+FLOPS_PER_STEP = {"kerr": 4 * 120 + 102, "schw": 4 * 42 + 102, "kerr_canonical": 4 * 72 + 74,
+                  "kerr_adm": 4 * (65 + 34) + 74}
 DIV_PER_STEP, SINCOS_PER_STEP = 4, 4
 
 
@@ -251,9 +254,12 @@ def run_profile_case(args) -> None:
     _b.build()
     cw = W.camera(nx=512, ny=512)
     cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
-    prec = "fp64" if args.profile_case == "camera_fp64" else "fp32_mixed"
+    prec = "fp32_mixed" if args.profile_case.endswith("mixed") else "fp64"
+    form = {"camera_canonical": mb.FORM_HAMILTONIAN, "camera_adm": mb.FORM_ADM}.get(args.profile_case,
+                                                                                   mb.FORM_GEODESIC)
+    term = mb.term_from(cw.term, form=form)
     for _ in range(max(1, args.steps)):
-        res = mb.trace_camera(cw.M, cw.a, cam, cw.term, prec)
+        res = mb.trace_camera(cw.M, cw.a, cam, term, prec)
     torch.cuda.synchronize()
     steps = int(res["steps"].to(torch.int64).sum().item())
     print(json.dumps({"profile_case": args.profile_case, "rays": cw.n, "rk4_steps": steps}))
@@ -742,7 +748,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="malbec", choices=["malbec", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", choices=["camera_fp64", "camera_mixed"], default=None,
+    ap.add_argument("--profile-case", choices=["camera_fp64", "camera_mixed", "camera_canonical", "camera_adm"],
+                    default=None,
                     help="small case for ncu: a 512x512 render of the same camera, --steps times")
     ap.add_argument("--workload", choices=["camera", "bundles", "serving", "bound", "paper"], default="camera",
                     help="camera: the headline line (with a bundles and a serving sample); bundles: uneven "
@@ -818,49 +825,68 @@ def main():
         value = world * steps_per_render * args.steps / t_total
         ms_per_step = 1e3 * t_total / args.steps
 
-        # ---------------- FP64, canonical form (eq. Ham), same protocol
-        term_c = mb.term_from(cw.term, form=mb.FORM_HAMILTONIAN)
-        cwc = CameraRun(cw.M, cw.a, term_c)
-        for _ in range(args.warmup):
-            mb.trace_camera(cw.M, cw.a, cam, term_c, "fp64", stream=stream, out=out)
-        barrier()
-        torch.cuda.synchronize()
-        times_c, res_c = timed_renders(mb, cwc, cam, "fp64", args.steps, stream, flush, out=out)
-        torch.cuda.synchronize()
-        barrier()
-        steps_c = int(res_c["steps"].to(torch.int64).sum().item())
-        t_c = max_over_ranks(sum(times_c) / 1e3)
-        value_c = world * steps_c * args.steps / t_c
-        agree_c = float((res_c["fate"] == fate64).float().mean().item())
-        esc_c = (fate64 == mb.FATE_ESCAPED) & (res_c["fate"] == mb.FATE_ESCAPED)
-        dth_c = (res_c["theta"][esc_c] - theta64[esc_c]).abs()
-        dph_c = (res_c["phi"][esc_c] - phi64[esc_c]).abs()
-        dth_c, dph_c = dth_c[torch.isfinite(dth_c)], dph_c[torch.isfinite(dph_c)]
-        canonical = {"value": value_c, "unit": UNIT, "ms_per_step": 1e3 * t_c / args.steps,
-                     "speedup_vs_geodesic_form": value_c / value, "fate_agreement_vs_geodesic_form": agree_c,
-                     "escaped_difference_vs_geodesic_form": err_stats(torch, dth_c, dph_c),
-                     "roofline": {"bound": "alu", "peak": peak64, "unit": "GFLOP/s (FP64)",
-                                  "flops_per_rk4_step": FLOPS_PER_STEP["kerr_canonical"],
-                                  "achieved": FLOPS_PER_STEP["kerr_canonical"] * steps_c /
-                                  (statistics.mean(times_c) / 1e3) / 1e9,
-                                  "frac": FLOPS_PER_STEP["kerr_canonical"] * steps_c /
-                                  (statistics.mean(times_c) / 1e3) / 1e9 / peak64},
-                     "note": "RK4 on (x, p) with p = g u (Sec. 2, eq. Ham); same camera, inputs and outputs (x, u); "
-                             "the two forms are different discrete maps of the same flow"}
-        fate_c = res_c["fate"].clone()
-        for _ in range(args.warmup):
-            mb.trace_camera(cw.M, cw.a, cam, term_c, "fp32_mixed", stream=stream, out=out)
-        barrier()
-        torch.cuda.synchronize()
-        times_cm, res_cm = timed_renders(mb, cwc, cam, "fp32_mixed", args.steps, stream, flush, out=out)
-        torch.cuda.synchronize()
-        barrier()
-        steps_cm = int(res_cm["steps"].to(torch.int64).sum().item())
-        t_cm = max_over_ranks(sum(times_cm) / 1e3)
-        canonical["fp32_mixed"] = {"value": world * steps_cm * args.steps / t_cm, "unit": UNIT,
-                                   "ms_per_step": 1e3 * t_cm / args.steps,
-                                   "fate_agreement_vs_fp64_canonical": float((res_cm["fate"] == fate_c).float().mean()
-                                                                             .item())}
+        # ---------------- FP64 and FP32_MIXED, the canonical forms (eq. Ham with
+        # g of eq. kerr; with the 3+1 quantities of eq. ADM), same protocol
+        def canonical_arm(form, flops_key, note):
+            term_c = mb.term_from(cw.term, form=form)
+            cwc = CameraRun(cw.M, cw.a, term_c)
+            for _ in range(args.warmup):
+                mb.trace_camera(cw.M, cw.a, cam, term_c, "fp64", stream=stream, out=out)
+            barrier()
+            torch.cuda.synchronize()
+            times_c, res_c = timed_renders(mb, cwc, cam, "fp64", args.steps, stream, flush, out=out)
+            torch.cuda.synchronize()
+            barrier()
+            steps_c = int(res_c["steps"].to(torch.int64).sum().item())
+            t_c = max_over_ranks(sum(times_c) / 1e3)
+            value_c = world * steps_c * args.steps / t_c
+            agree_c = float((res_c["fate"] == fate64).float().mean().item())
+            esc_c = (fate64 == mb.FATE_ESCAPED) & (res_c["fate"] == mb.FATE_ESCAPED)
+            dth_c = (res_c["theta"][esc_c] - theta64[esc_c]).abs()
+            dph_c = (res_c["phi"][esc_c] - phi64[esc_c]).abs()
+            dth_c, dph_c = dth_c[torch.isfinite(dth_c)], dph_c[torch.isfinite(dph_c)]
+            fl = FLOPS_PER_STEP[flops_key]
+            arm = {"value": value_c, "unit": UNIT, "ms_per_step": 1e3 * t_c / args.steps,
+                   "speedup_vs_geodesic_form": value_c / value, "fate_agreement_vs_geodesic_form": agree_c,
+                   "escaped_difference_vs_geodesic_form": err_stats(torch, dth_c, dph_c),
+                   "roofline": {"bound": "alu", "peak": peak64, "unit": "GFLOP/s (FP64)",
+                                "flops_per_rk4_step": fl,
+                                "achieved": fl * steps_c / (statistics.mean(times_c) / 1e3) / 1e9,
+                                "frac": fl * steps_c / (statistics.mean(times_c) / 1e3) / 1e9 / peak64},
+                   "note": note}
+            fate_c, theta_c = res_c["fate"].clone(), res_c["theta"].clone()
+            for _ in range(args.warmup):
+                mb.trace_camera(cw.M, cw.a, cam, term_c, "fp32_mixed", stream=stream, out=out)
+            barrier()
+            torch.cuda.synchronize()
+            times_cm, res_cm = timed_renders(mb, cwc, cam, "fp32_mixed", args.steps, stream, flush, out=out)
+            torch.cuda.synchronize()
+            barrier()
+            steps_cm = int(res_cm["steps"].to(torch.int64).sum().item())
+            t_cm = max_over_ranks(sum(times_cm) / 1e3)
+            arm["fp32_mixed"] = {"value": world * steps_cm * args.steps / t_cm, "unit": UNIT,
+                                 "ms_per_step": 1e3 * t_cm / args.steps,
+                                 "fate_agreement_vs_fp64_same_form": float((res_cm["fate"] == fate_c).float().mean()
+                                                                           .item())}
+            return arm, fate_c, theta_c
+
+        canonical, fate_bl, theta_bl = canonical_arm(
+            mb.FORM_HAMILTONIAN, "kerr_canonical",
+            "RK4 on (x, p) with p = g u (Sec. 2, eq. Ham); same camera, inputs and outputs (x, u); "
+            "the geodesic and canonical forms are different discrete maps of the same flow")
+        adm_form, fate_adm, theta_adm = canonical_arm(
+            mb.FORM_ADM, "kerr_adm",
+            "eq. Ham with H through the lapse, shift and 3-metric of eq. ADM (Kerr's, from a provider "
+            "function of r, theta); the same discrete map as the canonical form up to rounding")
+        esc_b = (fate_bl == mb.FATE_ESCAPED) & (fate_adm == mb.FATE_ESCAPED)
+        d_b = (theta_adm[esc_b] - theta_bl[esc_b]).abs()
+        d_b = d_b[torch.isfinite(d_b)]
+        adm_form["vs_canonical_form"] = {
+            "speedup": adm_form["value"] / canonical["value"],
+            "fate_agreement": float((fate_adm == fate_bl).float().mean().item()),
+            "escaped_theta_difference": {"median": float(d_b.median().item()) if d_b.numel() else None,
+                                         "p99": float(torch.quantile(d_b[::16], 0.99).item()) if d_b.numel()
+                                         else None}}
 
         # ---------------- FP32_MIXED, same protocol
         for _ in range(args.warmup):
@@ -913,6 +939,7 @@ def main():
                 "note": "malbec_trace_camera + copy of the image (fate, steps, theta, phi) to pinned host memory; "
                         "the rays are built on the device from the camera description passed by value"},
         "canonical_form": canonical,
+        "adm_form": adm_form,
         "fp32_mixed": {"value": value32, "unit": UNIT, "ms_per_step": 1e3 * t32 / args.steps,
                        "speedup_vs_fp64": value32 / value, "fate_agreement_vs_fp64": agree,
                        "escaped_error_vs_fp64": err_stats(torch, dth, dph),

@@ -95,10 +95,21 @@ typedef struct {
  *                            (same FP64 zones); malbec_trace, malbec_trace_noalloc
  *                            and malbec_trace_camera only (MALBEC_EINVAL for
  *                            bundles and server jobs).
- * Inputs and outputs are (x, u) states in both forms; the two discrete maps
- * agree to O(h^4) per unit lambda. */
+ *   MALBEC_FORM_ADM          (2) the same canonical equations with H written
+ *                            through the lapse alpha, shift beta^ph and
+ *                            spatial metric gamma_ij of the 3+1 line element
+ *                            (Sec. 2, eq. ADM; Kerr's alpha, beta, gamma as
+ *                            the paper gives them after eq. coord) and their
+ *                            r- and theta-derivatives.  The right-hand side
+ *                            holds for any stationary, axisymmetric, circular
+ *                            metric; Kerr is the metric supplied.  Same entry
+ *                            points and precisions as form 1; the same flow,
+ *                            so its RK4 map equals form 1's up to rounding.
+ * Inputs and outputs are (x, u) states in every form; the geodesic and the
+ * canonical maps agree to O(h^4) per unit lambda. */
 #define MALBEC_FORM_GEODESIC 0
 #define MALBEC_FORM_HAMILTONIAN 1
+#define MALBEC_FORM_ADM 2
 typedef struct {
   double eps_hor;
   double r_esc;

@@ -33,7 +33,8 @@ int check_metric(const malbec_metric& m) {
 // escape radius must clear that worst case.
 int check_term(const malbec_term& t, const malbec_metric& m) {
   if (!isfinite(t.eps_hor) || t.eps_hor < 0.0) return MALBEC_EINVAL;
-  if (t.form != MALBEC_FORM_GEODESIC && t.form != MALBEC_FORM_HAMILTONIAN) return MALBEC_EINVAL;
+  if (t.form != MALBEC_FORM_GEODESIC && t.form != MALBEC_FORM_HAMILTONIAN && t.form != MALBEC_FORM_ADM)
+    return MALBEC_EINVAL;
   const bool scaled = t.dl_r_scale != 0.0;
   if (scaled && !finite_pos(t.dl_r_scale)) return MALBEC_EINVAL;
   if (!scaled && !finite_pos(t.dl)) return MALBEC_EINVAL;

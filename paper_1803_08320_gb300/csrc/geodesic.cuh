@@ -238,10 +238,150 @@ __device__ __forceinline__ void ham_kerr(const BH<T>& bh, T r, T th, T pt, T pr,
   f[5] = mh * fma(T(2) * a2 * sc * F, irho2, dFth);
 }
 
+// ---------------------------------------------------------------------------
+// 3+1 form (Sec. 2, eq. ADM and the free-particle Lagrangian, then eq. Ham):
+// the same canonical state z = (x^mu, p_mu), with H written through the lapse
+// alpha, the shift beta^i and the spatial metric gamma_ij instead of
+// g^{mu nu} of eq. kerr.  The right-hand side below holds for any
+// stationary, axisymmetric, circular spacetime: every function depends on r
+// and theta only, beta^i = (0, 0, beta^ph) and gamma_ij is diagonal.  Kerr in
+// BL coordinates (Sec. 2, the comparison of eq. ADM with eq. kerr) is one
+// such metric; numerically computed metrics of rotating compact objects are
+// others.  A metric enters only through an Adm<T> point filled by a provider
+// function of (r, theta).  With A = p_t - beta^ph p_ph,
+//   H = -A^2 / (2 alpha^2) + (p_r^2/g_rr + p_th^2/g_thth + p_ph^2/g_phph) / 2
+// (g_ii standing for gamma_ii), so
+//   dt/dl = -A/alpha^2,  dr/dl = p_r/g_rr,  dth/dl = p_th/g_thth,
+//   dph/dl = p_ph/g_phph + beta^ph A/alpha^2,
+//   dp_k/dl = -(A/alpha^2) (p_ph d_k beta^ph + A d_k ln alpha)
+//             + 1/2 sum_i (p_i^2/g_ii) d_k ln g_ii        (k = r, theta),
+// and p_t, p_ph are constant.
+enum HamForm { kHamKerrBL = 1, kHamAdm = 2 };
+
+template <typename T>
+struct Adm {
+  T alpha2, beta, gam[3];  // alpha^2, beta^ph, gamma_rr, gamma_thth, gamma_phph
+  T ialpha2, igam[3];      // 1/alpha^2, 1/gamma_ii
+  T dlna[2];               // d_r ln alpha, d_th ln alpha
+  T dbeta[2];              // d_r beta^ph, d_th beta^ph
+  T dlng[3][2];            // d_k ln gamma_ii
+};
+
+// Provider: Kerr's lapse, shift and 3-metric in BL coordinates,
+//   alpha^2 = rho^2 Delta / Sigma, beta^ph = -2 M a r / Sigma,
+//   gamma = diag(rho^2/Delta, rho^2, Sigma sin^2 / rho^2),
+// with the logarithmic derivatives of rho^2, Delta, Sigma (d_r rho^2 = 2r,
+// d_th rho^2 = -2 a^2 s c, d_r Delta = 2(r - M), d_r Sigma = 4 r (r^2 + a^2)
+// - a^2 s^2 d_r Delta, d_th Sigma = -2 a^2 Delta s c).  FP64 shares one
+// division among 1/rho^2, 1/Delta, 1/Sigma and 1/sin^2; FP32 takes 1/Sigma
+// apart (the product of all four would overflow near r = 10^4).
+template <typename T>
+__device__ __forceinline__ void adm_kerr(const BH<T>& bh, T r, T th, Adm<T>& m) {
+  T s, c;
+  Trig<T>::sc(th, &s, &c);
+  const T a2 = bh.a2;
+  const T s2 = s * s, sc = s * c;
+  const T rho2 = fma(a2, c * c, r * r);
+  const T Delta = fma(r, r - bh.twoM, a2);
+  const T r2a2 = fma(r, r, a2);
+  const T Sigma = fma(r2a2, r2a2, -(a2 * Delta) * s2);
+  const T rD = rho2 * Delta;
+  T irho2, iDelta, iSigma, is2;
+  if constexpr (sizeof(T) == 8) {
+    const T SS = Sigma * s2;
+    const T inv = T(1) / (rD * SS);
+    irho2 = Delta * SS * inv;
+    iDelta = rho2 * SS * inv;
+    iSigma = rD * s2 * inv;
+    is2 = rD * Sigma * inv;
+  } else {
+    const T inv = T(1) / (rD * s2);
+    irho2 = Delta * s2 * inv;
+    iDelta = rho2 * s2 * inv;
+    is2 = rD * inv;
+    iSigma = T(1) / Sigma;
+  }
+  m.alpha2 = rD * iSigma;
+  m.ialpha2 = Sigma * irho2 * iDelta;
+  m.beta = -bh.twoM * bh.a * r * iSigma;
+  m.gam[0] = rho2 * iDelta;
+  m.gam[1] = rho2;
+  m.gam[2] = Sigma * s2 * irho2;
+  m.igam[0] = Delta * irho2;
+  m.igam[1] = irho2;
+  m.igam[2] = rho2 * iSigma * is2;
+  const T a2sc2 = T(2) * a2 * sc;
+  const T lrho_r = T(2) * r * irho2, lrho_t = -a2sc2 * irho2;
+  const T dDr = T(2) * (r - bh.M);
+  const T lD_r = dDr * iDelta;
+  const T lS_r = fma(T(4) * r, r2a2, -(a2 * s2) * dDr) * iSigma;
+  const T lS_t = -a2sc2 * Delta * iSigma;
+  m.dlna[0] = T(0.5) * (lrho_r + lD_r - lS_r);
+  m.dlna[1] = T(0.5) * (lrho_t - lS_t);
+  m.dbeta[0] = fma(-m.beta, lS_r, -bh.twoM * bh.a * iSigma);
+  m.dbeta[1] = -m.beta * lS_t;
+  m.dlng[0][0] = lrho_r - lD_r;
+  m.dlng[0][1] = lrho_t;
+  m.dlng[1][0] = lrho_r;
+  m.dlng[1][1] = lrho_t;
+  m.dlng[2][0] = lS_r - lrho_r;
+  m.dlng[2][1] = fma(T(2) * sc, is2, lS_t - lrho_t);
+}
+
+// The 3+1 right-hand side f = (dt, dr, dth, dph, dp_r, dp_th)/dl at one
+// point of any provider (formulas above).
+template <typename T>
+__device__ __forceinline__ void adm_rhs(const Adm<T>& m, T pt, T pr, T pth, T pph, T f[6]) {
+  const T A = fma(-m.beta, pph, pt);
+  const T u = A * m.ialpha2;
+  const T vr = pr * m.igam[0], vth = pth * m.igam[1], vph = pph * m.igam[2];
+  f[0] = -u;
+  f[1] = vr;
+  f[2] = vth;
+  f[3] = fma(m.beta, u, vph);
+  const T qr = T(0.5) * pr * vr, qth = T(0.5) * pth * vth, qph = T(0.5) * pph * vph;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const T kin = fma(qph, m.dlng[2][k], fma(qth, m.dlng[1][k], qr * m.dlng[0][k]));
+    f[4 + k] = fma(-u, fma(pph, m.dbeta[k], A * m.dlna[k]), kin);
+  }
+}
+
+// The canonical right-hand side of one form: eq. Ham through g^{mu nu} of
+// eq. kerr (kHamKerrBL) or through the 3+1 quantities of Kerr (kHamAdm).
+template <int kForm, typename T>
+__device__ __forceinline__ void ham_rhs(const BH<T>& bh, T r, T th, T pt, T pr, T pth, T pph, T f[6]) {
+  if constexpr (kForm == kHamAdm) {
+    Adm<T> m;
+    adm_kerr<T>(bh, r, th, m);
+    adm_rhs<T>(m, pt, pr, pth, pph, f);
+  } else {
+    ham_kerr<T>(bh, r, th, pt, pr, pth, pph, f);
+  }
+}
+
+// p_mu = g_{mu nu} u^nu from the 3+1 quantities: g_tt = -alpha^2 +
+// gamma_phph beta^2, g_tph = gamma_phph beta, g_ii = gamma_ii.
+__device__ __forceinline__ void adm_lower(const Adm<double>& m, const double u[4], double p[4]) {
+  const double w = m.gam[2] * fma(m.beta, u[0], u[3]);  // gamma_phph (beta u^t + u^ph)
+  p[0] = fma(-m.alpha2, u[0], m.beta * w);
+  p[1] = m.gam[0] * u[1];
+  p[2] = m.gam[1] * u[2];
+  p[3] = w;
+}
+
+// u^mu = g^{mu nu} p_nu from the 3+1 quantities (the first half of adm_rhs).
+__device__ __forceinline__ void adm_raise(const Adm<double>& m, const double p[4], double u[4]) {
+  double f[6];
+  adm_rhs<double>(m, p[0], p[1], p[2], p[3], f);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u[j] = f[j];
+}
+
 // One classical RK4 step of the canonical state z (same tableau and the same
 // stage-by-stage sums as rk4_step); p_t = z[4] and p_ph = z[7] stay fixed.
 // Returns the smallest radius among the three intermediate stage points.
-template <typename T, bool kRolled = false>
+template <typename T, bool kRolled = false, int kForm = kHamKerrBL>
 __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
   const T hh = T(0.5) * h;
   T r = z[1], th = z[2], pr = z[5], pth = z[6];
@@ -249,7 +389,7 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
   T rmin = T(0);
   auto stage = [&](int s) {
     T f[6];
-    ham_kerr<T>(bh, r, th, z[4], pr, pth, z[7], f);
+    ham_rhs<kForm, T>(bh, r, th, z[4], pr, pth, z[7], f);
     if (s == 0) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) sx[j] = f[j];

@@ -155,9 +155,10 @@ __device__ __forceinline__ float rk4_step_mixed(const BH<float>& bh, float hf, f
   return rmin;
 }
 
-// The canonical form of rk4_step_mixed: z = (x, p) as compensated pairs,
+// The canonical forms of rk4_step_mixed: z = (x, p) as compensated pairs,
 // p_t = z[4] and p_ph = z[7] fixed (their float hi words enter the right-hand
 // side); t, r, theta, phi, p_r, p_theta are integrated.
+template <int kForm>
 __device__ __forceinline__ float rk4_step_mixed_ham(const BH<float>& bh, float hf, float h6h, float h6l, float hi[8],
                                                     float lo[8]) {
   const float hh = 0.5f * hf;
@@ -167,7 +168,7 @@ __device__ __forceinline__ float rk4_step_mixed_ham(const BH<float>& bh, float h
 #pragma unroll 1
   for (int s = 0; s < 4; ++s) {
     float f[6];
-    ham_kerr<float>(bh, r, th, hi[4], pr, pth, hi[7], f);
+    ham_rhs<kForm, float>(bh, r, th, hi[4], pr, pth, hi[7], f);
     if (s == 0) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) sx[j] = f[j];
@@ -337,14 +338,41 @@ __device__ __forceinline__ unsigned nsmid() {
 constexpr unsigned long long kZoneWarpWaitNs = 600ull * 1000000000ull;
 
 // Launch bounds: at most kMaxTPB threads, one block per SM guaranteed.  The
+static_assert(kHamKerrBL == MALBEC_FORM_HAMILTONIAN && kHamAdm == MALBEC_FORM_ADM, "form codes");
+
+// (x, u) -> (x, p): p = g u, with g of eq. kerr or of the 3+1 quantities.
+template <int kForm>
+__device__ __forceinline__ void to_momenta(double M, double a, const double y[8], double p[4]) {
+  if constexpr (kForm == kHamAdm) {
+    Adm<double> m;
+    adm_kerr<double>(make_bh<double>(M, a), y[1], y[2], m);
+    adm_lower(m, y + 4, p);
+  } else {
+    lower_velocity(M, a, y, p);
+  }
+}
+
+// (x, p) -> u = g^{-1} p, the inverse of to_momenta.
+template <int kForm>
+__device__ __forceinline__ void to_velocity(double M, double a, const double z[8], double u[4]) {
+  if constexpr (kForm == kHamAdm) {
+    Adm<double> m;
+    adm_kerr<double>(make_bh<double>(M, a), z[1], z[2], m);
+    adm_raise(m, z + 4, u);
+  } else {
+    raise_momentum(M, a, z, u);
+  }
+}
+
 // kernel runs one to eight warps per SM (see choose_shape), so the register
 // budget is not the occupancy limit; without the minimum-blocks argument the
 // compiler capped some instantiations (the request-loop ones) at 128
 // registers and spilled.
-template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, bool kHam>
+template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, int kForm>
 __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) {
   static_assert(!kBanks || kMixed, "block banks exist for FP32_MIXED only");
-  static_assert(!kHam || kKerr, "the canonical form uses the Kerr Hamiltonian (a = 0 included)");
+  constexpr bool kHam = kForm != MALBEC_FORM_GEODESIC;
+  static_assert(!kHam || kKerr, "the canonical forms use the Kerr Hamiltonian (a = 0 included)");
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const float k6h = (float)(1.0 / 6.0), k6l = (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0));
@@ -766,7 +794,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         if constexpr (kHam) {
           // canonical form: integrate (x, p) with p = g u
           double pz[4];
-          lower_velocity(M, a, y, pz);
+          to_momenta<kForm>(M, a, y, pz);
 #pragma unroll
           for (int c = 0; c < 4; ++c) y[4 + c] = pz[c];
           if constexpr (kMixed) split_pair(y, hi, lo);
@@ -836,7 +864,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         const double h = dl_scale > 0.0 ? dl_scale * y[1] : dl;
         double rmin;
         if constexpr (kHam)
-          rmin = rk4_step_ham<double>(bh64, h, y);
+          rmin = rk4_step_ham<double, false, kForm>(bh64, h, y);
         else
           rmin = rk4_step<kKerr, double>(bh64, h, y);
         lam += h;
@@ -850,7 +878,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         const double h = dl_scale > 0.0 ? dl_scale * y[1] : dl;
         double rmin;
         if constexpr (kHam)
-          rmin = rk4_step_ham<double, true>(bh64, h, y);
+          rmin = rk4_step_ham<double, true, kForm>(bh64, h, y);
         else
           rmin = rk4_step<kKerr, double, true>(bh64, h, y);
         flush_lam();
@@ -878,7 +906,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         if ((nst & 31u) == 31u) flush_lam();
         float rmin;
         if constexpr (kHam)
-          rmin = rk4_step_mixed_ham(bh32, hf, h6h, h6l, hi, lo);
+          rmin = rk4_step_mixed_ham<kForm>(bh32, hf, h6h, h6l, hi, lo);
         else
           rmin = rk4_step_mixed<kKerr>(bh32, hf, h6h, h6l, hi, lo);
         captured = (hi[1] <= r_cap_f) | (rmin <= r_cap_f);
@@ -894,7 +922,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
           for (int c = 0; c < 8; ++c) yz[c] = kMixed ? (double)hi[c] + (double)lo[c] : y[c];
 #pragma unroll
           for (int c = 0; c < 4; ++c) yu[c] = yz[c];
-          raise_momentum(M, a, yz, yu + 4);
+          to_velocity<kForm>(M, a, yz, yu + 4);
 #pragma unroll
           for (int c = 0; c < 8; ++c) hu[c] = (float)yu[c];
           store_sample<kMixed>(p, id, nst / p.stride, yu, hu);
@@ -924,7 +952,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
       if constexpr (kHam) {
         // back to (x, u) for the outputs and the invariants
         double u[4];
-        raise_momentum(M, a, y, u);
+        to_velocity<kForm>(M, a, y, u);
 #pragma unroll
         for (int c = 0; c < 4; ++c) y[4 + c] = u[c];
       }
@@ -976,25 +1004,29 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
   }
 }
 
-template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, bool kHam = false>
+template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, int kForm = MALBEC_FORM_GEODESIC>
 const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&trace_kernel<kKerr, kMixed, kSrc, kSink, kBanks, kHam>);
+  return reinterpret_cast<const void*>(&trace_kernel<kKerr, kMixed, kSrc, kSink, kBanks, kForm>);
 }
 
 // The kernel for a launch; FP32_MIXED kernels come with and without the
 // block ray exchange (two instantiations, so that the one without carries
 // none of its code).
-const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, bool ham) {
-  // canonical form (Sec. 2, eq. Ham): FP64, state arrays and cameras
-  if (ham) {
-#define MALBEC_PICK_HAM(S, T)                                                   \
-  if (src == S && sink == T) {                                                  \
-    if (!mixed) return kernel_ptr<true, false, S, T, false, true>();            \
-    return banks ? kernel_ptr<true, true, S, T, true, true>() : kernel_ptr<true, true, S, T, false, true>(); \
+const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, int form) {
+  // canonical forms (Sec. 2, eq. Ham, with g of eq. kerr or of eq. ADM):
+  // state arrays and cameras
+  if (form != MALBEC_FORM_GEODESIC) {
+#define MALBEC_PICK_HAM(F, S, T)                                                                   \
+  if (form == F && src == S && sink == T) {                                                        \
+    if (!mixed) return kernel_ptr<true, false, S, T, false, F>();                                  \
+    return banks ? kernel_ptr<true, true, S, T, true, F>() : kernel_ptr<true, true, S, T, false, F>(); \
   }
-    MALBEC_PICK_HAM(kSrcStates, kSinkFinal)
-    MALBEC_PICK_HAM(kSrcStates, kSinkStrided)
-    MALBEC_PICK_HAM(kSrcCamera, kSinkCamera)
+    MALBEC_PICK_HAM(MALBEC_FORM_HAMILTONIAN, kSrcStates, kSinkFinal)
+    MALBEC_PICK_HAM(MALBEC_FORM_HAMILTONIAN, kSrcStates, kSinkStrided)
+    MALBEC_PICK_HAM(MALBEC_FORM_HAMILTONIAN, kSrcCamera, kSinkCamera)
+    MALBEC_PICK_HAM(MALBEC_FORM_ADM, kSrcStates, kSinkFinal)
+    MALBEC_PICK_HAM(MALBEC_FORM_ADM, kSrcStates, kSinkStrided)
+    MALBEC_PICK_HAM(MALBEC_FORM_ADM, kSrcCamera, kSinkCamera)
 #undef MALBEC_PICK_HAM
     return nullptr;
   }
@@ -1026,7 +1058,7 @@ const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, bool 
 }  // namespace
 
 int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, int threads_per_block) {
-  const void* k = pick(kerr, mixed, src, sink, mixed, false);  // the larger of the two kernels
+  const void* k = pick(kerr, mixed, src, sink, mixed, MALBEC_FORM_GEODESIC);  // the larger of the two kernels
   if (!k) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads_per_block, 0) != cudaSuccess) return 0;
@@ -1040,7 +1072,7 @@ cudaError_t launch_trace(const TraceParams& p, bool kerr, bool mixed, Source src
   // zone), off for whole-image cameras (too few steps in their zone to pay
   // for a zone warp)
   const int exchange = p.exchange >= 0 ? p.exchange : (src == kSrcCamera ? 0 : 1);
-  const void* k = pick(kerr, mixed, src, sink, mixed && exchange == 1, p.form == MALBEC_FORM_HAMILTONIAN);
+  const void* k = pick(kerr, mixed, src, sink, mixed && exchange == 1, (int)p.form);
   if (!k) return cudaErrorInvalidValue;
   // automatic FP64-zone batch: 8 lanes with the exchange (a warp hands fewer
   // zone rays to the zone warp), a full warp without it (a zone step then

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmalbec.so")
 
 FP64, FP32_MIXED = 0, 1
-FORM_GEODESIC, FORM_HAMILTONIAN = 0, 1
+FORM_GEODESIC, FORM_HAMILTONIAN, FORM_ADM = 0, 1, 2
 OUT_FINAL, OUT_STRIDED = 0, 1
 FATE_CAPTURED, FATE_ESCAPED, FATE_CAPPED, FATE_NONFINITE = 1, 2, 3, 4
 OK, EINVAL, ENOMEM, EBUSY, ETIMEDOUT, ECUDA, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
@@ -200,7 +200,7 @@ class Termination:
     n_steps_cap: int = 10_000
     dl: float = 0.01
     dl_r_scale: float = 0.0
-    form: int = 0  # FORM_GEODESIC or FORM_HAMILTONIAN
+    form: int = 0  # FORM_GEODESIC, FORM_HAMILTONIAN or FORM_ADM
 
     def c(self) -> Term:
         return Term(float(self.eps_hor), float(self.r_esc), int(self.n_steps_cap), float(self.dl),

@@ -101,7 +101,7 @@ def test_trace_validation_rejects_before_any_cuda_call(mb):
         (mb.Metric(1.0, 0.5, None), _term(dl=0.0, dl_r_scale=-0.05)),
         (mb.Metric(1.0, 0.5, None), _term(r_esc=1.5)),  # escape inside the capture radius
         (mb.Metric(1.0, 0.5, None), _term(eps_hor=-0.1)),
-        (mb.Metric(1.0, 0.5, None), _term(form=2)),   # no such form
+        (mb.Metric(1.0, 0.5, None), _term(form=3)),   # no such form
     ]
     for m, t in cases:
         assert lib.malbec_trace(m, fake, 10, t, mb.OUT_FINAL, 0, mb.FP64, fake, None) == mb.EINVAL

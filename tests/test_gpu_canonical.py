@@ -1,8 +1,10 @@
-"""The canonical form (Sec. 2, eq. Ham: RK4 on (x^mu, p_mu) with p = g u) on
-the GPU against the oracle's canonical trace, with the tolerance of the
-geodesic form (1e-9 per component, reading G11): circular orbits, generic
-bound orbits, the camera, strided trajectories; and p_t, p_phi exactly
-constant."""
+"""The canonical forms (Sec. 2, eq. Ham: RK4 on (x^mu, p_mu) with p = g u) on
+the GPU against the oracle's canonical trace of the same form, with the
+tolerance of the geodesic form (1e-9 per component, reading G11): circular
+orbits, generic bound orbits, the camera, strided trajectories; and p_t,
+p_phi exactly constant.  Every test runs for both ways of writing H: through
+g^{mu nu} of eq. kerr (form 1) and through the lapse, shift and 3-metric of
+eq. ADM (form 2)."""
 import dataclasses
 import math
 
@@ -34,18 +36,23 @@ def W():
     return workloads
 
 
-def canonical(mb, t):
-    return mb.Termination(t.eps_hor, t.r_esc, t.n_steps_cap, t.dl, t.dl_r_scale, mb.FORM_HAMILTONIAN)
+@pytest.fixture(scope="module", params=[1, 2], ids=["kerr_bl", "adm"])
+def form(request):
+    return request.param
 
 
-def test_circular_orbits(mb, orc, W):
+def canonical(mb, t, form):
+    return mb.Termination(t.eps_hor, t.r_esc, t.n_steps_cap, t.dl, t.dl_r_scale, form)
+
+
+def test_circular_orbits(mb, orc, W, form):
     """Schwarzschild (the Kerr Hamiltonian at a = 0) and Kerr a = 0.7
     circular orbits, 10^4 steps of 0.01: within 1e-9 of the oracle; r stays
     at r0; E and L_z unchanged to the conversion round trip."""
     wl = W.circular()
     for a, radii in ((0.0, wl.radii), (0.7, wl.radii[:256] + 2.0)):
         ics = np_(mb.ic_circular(1.0, a, radii))
-        t = canonical(mb, wl.term)
+        t = canonical(mb, wl.term, form)
         got = gpu_trace(mb, 1.0, a, ics, t)
         ref = orc.trace_many(1.0, a, ics, oracle_term(orc, t))
         assert_states_close(got["y"], ref["y"], what=f"canonical circular a={a}")
@@ -55,7 +62,7 @@ def test_circular_orbits(mb, orc, W):
         assert d.max() < 1e-13
 
 
-def test_bound_orbits_subsample(mb, orc, W):
+def test_bound_orbits_subsample(mb, orc, W, form):
     """The generic bound-orbit subsample (1024 particles, 10^4 steps of 0.02,
     per-particle spin) within 1e-9 of the oracle's canonical trace, apart from
     the few orbits whose discrete map is ill-conditioned next to the polar
@@ -63,7 +70,7 @@ def test_bound_orbits_subsample(mb, orc, W):
     wl = W.bound()
     idx = wl.subsample(1024)
     ys, spins, _ = orc.bound_samples(wl.M, wl.a_max, wl.seed, idx)
-    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=10_000, dl=0.02, form=mb.FORM_HAMILTONIAN)
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=10_000, dl=0.02, form=form)
     got = gpu_trace(mb, wl.M, 0.0, ys, t, a_per_ray=spins)
     ref, kappa = oracle_kappa(orc, wl.M, 0.0, ys, oracle_term(orc, t), a_per_ray=spins)
     good = kappa <= KAPPA_MAX
@@ -76,20 +83,20 @@ def test_bound_orbits_subsample(mb, orc, W):
     assert d.max() < 1e-12
 
 
-def test_camera_small_image(mb, orc, W):
+def test_camera_small_image(mb, orc, W, form):
     """64 x 64 Kerr a = 0.9 camera in the canonical form: fates and steps of
     well-conditioned pixels away from the critical curve equal the oracle's;
     escaped (theta, phi) within 1e-9."""
     import torch
 
     cw = W.camera(nx=64, ny=64)
-    cw = dataclasses.replace(cw, term=canonical(mb, cw.term))
+    cw = dataclasses.replace(cw, term=canonical(mb, cw.term, form))
     cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
     res = mb.trace_camera(cw.M, cw.a, cam, cw.term, "fp64")
     torch.cuda.synchronize()
     got = {k: np_(v) for k, v in res.items() if k != "buffer"}
     pix = np.arange(cw.n)
-    ref, near, agree, far = _camera_compare(mb, orc, cw, got, pix, form=1)
+    ref, near, agree, far = _camera_compare(mb, orc, cw, got, pix, form=form)
     good = ref["kappa"] <= KAPPA_MAX
     assert agree[far & good].all()
     assert agree[far].mean() >= 0.9999
@@ -100,13 +107,13 @@ def test_camera_small_image(mb, orc, W):
     assert_states_close(got["phi"][esc], ref["y"][3][esc], what="phi")
 
 
-def test_strided_trajectories(mb, orc):
+def test_strided_trajectories(mb, orc, form):
     """Trajectory samples of the canonical form are (x, u) states equal to the
     oracle's samples within 1e-9; samples after termination are NaN."""
     rng = np.random.default_rng(4)
     ys = np.stack([orc.circular_state(1.0, 0.5, r, 1) for r in rng.uniform(7.0, 12.0, 20)], axis=1)
     ys[5] *= 1.0 + 0.02 * rng.standard_normal(ys.shape[1])
-    t = mb.Termination(eps_hor=0.01, r_esc=60.0, n_steps_cap=800, dl=0.05, form=mb.FORM_HAMILTONIAN)
+    t = mb.Termination(eps_hor=0.01, r_esc=60.0, n_steps_cap=800, dl=0.05, form=form)
     got = gpu_trace(mb, 1.0, 0.5, ys, t, mode=mb.OUT_STRIDED, stride=50)
     ref = orc.trace_many(1.0, 0.5, ys, oracle_term(orc, t), stride=50, want_traj=True)
     tg, tr = got["traj"], ref["traj"]
@@ -115,35 +122,35 @@ def test_strided_trajectories(mb, orc):
     assert_states_close(tg[fin], tr[fin], what="canonical trajectory samples")
 
 
-def test_canonical_agrees_with_geodesic_form(mb, W):
+def test_canonical_agrees_with_geodesic_form(mb, W, form):
     """The two forms integrate the same flow: on smooth orbits their results
     differ by the RK4 truncation error only (well below 1e-6 here)."""
     ics = np_(mb.ic_bound(1.0, 0.5, W.bound().seed, 256, spin_fixed=True)[0])
     t0 = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=2000, dl=0.02)
     g = gpu_trace(mb, 1.0, 0.5, ics, t0)
-    c = gpu_trace(mb, 1.0, 0.5, ics, dataclasses.replace(t0, form=mb.FORM_HAMILTONIAN))
+    c = gpu_trace(mb, 1.0, 0.5, ics, dataclasses.replace(t0, form=form))
     ok = (g["fate"] == mb.FATE_CAPPED) & (c["fate"] == mb.FATE_CAPPED)
     assert ok.mean() > 0.95
     rel = np.abs(g["y"][:, ok] - c["y"][:, ok]) / np.maximum(np.abs(g["y"][:, ok]), 1.0)
     assert np.median(rel.max(axis=0)) < 1e-7
 
 
-def test_canonical_rejects_job_tables(mb):
-    t = mb.Termination(eps_hor=0.01, r_esc=60.0, n_steps_cap=10, dl=0.05, form=mb.FORM_HAMILTONIAN)
+def test_canonical_rejects_job_tables(mb, form):
+    t = mb.Termination(eps_hor=0.01, r_esc=60.0, n_steps_cap=10, dl=0.05, form=form)
     b = mb.make_bundle(mb.BUNDLE_BOUND, 4, 1.0, 0.5, t, seed=1)
     with pytest.raises(mb.MalbecError):
         mb.attach_outputs([b], "fp64")
         mb.trace_bundles([b], "fp64")
 
 
-def test_mixed_canonical_conserves_E_and_Lz(mb, W):
+def test_mixed_canonical_conserves_E_and_Lz(mb, W, form):
     """FP32_MIXED in the canonical form keeps p_t and p_phi fixed as float
     pairs: E and L_z change only through the end conversions (< 1e-12), while
     Q and the norm drift by at most 1e-6 on the orbits the FP64 form
     resolves (drift <= 1e-8)."""
     wl = W.bound()
     ics, spins, _ = mb.ic_bound(wl.M, wl.a_max, wl.seed, 4096)
-    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=20_000, dl=0.02, form=mb.FORM_HAMILTONIAN)
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=20_000, dl=0.02, form=form)
     r64 = gpu_trace(mb, wl.M, 0.0, np_(ics), t, a_per_ray=spins)
     r32 = gpu_trace(mb, wl.M, 0.0, np_(ics), t, a_per_ray=spins, precision="fp32_mixed")
 
@@ -160,7 +167,7 @@ def test_mixed_canonical_conserves_E_and_Lz(mb, W):
     assert d32[2:, resolved].max() <= 1e-6, d32[2:, resolved].max(axis=1)
 
 
-def test_mixed_canonical_camera(mb, W):
+def test_mixed_canonical_camera(mb, W, form):
     """The 256 x 256 camera in the canonical form: FP32_MIXED fates equal the
     FP64 ones on >= 99% of the pixels; escaped angles agree to 1e-6 on the
     median."""
@@ -168,7 +175,7 @@ def test_mixed_canonical_camera(mb, W):
 
     cw = W.camera(nx=256, ny=256)
     cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
-    t = canonical(mb, cw.term)
+    t = canonical(mb, cw.term, form)
     a = mb.trace_camera(cw.M, cw.a, cam, t, "fp64")
     fa, tha = a["fate"].clone(), a["theta"].clone()
     b = mb.trace_camera(cw.M, cw.a, cam, t, "fp32_mixed")
@@ -178,3 +185,19 @@ def test_mixed_canonical_camera(mb, W):
     d = (b["theta"][esc] - tha[esc]).abs()
     d = d[torch.isfinite(d)]
     assert d.median().item() < 1e-6
+
+
+def test_adm_and_kerr_bl_forms_agree(mb, W):
+    """Forms 1 and 2 are one flow and one RK4 map, written two ways: on the
+    bound-orbit sample their GPU results differ by rounding only (1e-9), far
+    below the geodesic/canonical difference."""
+    wl = W.bound()
+    ics, spins, _ = mb.ic_bound(wl.M, wl.a_max, wl.seed, 2048)
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=5000, dl=0.02, form=mb.FORM_HAMILTONIAN)
+    c = gpu_trace(mb, wl.M, 0.0, np_(ics), t, a_per_ray=spins)
+    d = gpu_trace(mb, wl.M, 0.0, np_(ics), dataclasses.replace(t, form=mb.FORM_ADM), a_per_ray=spins)
+    same = c["fate"] == d["fate"]
+    assert same.mean() > 0.995
+    ok = same & (c["fate"] == mb.FATE_CAPPED)
+    rel = np.abs(c["y"][:, ok] - d["y"][:, ok]) / np.maximum(np.abs(c["y"][:, ok]), 1.0)
+    assert np.quantile(rel.max(axis=0), 0.99) < 1e-9
