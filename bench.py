@@ -51,11 +51,12 @@ def kernel_source_hash() -> str:
 # canonical form (eq. Ham): 72 per Kerr right-hand side, 74 for its RK4
 # (p_t, p_ph fixed); the 3+1 form: 65 for Kerr's lapse, shift, 3-metric and
 # their logarithmic derivatives plus 34 for the 3+1 right-hand side, the same
-# 74 for its RK4.  Divisions and sincos are listed separately (4 each per
-# step).
+# 74 for its RK4.  Listed separately per step: 4 reciprocals (a hardware
+# estimate and 3 FMA each), 1 sincos and 3 stage-angle rotations (angle
+# addition with short Taylor series, about 19 FP64 operations each).
 FLOPS_PER_STEP = {"kerr": 4 * 120 + 102, "schw": 4 * 42 + 102, "kerr_canonical": 4 * 72 + 74,
                   "kerr_adm": 4 * (65 + 34) + 74}
-DIV_PER_STEP, SINCOS_PER_STEP = 4, 4
+PLUS_PER_STEP = {"reciprocal": 4, "sincos": 1, "stage_angle_rotation": 3}
 
 
 class ClockSampler:
@@ -798,6 +799,16 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     peak64 = mb.measure_fma_peak("fp64")
     peak32 = mb.measure_fma_peak("fp32_mixed")
+    # the bare RK4 step loop of each form: the ceiling of the trace kernels
+    # for their right-hand side's instruction mix
+    loop = {f: mb.measure_step_loop(f) for f in (mb.FORM_GEODESIC, mb.FORM_HAMILTONIAN, mb.FORM_ADM)}
+
+    def ceiling(form, flops_key, kernel_rate):
+        fl = FLOPS_PER_STEP[flops_key]
+        return {"steps_per_s": loop[form], "frac": fl * loop[form] / 1e9 / peak64,
+                "kernel_over_ceiling": kernel_rate / loop[form],
+                "note": "malbec_measure_step_loop: the same RK4 step with no queue, termination or output, "
+                        "one warp per SM sub-partition (more warps or rays per thread measured no faster)"}
     barrier, max_over_ranks = ranks.barrier, ranks.max
 
     with torch.cuda.stream(stream):
@@ -854,6 +865,7 @@ def main():
                                 "achieved": fl * steps_c / (statistics.mean(times_c) / 1e3) / 1e9,
                                 "frac": fl * steps_c / (statistics.mean(times_c) / 1e3) / 1e9 / peak64},
                    "note": note}
+            arm["roofline"]["step_loop_ceiling"] = ceiling(form, flops_key, value_c / world)
             fate_c, theta_c = res_c["fate"].clone(), res_c["theta"].clone()
             for _ in range(args.warmup):
                 mb.trace_camera(cw.M, cw.a, cam, term_c, "fp32_mixed", stream=stream, out=out)
@@ -934,7 +946,8 @@ def main():
                      "frac": achieved / peak64, "traffic": load_traffic("camera_fp64"),
                      "peak_note": "measured FP64 FMA loop on this GPU (malbec_measure_fma_peak), of measured",
                      "flops_per_rk4_step": FLOPS_PER_STEP["kerr"],
-                     "plus_per_rk4_step": {"div": DIV_PER_STEP, "sincos": SINCOS_PER_STEP}},
+                     "plus_per_rk4_step": PLUS_PER_STEP,
+                     "step_loop_ceiling": ceiling(mb.FORM_GEODESIC, "kerr", value / world)},
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(L.total),
                 "note": "malbec_trace_camera + copy of the image (fate, steps, theta, phi) to pinned host memory; "
                         "the rays are built on the device from the camera description passed by value"},

@@ -451,6 +451,26 @@ int malbec_invariants(malbec_metric m, const double* states, uint64_t n, double*
  * Writes GFLOP/s (2 flops per FMA). */
 int malbec_measure_fma_peak(malbec_precision prec, double* gflops);
 
+/* The bare FP64 RK4 step loop of one form (MALBEC_FORM_*): the step the trace
+ * kernels take (same right-hand side, Sec. 2 eq. kerr with eq. geo, eq. Ham
+ * or eq. ADM, and the classical RK4 tableau), with no work queue, termination
+ * test or output: every thread follows an inclined bound orbit of Kerr
+ * a = 0.9 M near r = 10 M with dtau = 0.5 for 4000 steps, one warp per SM
+ * sub-partition, all SMs.  Blocks the calling thread; best of three launches.
+ * Writes RK4 steps/s: the ceiling of a trace kernel for that right-hand
+ * side's instruction mix.  MALBEC_EINVAL for another form. */
+int malbec_measure_step_loop(uint32_t form, double* steps_per_s);
+
+/* Self-check of two FP64 device helpers of the right-hand sides, on 2^22
+ * seeded samples: the stage sine/cosine by angle addition (|d| <= 1/4)
+ * against CUDA's sincos at the same, exactly representable angle, and the
+ * refined reciprocal against the IEEE division 1.0 / x (x in 2^[-60, 60]).
+ * err[0], err[1]: max absolute sine, cosine difference; err[2]: max
+ * reciprocal difference in units of the last place of 1/x; err[3]: max
+ * relative error of the hardware reciprocal estimate before refinement.
+ * Blocks the calling thread. */
+int malbec_check_fp64_helpers(double err[4]);
+
 /* Library build information (static string). */
 const char* malbec_build_info(void);
 

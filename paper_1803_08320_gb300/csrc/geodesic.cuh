@@ -12,8 +12,9 @@
 // closed-form inverse of the (t, phi) block (det = -Delta sin^2).  It is the
 // same bilinear form as the twenty second-kind symbols of BL Kerr, with far
 // fewer operations.  Schwarzschild uses its nine non-zero second-kind symbols
-// directly.  One division per evaluation: 1/rho^2, 1/Delta and 1/sin^2 are
-// products of 1/(rho^2 Delta sin^2).
+// directly.  One reciprocal per evaluation: 1/rho^2, 1/Delta and 1/sin^2 are
+// products of 1/(rho^2 Delta sin^2).  In FP64 one sincos per RK4 step: the
+// later stage angles take the angle-addition formulas (stage_trig).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -30,6 +31,60 @@ template <>
 struct Trig<float> {
   __device__ __forceinline__ static void sc(float x, float* s, float* c) { sincosf(x, s, c); }
 };
+
+// 1/x.  FP64: the hardware estimate (PTX rcp.approx.ftz.f64) refined by one
+// step of the cubically convergent iteration y <- y (1 + e + e^2), e = 1 - x y
+// (Newton's iteration for 1/x with the next term of the series 1/(1 - e)
+// kept): the estimate's relative error e0 becomes O(e0^3) plus rounding.
+// Arguments here are positive and normal (products of rho^2, Delta, sin^2).
+// FP32: the IEEE division.
+template <typename T>
+__device__ __forceinline__ T recip(T x);
+template <>
+__device__ __forceinline__ double recip<double>(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+template <>
+__device__ __forceinline__ float recip<float>(float x) {
+  return 1.0f / x;
+}
+
+// sin and cos at an RK4 stage angle th = th0 + d, given s0 = sin th0 and
+// c0 = cos th0 of the step's start.  FP64 with |d| <= 1/4: the angle-addition
+// formulas with sin d and cos d - 1 from their Taylor series,
+//   sin d = d - d^3/3! + ... - d^11/11!,  cos d - 1 = -d^2/2! + ... + d^12/12!
+// (the first omitted terms are below 1e-17 relative for |d| <= 1/4), so one
+// sincos serves the four stages of a step.  Otherwise, and in FP32: sincos of
+// th itself.
+template <typename T>
+__device__ __forceinline__ void stage_trig(T s0, T c0, T d, T th, T* s, T* c) {
+  Trig<T>::sc(th, s, c);
+}
+template <>
+__device__ __forceinline__ void stage_trig<double>(double s0, double c0, double d, double th, double* s,
+                                                   double* c) {
+  if (fabs(d) <= 0.25) {
+    const double z = d * d;
+    double ps = fma(z, -1.0 / 39916800.0, 1.0 / 362880.0);
+    ps = fma(z, ps, -1.0 / 5040.0);
+    ps = fma(z, ps, 1.0 / 120.0);
+    ps = fma(z, ps, -1.0 / 6.0);
+    const double sd = fma(d * z, ps, d);  // sin d
+    double pc = fma(z, 1.0 / 479001600.0, -1.0 / 3628800.0);
+    pc = fma(z, pc, 1.0 / 40320.0);
+    pc = fma(z, pc, -1.0 / 720.0);
+    pc = fma(z, pc, 1.0 / 24.0);
+    pc = fma(z, pc, -0.5);
+    const double cm1 = z * pc;  // cos d - 1
+    *s = s0 + fma(s0, cm1, c0 * sd);
+    *c = c0 + fma(c0, cm1, -s0 * sd);
+  } else {
+    sincos(th, s, c);
+  }
+}
 
 template <typename T>
 struct BH {
@@ -53,13 +108,11 @@ __device__ __forceinline__ BH<T> make_bh(double M, double a) {
 // Gamma^th_rth = Gamma^ph_rph = 1/r, Gamma^th_phph = -sin cos,
 // Gamma^ph_thph = cot, with f = r - 2M.
 template <typename T>
-__device__ __forceinline__ void accel_schw(const BH<T>& bh, T r, T th, T ut, T ur, T uth, T uph,
+__device__ __forceinline__ void accel_schw(const BH<T>& bh, T r, T s, T c, T ut, T ur, T uth, T uph,
                                            T acc[4]) {
-  T s, c;
-  Trig<T>::sc(th, &s, &c);
   const T f = r - bh.twoM;
   const T rf = r * f;
-  const T inv = T(1) / (rf * s);  // 1 / (r f sin)
+  const T inv = recip<T>(rf * s);  // 1 / (r f sin)
   const T ir = f * s * inv;       // 1/r
   const T i_f = r * s * inv;      // 1/f
   const T cot = c * rf * inv;     // cos/sin
@@ -77,17 +130,15 @@ __device__ __forceinline__ void accel_schw(const BH<T>& bh, T r, T th, T ut, T u
 //   g_rr = rho^2/Delta, g_thth = rho^2,
 //   d_r q = (2M - 2 r q)/rho^2, d_th q = 2 a^2 s c q / rho^2.
 template <typename T>
-__device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T th, T ut, T ur, T uth, T uph,
+__device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T s, T c, T ut, T ur, T uth, T uph,
                                            T acc[4]) {
-  T s, c;
-  Trig<T>::sc(th, &s, &c);
   const T a = bh.a, a2 = bh.a2;
   const T s2 = s * s, sc = s * c;
   const T r2 = r * r;
   const T rho2 = fma(a2, c * c, r2);
   const T Delta = fma(r, r - bh.twoM, a2);
   const T Ds2 = Delta * s2;
-  const T inv = T(1) / (rho2 * Ds2);
+  const T inv = recip<T>(rho2 * Ds2);
   const T irho2 = Ds2 * inv;
   const T iDs2 = rho2 * inv;  // 1 / (Delta sin^2)
   const T iDelta = iDs2 * s2;
@@ -131,12 +182,20 @@ __device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T th, T ut, T u
   acc[3] = fma(q - T(1), Wp, as2 * q * Wt) * iDs2;
 }
 
+// The acceleration at (r, theta) given s = sin theta, c = cos theta.
+template <bool kKerr, typename T>
+__device__ __forceinline__ void accel_sc(const BH<T>& bh, T r, T s, T c, T ut, T ur, T uth, T uph, T acc[4]) {
+  if (kKerr)
+    accel_kerr<T>(bh, r, s, c, ut, ur, uth, uph, acc);
+  else
+    accel_schw<T>(bh, r, s, c, ut, ur, uth, uph, acc);
+}
+
 template <bool kKerr, typename T>
 __device__ __forceinline__ void accel(const BH<T>& bh, T r, T th, T ut, T ur, T uth, T uph, T acc[4]) {
-  if (kKerr)
-    accel_kerr<T>(bh, r, th, ut, ur, uth, uph, acc);
-  else
-    accel_schw<T>(bh, r, th, ut, ur, uth, uph, acc);
+  T s, c;
+  Trig<T>::sc(th, &s, &c);
+  accel_sc<kKerr, T>(bh, r, s, c, ut, ur, uth, uph, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -156,9 +215,12 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
   T u[4] = {y[4], y[5], y[6], y[7]};
   T sx[4], su[4];
   T rmin = T(0);
+  T s0, c0;
+  Trig<T>::sc(y[2], &s0, &c0);
+  T sn = s0, cs = c0;
   auto stage = [&](int s) {
     T acc[4];
-    accel<kKerr, T>(bh, r, th, u[0], u[1], u[2], u[3], acc);
+    accel_sc<kKerr, T>(bh, r, sn, cs, u[0], u[1], u[2], u[3], acc);
     if (s == 0) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -177,6 +239,7 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
       const T c = s < 2 ? hh : h;
       r = fma(c, u[1], y[1]);
       th = fma(c, u[2], y[2]);
+      stage_trig<T>(s0, c0, c * u[2], th, &sn, &cs);
 #pragma unroll
       for (int j = 0; j < 4; ++j) u[j] = fma(c, acc[j], y[4 + j]);
       rmin = s == 0 ? r : fmin(rmin, r);
@@ -206,17 +269,15 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
 // so dx/dl follows from dF/dp and dp_r/dl = -(dF/dr - F d(rho^2)/dr / rho^2)
 // / (2 rho^2), dp_th/dl likewise; p_t and p_ph are constant (H does not
 // depend on t, ph) and are not integrated.  f = (dt, dr, dth, dph, dp_r,
-// dp_th)/dl.  One division, as in the geodesic form.
+// dp_th)/dl.  One reciprocal, as in the geodesic form.
 template <typename T>
-__device__ __forceinline__ void ham_kerr(const BH<T>& bh, T r, T th, T pt, T pr, T pth, T pph, T f[6]) {
-  T s, c;
-  Trig<T>::sc(th, &s, &c);
+__device__ __forceinline__ void ham_kerr(const BH<T>& bh, T r, T s, T c, T pt, T pr, T pth, T pph, T f[6]) {
   const T a = bh.a, a2 = bh.a2;
   const T s2 = s * s, sc = s * c;
   const T rho2 = fma(a2, c * c, r * r);
   const T Delta = fma(r, r - bh.twoM, a2);
   const T rD = rho2 * Delta;
-  const T inv = T(1) / (rD * s2);
+  const T inv = recip<T>(rD * s2);
   const T irho2 = Delta * s2 * inv;
   const T iDelta = rho2 * s2 * inv;
   const T is2 = rD * inv;
@@ -276,9 +337,7 @@ struct Adm {
 // division among 1/rho^2, 1/Delta, 1/Sigma and 1/sin^2; FP32 takes 1/Sigma
 // apart (the product of all four would overflow near r = 10^4).
 template <typename T>
-__device__ __forceinline__ void adm_kerr(const BH<T>& bh, T r, T th, Adm<T>& m) {
-  T s, c;
-  Trig<T>::sc(th, &s, &c);
+__device__ __forceinline__ void adm_kerr_sc(const BH<T>& bh, T r, T s, T c, Adm<T>& m) {
   const T a2 = bh.a2;
   const T s2 = s * s, sc = s * c;
   const T rho2 = fma(a2, c * c, r * r);
@@ -289,7 +348,7 @@ __device__ __forceinline__ void adm_kerr(const BH<T>& bh, T r, T th, Adm<T>& m) 
   T irho2, iDelta, iSigma, is2;
   if constexpr (sizeof(T) == 8) {
     const T SS = Sigma * s2;
-    const T inv = T(1) / (rD * SS);
+    const T inv = recip<T>(rD * SS);
     irho2 = Delta * SS * inv;
     iDelta = rho2 * SS * inv;
     iSigma = rD * s2 * inv;
@@ -328,6 +387,13 @@ __device__ __forceinline__ void adm_kerr(const BH<T>& bh, T r, T th, Adm<T>& m) 
   m.dlng[2][1] = fma(T(2) * sc, is2, lS_t - lrho_t);
 }
 
+template <typename T>
+__device__ __forceinline__ void adm_kerr(const BH<T>& bh, T r, T th, Adm<T>& m) {
+  T s, c;
+  Trig<T>::sc(th, &s, &c);
+  adm_kerr_sc<T>(bh, r, s, c, m);
+}
+
 // The 3+1 right-hand side f = (dt, dr, dth, dph, dp_r, dp_th)/dl at one
 // point of any provider (formulas above).
 template <typename T>
@@ -350,14 +416,21 @@ __device__ __forceinline__ void adm_rhs(const Adm<T>& m, T pt, T pr, T pth, T pp
 // The canonical right-hand side of one form: eq. Ham through g^{mu nu} of
 // eq. kerr (kHamKerrBL) or through the 3+1 quantities of Kerr (kHamAdm).
 template <int kForm, typename T>
-__device__ __forceinline__ void ham_rhs(const BH<T>& bh, T r, T th, T pt, T pr, T pth, T pph, T f[6]) {
+__device__ __forceinline__ void ham_rhs_sc(const BH<T>& bh, T r, T s, T c, T pt, T pr, T pth, T pph, T f[6]) {
   if constexpr (kForm == kHamAdm) {
     Adm<T> m;
-    adm_kerr<T>(bh, r, th, m);
+    adm_kerr_sc<T>(bh, r, s, c, m);
     adm_rhs<T>(m, pt, pr, pth, pph, f);
   } else {
-    ham_kerr<T>(bh, r, th, pt, pr, pth, pph, f);
+    ham_kerr<T>(bh, r, s, c, pt, pr, pth, pph, f);
   }
+}
+
+template <int kForm, typename T>
+__device__ __forceinline__ void ham_rhs(const BH<T>& bh, T r, T th, T pt, T pr, T pth, T pph, T f[6]) {
+  T s, c;
+  Trig<T>::sc(th, &s, &c);
+  ham_rhs_sc<kForm, T>(bh, r, s, c, pt, pr, pth, pph, f);
 }
 
 // p_mu = g_{mu nu} u^nu from the 3+1 quantities: g_tt = -alpha^2 +
@@ -387,9 +460,12 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
   T r = z[1], th = z[2], pr = z[5], pth = z[6];
   T sx[6];
   T rmin = T(0);
+  T s0, c0;
+  Trig<T>::sc(z[2], &s0, &c0);
+  T sn = s0, cs = c0;
   auto stage = [&](int s) {
     T f[6];
-    ham_rhs<kForm, T>(bh, r, th, z[4], pr, pth, z[7], f);
+    ham_rhs_sc<kForm, T>(bh, r, sn, cs, z[4], pr, pth, z[7], f);
     if (s == 0) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) sx[j] = f[j];
@@ -402,6 +478,7 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
       const T c = s < 2 ? hh : h;
       r = fma(c, f[1], z[1]);
       th = fma(c, f[2], z[2]);
+      stage_trig<T>(s0, c0, c * f[2], th, &sn, &cs);
       pr = fma(c, f[4], z[5]);
       pth = fma(c, f[5], z[6]);
       rmin = s == 0 ? r : fmin(rmin, r);

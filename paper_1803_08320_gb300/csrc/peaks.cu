@@ -1,6 +1,12 @@
 // peaks.cu -- measured non-tensor FMA throughput (the roofline denominator of
 // the ALU-bound geodesic kernels).  Eight independent FMA chains per thread,
-// every SM busy, timed with CUDA events; best of three launches.
+// every SM busy, timed with CUDA events; best of three launches.  Also the
+// bare FP64 RK4 step loop (the ceiling the trace kernels approach for their
+// instruction mix) and a self-check of the FP64 stage trigonometry and
+// reciprocal against CUDA's sincos and division.
+#include <string.h>
+
+#include "geodesic.cuh"
 #include "internal.h"
 
 namespace malbec {
@@ -54,8 +60,134 @@ int measure(int iters, double* gflops) {
   return MALBEC_OK;
 }
 
+// The RK4 step of one form, nothing else: each thread follows an inclined
+// bound orbit of Kerr a = 0.9 M (r0 = 10 M + a lane offset, dtau = 0.5) for
+// nsteps steps; one warp per SM sub-partition, as in the trace kernels.
+template <int kForm>
+__global__ void __launch_bounds__(128, 1) step_loop_kernel(double* out, int nsteps) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const double M = 1.0, a = 0.9, h = 0.5;
+  const BH<double> bh = make_bh<double>(M, a);
+  const double r0 = 10.0 + 1e-3 * (tid % 97);
+  double y[8] = {0.0, r0, 1.2, 0.0, 1.0 / sqrt(1.0 - 3.0 / r0), 0.0, 0.01, 0.0};
+  y[7] = sqrt(1.0 / (r0 * r0 * r0)) * y[4];
+  if constexpr (kForm != MALBEC_FORM_GEODESIC) {
+    double p[4];
+    lower_velocity(M, a, y, p);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) y[4 + c] = p[c];
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    if constexpr (kForm == MALBEC_FORM_GEODESIC)
+      rk4_step<true, double>(bh, h, y);
+    else
+      rk4_step_ham<double, false, kForm>(bh, h, y);
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc += y[c];
+  out[tid] = acc;
+}
+
+template <int kForm>
+int step_loop(double* steps_per_s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  const int threads = 128, blocks = sms, nsteps = 4000;
+  double* buf = nullptr;
+  e = cudaMalloc(&buf, sizeof(double) * (size_t)threads * blocks);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  step_loop_kernel<kForm><<<blocks, threads>>>(buf, 50);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(e0);
+    step_loop_kernel<kForm><<<blocks, threads>>>(buf, nsteps);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  *steps_per_s = (double)nsteps * blocks * threads / (best * 1e-3);
+  return MALBEC_OK;
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// stage_trig against sincos at exactly representable angles th0 + d
+// (th0 = k / 256 with |th0| < 4, d = m / 2^40 with |d| <= 1/4, so the sum has
+// at most 42 significant bits), and recip against the IEEE division on
+// x = mantissa x 2^e, e in [-60, 60].  err: max |sin error|, max |cos error|,
+// max recip error in units of the last place of 1/x, max relative error of
+// the hardware estimate alone; non-negative doubles ordered as integers.
+__global__ void helpers_check_kernel(unsigned long long* err, uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long h1 = mix64(2 * i), h2 = mix64(2 * i + 1);
+    const double th0 = (double)((long long)(h1 % 2047ull) - 1023) / 256.0;
+    const double d = (double)((long long)(h2 % ((1ull << 39) + 1ull)) - (1ll << 38)) / 1099511627776.0;
+    const double th = th0 + d;
+    double s0, c0, s, c, sr, cr;
+    sincos(th0, &s0, &c0);
+    stage_trig<double>(s0, c0, d, th, &s, &c);
+    sincos(th, &sr, &cr);
+    const double es = fabs(s - sr), ec = fabs(c - cr);
+    const unsigned long long h3 = mix64(~i);
+    const double x = ldexp(1.0 + (double)(h3 >> 11) * 0x1.0p-53, (int)((h3 & 0xFFFFull) % 121ull) - 60);
+    const double q = 1.0 / x, y = recip<double>(x);
+    double y0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
+    const double ulp = ldexp(1.0, ilogb(q) - 52);
+    const double er = fabs(y - q) / ulp, e0 = fabs(y0 - q) / q;
+    atomicMax(&err[0], (unsigned long long)__double_as_longlong(es));
+    atomicMax(&err[1], (unsigned long long)__double_as_longlong(ec));
+    atomicMax(&err[2], (unsigned long long)__double_as_longlong(er));
+    atomicMax(&err[3], (unsigned long long)__double_as_longlong(e0));
+  }
+}
+
 }  // namespace
 }  // namespace malbec
+
+extern "C" int malbec_measure_step_loop(uint32_t form, double* steps_per_s) {
+  if (!steps_per_s) return MALBEC_EINVAL;
+  if (form == MALBEC_FORM_GEODESIC) return malbec::step_loop<MALBEC_FORM_GEODESIC>(steps_per_s);
+  if (form == MALBEC_FORM_HAMILTONIAN) return malbec::step_loop<MALBEC_FORM_HAMILTONIAN>(steps_per_s);
+  if (form == MALBEC_FORM_ADM) return malbec::step_loop<MALBEC_FORM_ADM>(steps_per_s);
+  return MALBEC_EINVAL;
+}
+
+extern "C" int malbec_check_fp64_helpers(double err[4]) {
+  if (!err) return MALBEC_EINVAL;
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 4 * sizeof(unsigned long long));
+  if (e != cudaSuccess) return malbec::set_cuda_error(e);
+  e = cudaMemset(d, 0, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    malbec::helpers_check_kernel<<<1024, 256>>>(d, 1ull << 22);
+    e = cudaGetLastError();
+  }
+  unsigned long long h[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return malbec::set_cuda_error(e);
+  for (int k = 0; k < 4; ++k) memcpy(&err[k], &h[k], sizeof(double));
+  return MALBEC_OK;
+}
 
 extern "C" int malbec_measure_fma_peak(malbec_precision prec, double* gflops) {
   if (!gflops) return MALBEC_EINVAL;

@@ -130,6 +130,8 @@ def _declare(L):
     sig("malbec_ic_bound", ctypes.c_int, _D, _D, ctypes.c_int, _U64, _U64, _U64, _VP, _VP, _VP, _VP)
     sig("malbec_invariants", ctypes.c_int, Metric, _VP, _U64, _VP, _VP)
     sig("malbec_measure_fma_peak", ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D))
+    sig("malbec_measure_step_loop", ctypes.c_int, _U32, ctypes.POINTER(_D))
+    sig("malbec_check_fp64_helpers", ctypes.c_int, ctypes.POINTER(_D))
     sig("malbec_bundle_out_bytes", _SZ, ctypes.POINTER(Bundle), ctypes.c_int)
     sig("malbec_trace_bundles", ctypes.c_int, ctypes.POINTER(Bundle), _U32, ctypes.c_int, _VP)
     sig("malbec_plan_create", ctypes.c_int, ctypes.POINTER(Bundle), _U32, ctypes.c_int, ctypes.POINTER(_VP))
@@ -555,3 +557,19 @@ def measure_fma_peak(precision="fp64") -> float:
     g = _D()
     _check(lib().malbec_measure_fma_peak(_prec(precision), ctypes.byref(g)), "malbec_measure_fma_peak")
     return g.value
+
+
+def measure_step_loop(form=FORM_GEODESIC) -> float:
+    """RK4 steps/s of the bare FP64 step loop of one form (blocks the caller):
+    the ceiling of the trace kernels for that right-hand side."""
+    g = _D()
+    _check(lib().malbec_measure_step_loop(int(form), ctypes.byref(g)), "malbec_measure_step_loop")
+    return g.value
+
+
+def check_fp64_helpers() -> dict:
+    """Max errors of the FP64 stage sine/cosine and reciprocal against CUDA's
+    sincos and IEEE division (blocks the caller)."""
+    e = (_D * 4)()
+    _check(lib().malbec_check_fp64_helpers(e), "malbec_check_fp64_helpers")
+    return {"sin_abs": e[0], "cos_abs": e[1], "recip_ulp": e[2], "recip_estimate_rel": e[3]}
