@@ -41,6 +41,9 @@ class Term(ctypes.Structure):
         ("dl", _D),
         ("dl_r_scale", _D),
         ("form", _U32),
+        ("method", _U32),
+        ("rtol", _D),
+        ("atol", _D),
     ]
 
 
@@ -91,6 +94,8 @@ def _declare(L):
     sig("orc_rhs_adm", None, _D, _D, _PD, _PD)
     sig("orc_hamiltonian_adm", _D, _D, _D, _PD)
     sig("orc_rk4_step_adm", None, _D, _D, _D, _PD)
+    sig("orc_dopri5_tableau", None, _PD, _PD, _PD, _PD)
+    sig("orc_dopri5_linear_test", None, _D, _D, _D, _PD, _PD)
     sig("orc_rk4_linear_test", None, _D, _D, ctypes.c_int, _PD)
     sig("orc_rk4_step", None, _D, _D, _D, _PD)
     sig("orc_rk4_step_hamiltonian", None, _D, _D, _D, _PD)
@@ -130,10 +135,13 @@ def _vp(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
 
 
-def make_term(eps_hor=0.01, r_esc=1e30, n_steps_cap=1000, dl=0.01, dl_r_scale=0.0, form=0) -> Term:
+def make_term(eps_hor=0.01, r_esc=1e30, n_steps_cap=1000, dl=0.01, dl_r_scale=0.0, form=0, method=0, rtol=0.0,
+              atol=0.0) -> Term:
     """form 0: geodesic equation (eq. geo); 1: canonical equations (eq. Ham)
-    with g of eq. kerr; 2: the same equations with g from eq. ADM."""
-    return Term(float(eps_hor), float(r_esc), int(n_steps_cap), float(dl), float(dl_r_scale), int(form))
+    with g of eq. kerr; 2: the same equations with g from eq. ADM.  method 0:
+    classical RK4; 1: Dormand-Prince 5(4) with step-size control (rtol, atol)."""
+    return Term(float(eps_hor), float(r_esc), int(n_steps_cap), float(dl), float(dl_r_scale), int(form),
+                int(method), float(rtol), float(atol))
 
 
 # ---------------------------------------------------------------- geometry
@@ -229,6 +237,18 @@ def rk4_step_adm(M, a, h, z):
     z = np.array(z, dtype=np.float64)
     lib().orc_rk4_step_adm(M, a, h, _p(z))
     return z
+
+
+def dopri5_tableau():
+    c, a, b, bh = np.zeros(7), np.zeros(49), np.zeros(7), np.zeros(7)
+    lib().orc_dopri5_tableau(_p(c), _p(a), _p(b), _p(bh))
+    return c, a.reshape(7, 7), b, bh
+
+
+def dopri5_linear(lam, h, y0):
+    y5, e = _D(), _D()
+    lib().orc_dopri5_linear_test(lam, h, y0, ctypes.byref(y5), ctypes.byref(e))
+    return y5.value, e.value
 
 
 def rk4_linear(lam, h, nsteps, y0):

@@ -423,6 +423,93 @@ void orc_rk4_step_adm(double M, double a, double h, double z[8]) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Dormand-Prince 5(4) (the paper's future work names more Runge-Kutta       */
+/* methods, Sec. 7) [not in paper]                                            */
+/* ------------------------------------------------------------------------ */
+
+/* The coefficients of Dormand & Prince, "A family of embedded Runge-Kutta
+ * formulae", J. Comput. Appl. Math. 6 (1980) 19-26: seven stages, the last
+ * evaluated at the fifth-order result (a_7j = b_j), so it is the first stage
+ * of the next step. */
+static const double DP_C[7] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0};
+static const double DP_A[7][7] = {
+    {0, 0, 0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0, 0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0, 0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0, 0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0, 0},
+    {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0}};
+static const double DP_B[7] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0.0};
+static const double DP_BH[7] = {5179.0 / 57600.0, 0.0,          7571.0 / 16695.0, 393.0 / 640.0,
+                                -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0};
+
+void orc_dopri5_tableau(double c[7], double a[49], double b[7], double bhat[7]) {
+  for (int i = 0; i < 7; ++i) {
+    c[i] = DP_C[i];
+    b[i] = DP_B[i];
+    bhat[i] = DP_BH[i];
+    for (int j = 0; j < 7; ++j) a[i * 7 + j] = DP_A[i][j];
+  }
+}
+
+/* One attempt of size h from y with k1 = f(y): the stage points
+ * y_i = y + h sum_j a_ij k_j and k_i = f(y_i) for i = 2..7, the fifth-order
+ * result y5 = y_7, the error estimate e = h sum_j (b_j - bhat_j) k_j, k7 =
+ * f(y5), and the smallest component `watch` among the stage points 2..7. */
+static void dopri5_attempt(orc_rhs_fn fn, const void* ctx, int dim, double h, const double* y,
+                           const double* k1, double* y5, double* e, double* k7, int watch, double* stage_min) {
+  double k[7][8], ys[8];
+  double mn = INFINITY;
+  for (int q = 0; q < dim; ++q) k[0][q] = k1[q];
+  for (int i = 1; i < 7; ++i) {
+    for (int q = 0; q < dim; ++q) {
+      double acc = 0.0;
+      for (int j = 0; j < i; ++j) acc += DP_A[i][j] * k[j][q];
+      ys[q] = y[q] + h * acc;
+    }
+    if (ys[watch] < mn) mn = ys[watch];
+    fn(ctx, ys, k[i]);
+  }
+  for (int q = 0; q < dim; ++q) {
+    y5[q] = ys[q];
+    k7[q] = k[6][q];
+    double acc = 0.0;
+    for (int j = 0; j < 7; ++j) acc += (DP_B[j] - DP_BH[j]) * k[j][q];
+    e[q] = h * acc;
+  }
+  if (stage_min) *stage_min = mn;
+}
+
+/* Root-mean-square error norm with the mixed scale atol + rtol max(|y|, |y5|)
+ * (Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.4). */
+static double dopri5_norm(int dim, const double* y, const double* y5, const double* e, double rtol, double atol) {
+  double s = 0.0;
+  for (int q = 0; q < dim; ++q) {
+    double sc = atol + rtol * fmax(fabs(y[q]), fabs(y5[q]));
+    s += (e[q] / sc) * (e[q] / sc);
+  }
+  return sqrt(s / dim);
+}
+
+/* Step-size factor after an attempt with error norm err (safety 0.9, bounds
+ * 0.2 and 10 on the factor, exponent 1/5 for the fifth-order pair; no
+ * increase right after a rejection). */
+static double dopri5_factor(double err, int accepted, int after_reject) {
+  const double safety = 0.9, fmin_ = 0.2, fmax_ = 10.0;
+  if (!accepted) return fmax(fmin_, safety * pow(err, -0.2));
+  double f = err > 0.0 ? fmin(fmax_, fmax(fmin_, safety * pow(err, -0.2))) : fmax_;
+  if (after_reject && f > 1.0) f = 1.0;
+  return f;
+}
+
+void orc_dopri5_linear_test(double lam, double h, double y0, double* y5, double* err) {
+  double k1 = lam * y0, k7, e;
+  dopri5_attempt(lin_fn, &lam, 1, h, &y0, &k1, y5, &e, &k7, 0, NULL);
+  *err = e;
+}
+
+/* ------------------------------------------------------------------------ */
 /* integration with termination                                              */
 /* ------------------------------------------------------------------------ */
 
@@ -487,7 +574,58 @@ int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, dou
   }
   if (ns) memcpy(traj, y, 8 * sizeof(double));
   orc_bh bh = {M, a};
-  while (n < t->n_steps_cap) {
+  if (t->method == 1) {
+    /* Dormand-Prince 5(4) with step-size control; n counts attempts; the
+     * termination tests follow every attempt (capture and non-finite on the
+     * attempted state, escape on accepted states) */
+    double h = t->dl > 0.0 ? t->dl : t->dl_r_scale * z[1];
+    double k1[8], y5[8], e[8], k7[8];
+    int after_reject = 0;
+    rhs(&bh, z, k1);
+    while (n < t->n_steps_cap) {
+      if (t->dl_r_scale > 0.0 && h > t->dl_r_scale * z[1]) h = t->dl_r_scale * z[1];
+      double r_stage_min;
+      dopri5_attempt(rhs, &bh, 8, h, z, k1, y5, e, k7, 1, &r_stage_min);
+      ++n;
+      int done = 0;
+      if (y5[1] <= r_cap || r_stage_min <= r_cap) {
+        fate = ORC_FATE_CAPTURED;
+        done = 1;
+      } else if (!all_finite(y5)) {
+        fate = ORC_FATE_NONFINITE;
+        done = 1;
+      }
+      if (done) {
+        memcpy(z, y5, 8 * sizeof(double));
+        lam += h;
+      } else {
+        double err = dopri5_norm(8, z, y5, e, t->rtol, t->atol);
+        if (err <= 1.0) {
+          memcpy(z, y5, 8 * sizeof(double));
+          memcpy(k1, k7, 8 * sizeof(double));
+          lam += h;
+          h *= dopri5_factor(err, 1, after_reject);
+          after_reject = 0;
+          if (z[1] >= t->r_esc) {
+            fate = ORC_FATE_ESCAPED;
+            done = 1;
+          }
+        } else {
+          h *= dopri5_factor(err, 0, 0);
+          after_reject = 1;
+        }
+      }
+      if (ns && n % stride == 0) {
+        double* s = traj + (size_t)(n / stride) * 8;
+        if (canonical)
+          canonical_to_state(M, a, form, z, s);
+        else
+          memcpy(s, z, 8 * sizeof(double));
+      }
+      if (done) break;
+    }
+  }
+  while (t->method != 1 && n < t->n_steps_cap) {
     double h = (t->dl_r_scale > 0.0) ? t->dl_r_scale * z[1] : t->dl;
     double r_stage_min;
     rk4_generic(rhs, &bh, 8, h, z, 1, &r_stage_min);

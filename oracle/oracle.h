@@ -44,6 +44,13 @@ typedef struct {
                              with g of eq. kerr;
                           2: the same equations with g built from the lapse,
                              shift and 3-metric of eq. ADM */
+  uint32_t method;     /* 0: classical RK4 with the fixed step rule above;
+                          1: Dormand-Prince 5(4) with step-size control:
+                             first trial step dl (or dl_r_scale r0 if dl = 0),
+                             every step at most dl_r_scale r when dl_r_scale > 0,
+                             local error norm against atol + rtol |y|;
+                             n_steps_cap and the step count then count attempts */
+  double rtol, atol;   /* tolerances of method 1 (atol > 0) */
 } orc_term;
 
 /* -------- geometry (Sec. 2, eq. kerr) -------- */
@@ -71,6 +78,12 @@ void orc_rk4_linear_test(double lam, double h, int nsteps, double* y);   /* RK4 
 void orc_rk4_step(double M, double a, double h, double y[8]);
 void orc_rk4_step_hamiltonian(double M, double a, double h, double z[8]);
 void orc_rk4_step_adm(double M, double a, double h, double z[8]);
+/* Dormand-Prince 5(4) tableau: c[7], a[7*7] row-major (strictly lower), the
+ * fifth-order weights b[7] and the embedded fourth-order weights bhat[7]. */
+void orc_dopri5_tableau(double c[7], double a[49], double b[7], double bhat[7]);
+/* One Dormand-Prince attempt of size h on y' = lam y (y scalar): y5, and the
+ * error estimate y5 - y4 in *err. */
+void orc_dopri5_linear_test(double lam, double h, double y0, double* y5, double* err);
 
 /* -------- integration with termination (Sec. 5) -------- */
 int orc_trace_one(double M, double a, const double y0[8], const orc_term* t,

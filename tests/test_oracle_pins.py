@@ -939,3 +939,96 @@ def test_adm_trace_matches_canonical_and_conserves(orc):
         res = orc.trace_one(1.0, a, y0, orc.make_term(n_steps_cap=5000, dl=0.02, form=2))
         assert abs(res["y"][1] - r0) < 1e-9
         assert res["y"][3] == pytest.approx(y0[7] / y0[4] * res["y"][0], rel=1e-10)
+
+
+# --------------------------------------------------------------------------- Dormand-Prince 5(4)
+def _rk_order_conditions(b, A, c, order):
+    """Residuals of the Runge-Kutta order conditions (Butcher trees) up to
+    `order` (at most 5) for weights b, matrix A, nodes c."""
+    one = np.ones_like(c)
+    Ac = A @ c
+    res = [b @ one - 1.0]
+    if order >= 2:
+        res += [b @ c - 1 / 2]
+    if order >= 3:
+        res += [b @ c**2 - 1 / 3, b @ Ac - 1 / 6]
+    if order >= 4:
+        res += [b @ c**3 - 1 / 4, b @ (c * Ac) - 1 / 8, b @ (A @ c**2) - 1 / 12, b @ (A @ Ac) - 1 / 24]
+    if order >= 5:
+        res += [b @ c**4 - 1 / 5, b @ (c**2 * Ac) - 1 / 10, b @ (c * (A @ c**2)) - 1 / 15,
+                b @ (c * (A @ Ac)) - 1 / 30, b @ (Ac * Ac) - 1 / 20, b @ (A @ c**3) - 1 / 20,
+                b @ (A @ (c * Ac)) - 1 / 40, b @ (A @ (A @ c**2)) - 1 / 60, b @ (A @ (A @ Ac)) - 1 / 120]
+    return np.array(res)
+
+
+def test_dopri5_tableau_satisfies_order_conditions(orc):
+    """The typed Dormand-Prince coefficients against the theory they must
+    satisfy: row sums equal the nodes, the fifth-order weights meet all 17
+    conditions to order 5, the embedded weights all 8 to order 4 but not all
+    of order 5, and the last stage is the fifth-order result (FSAL)."""
+    c, A, b, bh = orc.dopri5_tableau()
+    np.testing.assert_allclose(A.sum(axis=1), c, atol=1e-15)
+    assert np.all(np.triu(A) == 0.0)
+    assert np.abs(_rk_order_conditions(b, A, c, 5)).max() < 1e-15
+    assert np.abs(_rk_order_conditions(bh, A, c, 4)).max() < 1e-15
+    assert np.abs(_rk_order_conditions(bh, A, c, 5)[8:]).max() > 1e-5
+    np.testing.assert_array_equal(A[6], b)
+
+
+def test_dopri5_linear_step_is_its_stability_polynomial(orc):
+    """On y' = lam y one Dormand-Prince step multiplies y by the stability
+    function R(z) = sum_{k<=5} z^k/k! + z^6/600 (Hairer & Wanner, Solving
+    ODEs II, Sec. IV.2), and its error estimate falls as h^5."""
+    for z in (-0.5, -0.1, 0.05, 0.3, -2.0):
+        y5, _ = orc.dopri5_linear(z, 1.0, 1.0)
+        R = sum(z**k / math.factorial(k) for k in range(6)) + z**6 / 600
+        assert y5 == pytest.approx(R, rel=1e-14, abs=1e-16)
+    e1 = abs(orc.dopri5_linear(-1.0, 0.1, 1.0)[1])
+    e2 = abs(orc.dopri5_linear(-1.0, 0.05, 1.0)[1])
+    assert 28.0 < e1 / e2 < 36.0
+
+
+def test_dopri5_trace_meets_tolerance(orc):
+    """Adaptive traces of generic bound Kerr orbits (3000 attempts): E, L_z,
+    Q and the norm, exact invariants of the flow, drift by less than the
+    attempts times the tolerance, ten times less at tolerance 1e-12 than at
+    1e-10, and the tighter tolerance covers less lambda in as many attempts; a circular orbit stays at r0 with phi advancing at the
+    angular frequency of eq. omega."""
+    ys, spins, _ = orc.bound_samples(1.0, 0.9, 11, np.arange(8), spin_fixed=True)
+    drift, rate = {}, {}
+    for tol in (1e-10, 1e-12):
+        t = orc.make_term(n_steps_cap=3000, dl=0.01, method=1, rtol=tol, atol=tol)
+        d_max, lam_sum = 0.0, 0.0
+        for i in range(ys.shape[1]):
+            got = orc.trace_one(1.0, 0.9, ys[:, i], t)
+            assert got["fate"] == 3 and got["steps"] == 3000
+            i0, i1 = orc.invariants(1.0, 0.9, ys[:, i]), orc.invariants(1.0, 0.9, got["y"])
+            d_max = max(d_max, (np.abs(i1 - i0) / np.maximum(np.abs(i0), 1.0)).max())
+            lam_sum += got["lambda"]
+        drift[tol], rate[tol] = d_max, lam_sum
+    # the local error per accepted step is held below tol (times the scale
+    # of the state); over 3000 attempts the drift stays below 3000 tol
+    assert drift[1e-10] < 3000 * 1e-10 and drift[1e-12] < 3000 * 1e-12, drift
+    assert drift[1e-12] < drift[1e-10] / 10, drift
+    assert rate[1e-12] < rate[1e-10], rate
+    y0 = orc.circular_state(1.0, 0.7, 7.0, 1)
+    res = orc.trace_one(1.0, 0.7, y0, orc.make_term(n_steps_cap=3000, dl=0.1, method=1, rtol=1e-11, atol=1e-11))
+    assert res["fate"] == 3 and abs(res["y"][1] - 7.0) < 1e-8
+    assert res["y"][3] == pytest.approx(y0[7] / y0[4] * res["y"][0], rel=1e-8)
+
+
+def test_dopri5_step_control_and_capture(orc):
+    """The controller grows a tiny first step (far fewer attempts than
+    lambda / dl), caps steps at dl_r_scale r, and a radially infalling ray is
+    captured as with RK4."""
+    y0 = orc.circular_state(1.0, 0.0, 10.0, 1)
+    res = orc.trace_one(1.0, 0.0, y0, orc.make_term(n_steps_cap=500, dl=1e-6, method=1, rtol=1e-9, atol=1e-9))
+    assert res["lambda"] > 1e3 * 1e-6 * res["steps"]
+    capped = orc.trace_one(1.0, 0.0, y0, orc.make_term(n_steps_cap=200, dl=1e-6, dl_r_scale=0.01, method=1,
+                                                        rtol=1e-6, atol=1e-6))
+    assert capped["lambda"] <= 0.01 * 10.0 * 200 * (1 + 1e-12)
+    # radial infall from rest at r = 10 (Schwarzschild): u^t = 1/sqrt(1 - 2/10)
+    yi = np.array([0.0, 10.0, math.pi / 2, 0.0, 1.0 / math.sqrt(0.8), 0.0, 0.0, 0.0])
+    a = orc.trace_one(1.0, 0.0, yi, orc.make_term(n_steps_cap=10000, dl=0.01, method=1, rtol=1e-9, atol=1e-9))
+    b = orc.trace_one(1.0, 0.0, yi, orc.make_term(n_steps_cap=10000, dl=0.01))
+    assert a["fate"] == b["fate"] == 1
