@@ -514,6 +514,57 @@ def run_paper_case(mb, torch, stream, stride: int = 10) -> dict:
             "paper_hardware": "GTX 960M (Maxwell), CUDA 7.5; the paper's numbers are context, not a target"}
 
 
+def q_ratio(finals):
+    """The paper's self-convergence ratio Q = |y_h - y_h/2| / |y_h/2 - y_h/4|
+    (Sec. 6.3, eq. Qt; 2^4 for a fourth-order method), per ray from the max
+    over state components; rays with a non-finite or vanishing difference
+    are left out."""
+    import numpy as np
+
+    d1 = np.abs(finals[0] - finals[1]).max(axis=0)
+    d2 = np.abs(finals[1] - finals[2]).max(axis=0)
+    ok = np.isfinite(d1) & np.isfinite(d2) & (d2 > 1e-12)
+    q = d1[ok] / d2[ok]
+    return {"rays": int(ok.sum()), "of": int(d1.size), "median": float(np.median(q)) if q.size else None,
+            "frac_13_19": float(np.mean((q > 13.0) & (q < 19.0))) if q.size else None}
+
+
+def run_convergence_case(mb, torch, stream) -> dict:
+    """The paper's self-convergence test (Sec. 6.3) on the GPU, FP64, for the
+    three physics configurations: each traced with fixed steps h, h/2, h/4 to
+    the same affine parameter (camera rays with a fixed step, which is what
+    the test is defined for, from their camera initial states)."""
+    import numpy as np
+
+    from paper_1803_08320_gb300 import workloads as W
+
+    out = {}
+    cases = []
+    wl = W.circular()
+    cases.append(("1_schwarzschild_circular_1024", 0.0, mb.ic_circular(1.0, 0.0, wl.radii), None,
+                  (0.4, 0.2, 0.1), 400.0))
+    cw = W.camera(nx=128, ny=128)
+    cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
+    cases.append(("2_kerr_a0.9_camera_128x128", cw.a, mb.ic_camera(cw.M, cw.a, cam, np.arange(cw.n)), None,
+                  (0.2, 0.1, 0.05), 1040.0))
+    bw = W.bound()
+    ics, spins, _ = mb.ic_bound(bw.M, bw.a_max, bw.seed, 1024)
+    cases.append(("3_kerr_generic_bound_1024", 0.0, ics, spins, (0.1, 0.05, 0.025), 100.0))
+    with torch.cuda.stream(stream):
+        for name, a, y0, spins, hs, lam_end in cases:
+            finals = []
+            for h in hs:
+                t = W.Termination(eps_hor=0.01, r_esc=1e9, n_steps_cap=int(round(lam_end / h)), dl=h)
+                r = mb.trace(1.0, a, y0, t, precision="fp64", stream=stream, a_per_ray=spins)
+                stream.synchronize()
+                keep = (r["fate"] == mb.FATE_CAPPED)
+                y = r["y"].clone()
+                y[:, ~keep] = float("nan")
+                finals.append(y.cpu().numpy())
+            out[name] = dict(q_ratio(finals), h=list(hs), affine_end=lam_end)
+    return out
+
+
 def serving_bundle(mb, r):
     return bundle_of(mb, r.kind, r.n, r.a, r.cap, r.incl, r.seed, side=r.side)
 
@@ -670,6 +721,7 @@ def run_workload(args) -> None:
                          "gpu_launches": args.steps, "bundles": res})
         elif args.workload == "paper":
             res = run_paper_case(mb, torch, stream)
+            res["self_convergence"] = run_convergence_case(mb, torch, stream)
             big = res["rows"][-1]
             line.update({"value": big["final"]["steps_per_s"], "ms_per_step": 1e3 * big["final"]["seconds"],
                          "dtype": "f64",

@@ -84,7 +84,8 @@ typedef struct {
 /* Step rule and termination.  The step is h = dl, or h = dl_r_scale * r_n
  * (r at the start of the step, held for all four stages) when
  * dl_r_scale > 0.  The paper uses a fixed h (Sec. 6).  Requires eps_hor >= 0,
- * r_esc > (1+eps_hor) r_+, and a finite positive step.
+ * r_esc > (1+eps_hor) r_+, and a finite positive step (for DOPRI5 below,
+ * dl >= 0 when dl_r_scale > 0).
  * form: the equations RK4 integrates --
  *   MALBEC_FORM_GEODESIC     (0) the geodesic equation in (x^mu, u^mu),
  *                            du/dl = -Gamma u u (Sec. 2, eq. geo);
@@ -106,10 +107,35 @@ typedef struct {
  *                            points and precisions as form 1; the same flow,
  *                            so its RK4 map equals form 1's up to rounding.
  * Inputs and outputs are (x, u) states in every form; the geodesic and the
- * canonical maps agree to O(h^4) per unit lambda. */
+ * canonical maps agree to O(h^4) per unit lambda.
+ * method: the integrator --
+ *   MALBEC_METHOD_RK4     (0) classical fourth-order Runge-Kutta with the
+ *                         step rule above (the paper's, Sec. 5);
+ *   MALBEC_METHOD_DOPRI5  (1) the Dormand-Prince 5(4) embedded pair
+ *                         (Dormand & Prince 1980) with step-size control,
+ *                         one of the further Runge-Kutta methods the paper's
+ *                         conclusions name.  The first trial step is dl (or
+ *                         dl_r_scale r_0 when dl = 0); when dl_r_scale > 0
+ *                         every step is at most dl_r_scale r (r at its start).
+ *                         An attempt is accepted when the RMS over the 8
+ *                         state components of e_i / (atol + rtol max(|y_i|,
+ *                         |y5_i|)) is <= 1 (e = fifth- minus fourth-order
+ *                         result); the next step is h min(10, max(0.2,
+ *                         0.9 err^-1/5)), not above h right after a
+ *                         rejection, and max(0.2, 0.9 err^-1/5) h after one.
+ *                         n_steps_cap, the reported steps and the trajectory
+ *                         stride count attempts; capture and non-finite are
+ *                         tested on every attempt (at its result and its
+ *                         stage points, as for RK4), escape on accepted
+ *                         steps.  Requires atol > 0, rtol >= 0, form
+ *                         MALBEC_FORM_GEODESIC and MALBEC_FP64; malbec_trace,
+ *                         malbec_trace_noalloc and malbec_trace_camera only.
+ * rtol, atol: the tolerances of MALBEC_METHOD_DOPRI5 (ignored by RK4). */
 #define MALBEC_FORM_GEODESIC 0
 #define MALBEC_FORM_HAMILTONIAN 1
 #define MALBEC_FORM_ADM 2
+#define MALBEC_METHOD_RK4 0
+#define MALBEC_METHOD_DOPRI5 1
 typedef struct {
   double eps_hor;
   double r_esc;
@@ -117,6 +143,9 @@ typedef struct {
   double dl;
   double dl_r_scale;
   uint32_t form;
+  uint32_t method;
+  double rtol;
+  double atol;
 } malbec_term;
 
 typedef enum {

@@ -40,6 +40,18 @@ int check_term(const malbec_term& t, const malbec_metric& m) {
   if (!scaled && !finite_pos(t.dl)) return MALBEC_EINVAL;
   const double rp = m.a_per_ray ? 2.0 * m.M : host_r_plus(m.M, m.a);
   if (!isfinite(t.r_esc) || !(t.r_esc > (1.0 + t.eps_hor) * rp)) return MALBEC_EINVAL;
+  if (t.method != MALBEC_METHOD_RK4 && t.method != MALBEC_METHOD_DOPRI5) return MALBEC_EINVAL;
+  if (t.method == MALBEC_METHOD_DOPRI5) {
+    if (t.form != MALBEC_FORM_GEODESIC) return MALBEC_EINVAL;
+    if (!finite_pos(t.atol) || !isfinite(t.rtol) || t.rtol < 0.0) return MALBEC_EINVAL;
+    if (scaled && (!isfinite(t.dl) || t.dl < 0.0)) return MALBEC_EINVAL;
+  }
+  return MALBEC_OK;
+}
+
+// The adaptive method runs in FP64 only.
+int check_method_precision(const malbec_term& t, malbec_precision prec) {
+  if (t.method == MALBEC_METHOD_DOPRI5 && prec != MALBEC_FP64) return MALBEC_EINVAL;
   return MALBEC_OK;
 }
 
@@ -294,6 +306,8 @@ int malbec_trace(malbec_metric m, const double* ics, uint64_t n, malbec_term t, 
   if (rc) return rc;
   rc = check_term(t, m);
   if (rc) return rc;
+  rc = check_method_precision(t, prec);
+  if (rc) return rc;
   if (!ics || !out) return MALBEC_EINVAL;
   malbec_layout L;
   rc = malbec_out_layout(mode, prec, n, t.n_steps_cap, stride, &L);
@@ -310,6 +324,9 @@ int malbec_trace(malbec_metric m, const double* ics, uint64_t n, malbec_term t, 
   p.dl = t.dl;
   p.dl_r_scale = t.dl_r_scale;
   p.form = t.form;
+  p.method = t.method;
+  p.rtol = t.rtol;
+  p.atol = t.atol;
   p.cap = t.n_steps_cap;
   p.ics = ics;
   p.n = n;
@@ -373,6 +390,8 @@ int malbec_trace_camera(malbec_metric m, const malbec_camera* cam, malbec_term t
   if (rc) return rc;
   if (!out || ((uintptr_t)out & 255u) != 0) return MALBEC_EINVAL;
   if (prec != MALBEC_FP64 && prec != MALBEC_FP32_MIXED) return MALBEC_EINVAL;
+  rc = check_method_precision(t, prec);
+  if (rc) return rc;
   malbec_camera_layout L;
   rc = malbec_camera_out_layout(cam, &L);
   if (rc) return rc;
@@ -386,6 +405,9 @@ int malbec_trace_camera(malbec_metric m, const malbec_camera* cam, malbec_term t
   p.dl = t.dl;
   p.dl_r_scale = t.dl_r_scale;
   p.form = t.form;
+  p.method = t.method;
+  p.rtol = t.rtol;
+  p.atol = t.atol;
   p.cap = t.n_steps_cap;
   p.n = (uint64_t)cam->nx * cam->ny;
   p.cam = make_camera_const(m.M, m.a, *cam);

@@ -37,7 +37,8 @@ CameraFields camera_fields(uint64_t n) {
 
 int validate(const malbec_bundle& b, malbec_precision prec) {
   if (b.n == 0 || !b.out || ((uintptr_t)b.out & 255u) != 0) return MALBEC_EINVAL;
-  if (b.term.form != MALBEC_FORM_GEODESIC) return MALBEC_EINVAL;  // job tables: geodesic form
+  // job tables: geodesic form, classical RK4
+  if (b.term.form != MALBEC_FORM_GEODESIC || b.term.method != MALBEC_METHOD_RK4) return MALBEC_EINVAL;
   const malbec_metric m = {b.M, b.a, nullptr};
   int rc = check_metric(m);
   if (rc) return rc;

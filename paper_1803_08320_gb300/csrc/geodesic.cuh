@@ -561,3 +561,95 @@ __device__ __forceinline__ void invariants64(double M, double a, const double y[
 }
 
 }  // namespace malbec
+
+namespace malbec {
+
+// ---------------------------------------------------------------------------
+// Dormand-Prince 5(4) (Dormand & Prince, J. Comput. Appl. Math. 6 (1980)
+// 19-26), one of the further Runge-Kutta methods the paper's conclusions
+// name: seven stages, the seventh taken at the fifth-order result, so that
+// it is the first stage of the next step (k1 = k7 of the last accepted
+// attempt).  One attempt of size h from y (geodesic form) with k1 = f(y):
+// y5 (fifth order), e = y5 - y4 (the embedded fourth-order result), k7 =
+// f(y5); returns the smallest radius among the stage points 2..7.  One sincos
+// per attempt: the stage angles are reached by stage_trig.
+template <bool kKerr>
+__device__ __forceinline__ double dopri5_attempt(const BH<double>& bh, double h, const double y[8],
+                                                 const double k1[8], double y5[8], double e[8], double k7[8]) {
+  double s0, c0;
+  sincos(y[2], &s0, &c0);
+  double k2[8], k3[8], k4[8], k5[8], k6[8];
+  double d[8];
+  double rmin = 0.0;
+  // k = f(y + h d): stage velocity (the first half of k) and acceleration
+  auto stage = [&](double k[8], bool first) {
+    const double r = fma(h, d[1], y[1]);
+    const double th = fma(h, d[2], y[2]);
+    double sn, cs;
+    stage_trig<double>(s0, c0, h * d[2], th, &sn, &cs);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) k[j] = fma(h, d[4 + j], y[4 + j]);
+    accel_sc<kKerr, double>(bh, r, sn, cs, k[0], k[1], k[2], k[3], k + 4);
+    rmin = first ? r : fmin(rmin, r);
+  };
+#pragma unroll
+  for (int q = 0; q < 8; ++q) d[q] = (1.0 / 5.0) * k1[q];
+  stage(k2, true);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) d[q] = fma(3.0 / 40.0, k1[q], (9.0 / 40.0) * k2[q]);
+  stage(k3, false);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) d[q] = fma(44.0 / 45.0, k1[q], fma(-56.0 / 15.0, k2[q], (32.0 / 9.0) * k3[q]));
+  stage(k4, false);
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    d[q] = fma(19372.0 / 6561.0, k1[q],
+               fma(-25360.0 / 2187.0, k2[q], fma(64448.0 / 6561.0, k3[q], (-212.0 / 729.0) * k4[q])));
+  stage(k5, false);
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    d[q] = fma(9017.0 / 3168.0, k1[q],
+               fma(-355.0 / 33.0, k2[q],
+                   fma(46732.0 / 5247.0, k3[q], fma(49.0 / 176.0, k4[q], (-5103.0 / 18656.0) * k5[q]))));
+  stage(k6, false);
+  // the fifth-order weights (a_2 = 0)
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    d[q] = fma(35.0 / 384.0, k1[q],
+               fma(500.0 / 1113.0, k3[q], fma(125.0 / 192.0, k4[q], fma(-2187.0 / 6784.0, k5[q], (11.0 / 84.0) * k6[q]))));
+#pragma unroll
+  for (int q = 0; q < 8; ++q) y5[q] = fma(h, d[q], y[q]);
+  stage(k7, false);
+  // e = h sum_j (b_j - bhat_j) k_j
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    e[q] = h * fma(71.0 / 57600.0, k1[q],
+                   fma(-71.0 / 16695.0, k3[q],
+                       fma(71.0 / 1920.0, k4[q],
+                           fma(-17253.0 / 339200.0, k5[q], fma(22.0 / 525.0, k6[q], (-1.0 / 40.0) * k7[q])))));
+  return rmin;
+}
+
+// RMS error norm of an attempt with the scale atol + rtol max(|y|, |y5|)
+// (Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.4), and the step-size
+// factor that follows it: safety 0.9, factor within [0.2, 10], exponent 1/5,
+// no increase right after a rejection.
+__device__ __forceinline__ double dopri5_norm(const double y[8], const double y5[8], const double e[8], double rtol,
+                                              double atol) {
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double t = e[q] / fma(rtol, fmax(fabs(y[q]), fabs(y5[q])), atol);
+    s = fma(t, t, s);
+  }
+  return sqrt(0.125 * s);
+}
+
+__device__ __forceinline__ double dopri5_factor(double err, bool accepted, bool after_reject) {
+  if (!accepted) return fmax(0.2, 0.9 * pow(err, -0.2));
+  double f = err > 0.0 ? fmin(10.0, fmax(0.2, 0.9 * pow(err, -0.2))) : 10.0;
+  if (after_reject && f > 1.0) f = 1.0;
+  return f;
+}
+
+}  // namespace malbec

@@ -75,6 +75,8 @@ struct TraceParams {
   int zone_batch, zone_wait;
   int exchange;       // FP32_MIXED: block ray exchange on (1) / off (0)
   uint32_t form;      // MALBEC_FORM_*
+  uint32_t method;    // MALBEC_METHOD_*
+  double rtol, atol;  // MALBEC_METHOD_DOPRI5 tolerances
   // work queue (scratch, zeroed before launch)
   unsigned long long* head;
   // multi-job source: job table, per-job counters (zeroed), longest-first
@@ -127,6 +129,7 @@ int set_cuda_error(cudaError_t e);
 void fill_zone(TraceParams& p);
 int check_metric(const malbec_metric& m);
 int check_term(const malbec_term& t, const malbec_metric& m);
+int check_method_precision(const malbec_term& t, malbec_precision prec);
 int choose_shape(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, LaunchShape* shape, int* refill_min);
 int choose_shape_cfg(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, const malbec_launch_config& cfg,
                      LaunchShape* shape, int* refill_min);

@@ -62,6 +62,8 @@ extern "C" int malbec_trace_noalloc(malbec_metric m, const double* ics, uint64_t
   if (rc) return rc;
   rc = check_term(t, m);
   if (rc) return rc;
+  rc = check_method_precision(t, prec);
+  if (rc) return rc;
   if (!ics || !out) return MALBEC_EINVAL;
   malbec_layout L;
   rc = malbec_out_layout(mode, prec, n, t.n_steps_cap, stride, &L);
@@ -79,6 +81,9 @@ extern "C" int malbec_trace_noalloc(malbec_metric m, const double* ics, uint64_t
   p.dl = t.dl;
   p.dl_r_scale = t.dl_r_scale;
   p.form = t.form;
+  p.method = t.method;
+  p.rtol = t.rtol;
+  p.atol = t.atol;
   p.cap = t.n_steps_cap;
   p.ics = ics;
   p.n = n;

@@ -368,11 +368,13 @@ __device__ __forceinline__ void to_velocity(double M, double a, const double z[8
 // budget is not the occupancy limit; without the minimum-blocks argument the
 // compiler capped some instantiations (the request-loop ones) at 128
 // registers and spilled.
-template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, int kForm>
+template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, int kForm, int kMethod>
 __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) {
   static_assert(!kBanks || kMixed, "block banks exist for FP32_MIXED only");
   constexpr bool kHam = kForm != MALBEC_FORM_GEODESIC;
   static_assert(!kHam || kKerr, "the canonical forms use the Kerr Hamiltonian (a = 0 included)");
+  constexpr bool kDopri = kMethod == MALBEC_METHOD_DOPRI5;
+  static_assert(!kDopri || (!kMixed && !kHam), "Dormand-Prince: FP64, geodesic form");
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const float k6h = (float)(1.0 / 6.0), k6l = (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0));
@@ -405,8 +407,13 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
   // and the flush points depend on the ray's own steps alone.
   float lam_h = 0.f, lam_l = 0.f;
   uint32_t lam_fix = 0;
+  // Dormand-Prince: the next step size, f(y) of the accepted state (the
+  // first stage of the next attempt) and whether the last attempt failed
+  double h_next = 0.0, k1d[8];
+  bool after_reject = false;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
+    k1d[c] = 0.0;
     y[c] = 0.0;
     hi[c] = 0.f;
     lo[c] = 0.f;
@@ -799,6 +806,14 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
           for (int c = 0; c < 4; ++c) y[4 + c] = pz[c];
           if constexpr (kMixed) split_pair(y, hi, lo);
         }
+        if constexpr (kDopri) {
+          // first trial step; k1 = f(y) for the first attempt
+          h_next = dl > 0.0 ? dl : dl_scale * y[1];
+          after_reject = false;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) k1d[c] = y[4 + c];
+          accel<kKerr, double>(bh64, y[1], y[2], y[4], y[5], y[6], y[7], k1d + 4);
+        }
       }
       continue;
     }
@@ -860,7 +875,35 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
     if (nst < cap) {
       // ---- one RK4 step
       bool captured, escaped, finite;
-      if (!kMixed) {
+      if constexpr (kDopri) {
+        // ---- one Dormand-Prince attempt: capture and non-finite on the
+        // attempted state, acceptance by the error norm, escape on accepted
+        // states; the step size adapts after every attempt
+        if (dl_scale > 0.0) h_next = fmin(h_next, dl_scale * y[1]);
+        const double h = h_next;
+        double y5[8], e[8], k7[8];
+        const double rmin = dopri5_attempt<kKerr>(bh64, h, y, k1d, y5, e, k7);
+        captured = (y5[1] <= r_cap) | (rmin <= r_cap);
+        finite = finite8(y5);
+        escaped = false;
+        bool accept = captured || !finite;
+        if (!accept) {
+          const double err = dopri5_norm(y, y5, e, p.rtol, p.atol);
+          accept = err <= 1.0;
+          h_next = h * dopri5_factor(err, accept, after_reject);
+          after_reject = !accept;
+          if (accept) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) k1d[c] = k7[c];
+            escaped = y5[1] >= r_esc;
+          }
+        }
+        if (accept) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) y[c] = y5[c];
+          lam += h;
+        }
+      } else if (!kMixed) {
         const double h = dl_scale > 0.0 ? dl_scale * y[1] : dl;
         double rmin;
         if constexpr (kHam)
@@ -1004,15 +1047,28 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
   }
 }
 
-template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, int kForm = MALBEC_FORM_GEODESIC>
+template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, int kForm = MALBEC_FORM_GEODESIC,
+          int kMethod = MALBEC_METHOD_RK4>
 const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&trace_kernel<kKerr, kMixed, kSrc, kSink, kBanks, kForm>);
+  return reinterpret_cast<const void*>(&trace_kernel<kKerr, kMixed, kSrc, kSink, kBanks, kForm, kMethod>);
 }
 
 // The kernel for a launch; FP32_MIXED kernels come with and without the
 // block ray exchange (two instantiations, so that the one without carries
 // none of its code).
-const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, int form) {
+const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, int form, int method) {
+  // Dormand-Prince 5(4): FP64, geodesic form (the Kerr right-hand side,
+  // a = 0 included), state arrays and cameras
+  if (method == MALBEC_METHOD_DOPRI5) {
+    if (mixed || form != MALBEC_FORM_GEODESIC) return nullptr;
+    if (src == kSrcStates && sink == kSinkFinal)
+      return kernel_ptr<true, false, kSrcStates, kSinkFinal, false, MALBEC_FORM_GEODESIC, MALBEC_METHOD_DOPRI5>();
+    if (src == kSrcStates && sink == kSinkStrided)
+      return kernel_ptr<true, false, kSrcStates, kSinkStrided, false, MALBEC_FORM_GEODESIC, MALBEC_METHOD_DOPRI5>();
+    if (src == kSrcCamera && sink == kSinkCamera)
+      return kernel_ptr<true, false, kSrcCamera, kSinkCamera, false, MALBEC_FORM_GEODESIC, MALBEC_METHOD_DOPRI5>();
+    return nullptr;
+  }
   // canonical forms (Sec. 2, eq. Ham, with g of eq. kerr or of eq. ADM):
   // state arrays and cameras
   if (form != MALBEC_FORM_GEODESIC) {
@@ -1058,7 +1114,7 @@ const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, int f
 }  // namespace
 
 int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, int threads_per_block) {
-  const void* k = pick(kerr, mixed, src, sink, mixed, MALBEC_FORM_GEODESIC);  // the larger of the two kernels
+  const void* k = pick(kerr, mixed, src, sink, mixed, MALBEC_FORM_GEODESIC, MALBEC_METHOD_RK4);  // the larger of the two
   if (!k) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads_per_block, 0) != cudaSuccess) return 0;
@@ -1072,7 +1128,7 @@ cudaError_t launch_trace(const TraceParams& p, bool kerr, bool mixed, Source src
   // zone), off for whole-image cameras (too few steps in their zone to pay
   // for a zone warp)
   const int exchange = p.exchange >= 0 ? p.exchange : (src == kSrcCamera ? 0 : 1);
-  const void* k = pick(kerr, mixed, src, sink, mixed && exchange == 1, (int)p.form);
+  const void* k = pick(kerr, mixed, src, sink, mixed && exchange == 1, (int)p.form, (int)p.method);
   if (!k) return cudaErrorInvalidValue;
   // automatic FP64-zone batch: 8 lanes with the exchange (a warp hands fewer
   // zone rays to the zone warp), a full warp without it (a zone step then

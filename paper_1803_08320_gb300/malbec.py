@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmalbec.so")
 
 FP64, FP32_MIXED = 0, 1
 FORM_GEODESIC, FORM_HAMILTONIAN, FORM_ADM = 0, 1, 2
+METHOD_RK4, METHOD_DOPRI5 = 0, 1
 OUT_FINAL, OUT_STRIDED = 0, 1
 FATE_CAPTURED, FATE_ESCAPED, FATE_CAPPED, FATE_NONFINITE = 1, 2, 3, 4
 OK, EINVAL, ENOMEM, EBUSY, ETIMEDOUT, ECUDA, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
@@ -36,7 +37,7 @@ class Metric(ctypes.Structure):
 
 class Term(ctypes.Structure):
     _fields_ = [("eps_hor", _D), ("r_esc", _D), ("n_steps_cap", _U32), ("dl", _D), ("dl_r_scale", _D),
-                ("form", _U32)]
+                ("form", _U32), ("method", _U32), ("rtol", _D), ("atol", _D)]
 
 
 class Camera(ctypes.Structure):
@@ -203,17 +204,25 @@ class Termination:
     dl: float = 0.01
     dl_r_scale: float = 0.0
     form: int = 0  # FORM_GEODESIC, FORM_HAMILTONIAN or FORM_ADM
+    method: int = 0  # METHOD_RK4 or METHOD_DOPRI5 (adaptive; rtol, atol)
+    rtol: float = 0.0
+    atol: float = 0.0
 
     def c(self) -> Term:
         return Term(float(self.eps_hor), float(self.r_esc), int(self.n_steps_cap), float(self.dl),
-                    float(self.dl_r_scale), int(self.form))
+                    float(self.dl_r_scale), int(self.form), int(self.method), float(self.rtol), float(self.atol))
 
 
-def term_from(t, form=None) -> Termination:
-    if isinstance(t, Termination) and form is None:
+def term_from(t, form=None, method=None, rtol=None, atol=None) -> Termination:
+    """A Termination from any object with the same fields (e.g. a workload's
+    term), optionally with another form or integrator."""
+    if isinstance(t, Termination) and form is None and method is None and rtol is None and atol is None:
         return t
     f = getattr(t, "form", 0) if form is None else form
-    return Termination(t.eps_hor, t.r_esc, t.n_steps_cap, t.dl, t.dl_r_scale, int(f))
+    m = getattr(t, "method", 0) if method is None else method
+    rt = getattr(t, "rtol", 0.0) if rtol is None else rtol
+    at = getattr(t, "atol", 0.0) if atol is None else atol
+    return Termination(t.eps_hor, t.r_esc, t.n_steps_cap, t.dl, t.dl_r_scale, int(f), int(m), float(rt), float(at))
 
 
 def _prec(p) -> int:

@@ -102,6 +102,11 @@ def test_trace_validation_rejects_before_any_cuda_call(mb):
         (mb.Metric(1.0, 0.5, None), _term(r_esc=1.5)),  # escape inside the capture radius
         (mb.Metric(1.0, 0.5, None), _term(eps_hor=-0.1)),
         (mb.Metric(1.0, 0.5, None), _term(form=3)),   # no such form
+        (mb.Metric(1.0, 0.5, None), _term(method=2)),  # no such integrator
+        (mb.Metric(1.0, 0.5, None), _term(method=1, rtol=1e-9, atol=0.0)),   # Dormand-Prince: atol > 0
+        (mb.Metric(1.0, 0.5, None), _term(method=1, rtol=-1.0, atol=1e-9)),
+        (mb.Metric(1.0, 0.5, None), _term(method=1, rtol=1e-9, atol=1e-9, form=1)),  # geodesic form only
+        (mb.Metric(1.0, 0.5, None), _term(method=1, rtol=1e-9, atol=1e-9, dl=-1.0, dl_r_scale=0.5)),
     ]
     for m, t in cases:
         assert lib.malbec_trace(m, fake, 10, t, mb.OUT_FINAL, 0, mb.FP64, fake, None) == mb.EINVAL
@@ -110,6 +115,9 @@ def test_trace_validation_rejects_before_any_cuda_call(mb):
     assert lib.malbec_trace(m, fake, 0, good, mb.OUT_FINAL, 0, mb.FP64, fake, None) == mb.EINVAL
     assert lib.malbec_trace(m, fake, 10, good, mb.OUT_STRIDED, 0, mb.FP64, fake, None) == mb.EINVAL
     assert lib.malbec_trace(m, fake, 10, good, mb.OUT_FINAL, 0, mb.FP64, ctypes.c_void_p(257), None) == mb.EINVAL
+    # Dormand-Prince runs in FP64 only
+    dp = _term(eps_hor=0.01, r_esc=1000.0, n_steps_cap=10, dl=0.01, method=1, rtol=1e-9, atol=1e-9)
+    assert lib.malbec_trace(m, fake, 10, dp, mb.OUT_FINAL, 0, mb.FP32_MIXED, fake, None) == mb.EINVAL
 
 
 

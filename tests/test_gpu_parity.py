@@ -110,7 +110,8 @@ def gpu_trace(mb, M, a, ics, term, **kw):
 
 def oracle_term(orc, t, form=None):
     f = getattr(t, "form", 0) if form is None else form
-    return orc.make_term(t.eps_hor, t.r_esc, t.n_steps_cap, t.dl, t.dl_r_scale, f)
+    return orc.make_term(t.eps_hor, t.r_esc, t.n_steps_cap, t.dl, t.dl_r_scale, f, getattr(t, "method", 0),
+                         getattr(t, "rtol", 0.0), getattr(t, "atol", 0.0))
 
 
 # --------------------------------------------------------------------------- initial data
@@ -527,3 +528,37 @@ def test_mixed_camera_pixel_agreement(mb, orc, W):
     # reading G19) the fates agree; near the axis both paths are ill-conditioned
     assert same[far & off_axis].mean() >= 0.9999
     assert (f64 == f32).mean() >= 0.99
+
+
+@pytest.mark.parametrize("config", ["circular", "camera", "bound"])
+def test_self_convergence_every_config(mb, W, config):
+    """The paper's self-convergence test (Sec. 6.3, eq. Qt) for the three
+    physics configurations: fixed steps h, h/2, h/4 to the same affine
+    parameter; Q = |y_h - y_h/2| / |y_h/2 - y_h/4| near 2^4 = 16 for the
+    bulk of the rays (camera rays from their camera initial states, with a
+    fixed step and no escape radius, so that every ray reaches the end)."""
+    if config == "circular":
+        wl = W.circular(n=256)
+        ics, spins, a, hs, lam_end = mb.ic_circular(1.0, 0.0, wl.radii), None, 0.0, (0.4, 0.2, 0.1), 400.0
+    elif config == "camera":
+        cw = W.camera(nx=48, ny=48)
+        cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
+        ics, spins, a, hs, lam_end = mb.ic_camera(cw.M, cw.a, cam, np.arange(cw.n)), None, cw.a, (0.2, 0.1, 0.05), 1040.0
+    else:
+        bw = W.bound()
+        ics, spins, _ = mb.ic_bound(bw.M, bw.a_max, bw.seed, 256)
+        a, hs, lam_end = 0.0, (0.1, 0.05, 0.025), 100.0
+    finals = []
+    for h in hs:
+        t = W.Termination(eps_hor=0.01, r_esc=1e9, n_steps_cap=int(round(lam_end / h)), dl=h)
+        r = gpu_trace(mb, 1.0, a, ics, t, a_per_ray=spins)
+        y = r["y"].copy()
+        y[:, r["fate"] != mb.FATE_CAPPED] = np.nan
+        finals.append(y)
+    d1 = np.abs(finals[0] - finals[1]).max(axis=0)
+    d2 = np.abs(finals[1] - finals[2]).max(axis=0)
+    ok = np.isfinite(d1) & np.isfinite(d2) & (d2 > 1e-12)
+    q = d1[ok] / d2[ok]
+    assert ok.sum() >= 0.5 * d1.size
+    assert 14.0 < np.median(q) < 18.0, np.median(q)
+    assert np.mean((q > 13.0) & (q < 19.0)) > 0.6, np.sort(q)
