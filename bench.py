@@ -540,9 +540,13 @@ def run_convergence_case(mb, torch, stream) -> dict:
 
     out = {}
     cases = []
+    # config 1's circular orbits with a radial kick u^r = 0.01: an exact
+    # circular orbit is a fixed point of the right-hand side in (r, theta, u),
+    # which RK4 follows exactly up to rounding, so Q needs some dynamics
     wl = W.circular()
-    cases.append(("1_schwarzschild_circular_1024", 0.0, mb.ic_circular(1.0, 0.0, wl.radii), None,
-                  (0.4, 0.2, 0.1), 400.0))
+    ic1 = mb.ic_circular(1.0, 0.0, wl.radii)
+    ic1[5] = 0.01
+    cases.append(("1_schwarzschild_circular_1024_kicked", 0.0, ic1, None, (1.6, 0.8, 0.4), 800.0))
     cw = W.camera(nx=128, ny=128)
     cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
     cases.append(("2_kerr_a0.9_camera_128x128", cw.a, mb.ic_camera(cw.M, cw.a, cam, np.arange(cw.n)), None,
@@ -942,6 +946,49 @@ def main():
             mb.FORM_ADM, "kerr_adm",
             "eq. Ham with H through the lapse, shift and 3-metric of eq. ADM (Kerr's, from a provider "
             "function of r, theta); the same discrete map as the canonical form up to rounding")
+        # ---------------- FP64, Dormand-Prince 5(4) with step-size control
+        # (tolerance 1e-9, steps at most 0.5 r), same protocol; accuracy of
+        # it and of the RK4 render against a tolerance-1e-12 reference render
+        term_dp = mb.term_from(cw.term, method=mb.METHOD_DOPRI5, rtol=1e-9, atol=1e-9)
+        term_dp = dataclasses.replace(term_dp, dl=0.0, dl_r_scale=0.5)
+        cwd = CameraRun(cw.M, cw.a, term_dp)
+        for _ in range(args.warmup):
+            mb.trace_camera(cw.M, cw.a, cam, term_dp, "fp64", stream=stream, out=out)
+        barrier()
+        torch.cuda.synchronize()
+        times_dp, res_dp = timed_renders(mb, cwd, cam, "fp64", args.steps, stream, flush, out=out)
+        torch.cuda.synchronize()
+        barrier()
+        att_dp = int(res_dp["steps"].to(torch.int64).sum().item())
+        t_dp = max_over_ranks(sum(times_dp) / 1e3)
+        # accuracy: drift of the flow's invariants on 65536 of the pixels
+        # (every 16th), traced as state arrays with each method
+        pix = torch.arange(0, cw.n, 16, dtype=torch.int64)
+        ics_s = mb.ic_camera(cw.M, cw.a, cam, pix.numpy(), stream=stream)
+        drift = {}
+        for name, tt in (("rk4_h0.05r", cw.term), ("dopri5_tol1e-9", term_dp)):
+            rr = mb.trace(cw.M, cw.a, ics_s, tt, precision="fp64", stream=stream)
+            torch.cuda.synchronize()
+            ok = rr["fate"] != mb.FATE_NONFINITE
+            dd = {}
+            for c, nm in enumerate(("E", "Lz", "Q", "norm")):
+                d = (rr["inv1"][c] - rr["inv0"][c]).abs()[ok]
+                d = d[torch.isfinite(d)]
+                dd[nm] = {"median": float(d.median().item()), "p99": float(torch.quantile(d, 0.99).item())}
+            drift[name] = dd
+        dopri5 = {"value": world * att_dp * args.steps / t_dp, "unit": "attempts/s",
+                  "ms_per_step": 1e3 * t_dp / args.steps,
+                  "rays_per_s": world * cw.n * args.steps / t_dp,
+                  "rays_per_s_rk4": world * cw.n * args.steps / t_total,
+                  "attempts_per_ray": att_dp / cw.n, "rk4_steps_per_ray": steps_per_render / cw.n,
+                  "rhs_per_ray": {"dopri5": 6.0 * att_dp / cw.n + 1.0, "rk4": 4.0 * steps_per_render / cw.n},
+                  "fate_agreement_vs_rk4": float((res_dp["fate"] == fate64).float().mean().item()),
+                  "tolerance": {"rtol": 1e-9, "atol": 1e-9, "max_step": "0.5 r"},
+                  "invariant_drift_65536_pixels": drift,
+                  "note": "Dormand-Prince 5(4) (MALBEC_METHOD_DOPRI5), the same camera; accuracy compared by "
+                          "the drift of E, L_z, Q and g(u,u) (exact invariants of the flow), since the final "
+                          "angles of escaped rays depend on where each method's last step crosses r_esc"}
+
         esc_b = (fate_bl == mb.FATE_ESCAPED) & (fate_adm == mb.FATE_ESCAPED)
         d_b = (theta_adm[esc_b] - theta_bl[esc_b]).abs()
         d_b = d_b[torch.isfinite(d_b)]
@@ -1005,6 +1052,7 @@ def main():
                         "the rays are built on the device from the camera description passed by value"},
         "canonical_form": canonical,
         "adm_form": adm_form,
+        "dopri5": dopri5,
         "fp32_mixed": {"value": value32, "unit": UNIT, "ms_per_step": 1e3 * t32 / args.steps,
                        "speedup_vs_fp64": value32 / value, "fate_agreement_vs_fp64": agree,
                        "escaped_error_vs_fp64": err_stats(torch, dth, dph),
