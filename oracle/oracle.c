@@ -492,15 +492,27 @@ static double dopri5_norm(int dim, const double* y, const double* y5, const doub
   return sqrt(s / dim);
 }
 
-/* Step-size factor after an attempt with error norm err (safety 0.9, bounds
- * 0.2 and 10 on the factor, exponent 1/5 for the fifth-order pair; no
- * increase right after a rejection). */
+/* Step-size factor after an attempt with error norm err: the usual
+ * 0.9 err^(-1/5) (safety 0.9, exponent 1/5 for the fifth-order pair) taken
+ * down to the grid 2^(j/4), j = floor(4 log2 0.9 - 0.8 log2 err), with j in
+ * [-10, 13] (factors 0.18 .. 9.5), j <= 0 for the step after a rejection and
+ * j <= -1 after a rejection itself.  The embedded error estimate is a small
+ * difference of O(1) terms, so err carries rounding noise of relative size
+ * ~1e-16 / tol; on the grid that noise changes the step only when it moves
+ * the exponent across an integer, and the sequence of steps is the same for
+ * any two correct implementations (a continuous factor would pass the noise
+ * into every step and end a fixed number of attempts at a slightly
+ * different lambda) [not in paper]. */
 static double dopri5_factor(double err, int accepted, int after_reject) {
-  const double safety = 0.9, fmin_ = 0.2, fmax_ = 10.0;
-  if (!accepted) return fmax(fmin_, safety * pow(err, -0.2));
-  double f = err > 0.0 ? fmin(fmax_, fmax(fmin_, safety * pow(err, -0.2))) : fmax_;
-  if (after_reject && f > 1.0) f = 1.0;
-  return f;
+  double q = err > 0.0 ? 4.0 * log2(0.9) - 0.8 * log2(err) : 13.0;
+  int jmax = accepted ? (after_reject ? 0 : 13) : -1;
+  if (q > (double)jmax) q = (double)jmax;
+  if (q < -10.0) q = -10.0;
+  int j = (int)floor(q);
+  int r = j & 3;        /* j mod 4, in 0..3 */
+  int e = (j - r) / 4;  /* floor(j / 4) */
+  static const double quarter[4] = {1.0, 1.1892071150027210667, 1.4142135623730950488, 1.6817928305074290861};
+  return ldexp(quarter[r], e);
 }
 
 void orc_dopri5_linear_test(double lam, double h, double y0, double* y5, double* err) {

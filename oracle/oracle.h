@@ -48,7 +48,8 @@ typedef struct {
                           1: Dormand-Prince 5(4) with step-size control:
                              first trial step dl (or dl_r_scale r0 if dl = 0),
                              every step at most dl_r_scale r when dl_r_scale > 0,
-                             local error norm against atol + rtol |y|;
+                             local error norm against atol + rtol |y|, step
+                             factor 0.9 err^(-1/5) taken down to the grid 2^(j/4);
                              n_steps_cap and the step count then count attempts */
   double rtol, atol;   /* tolerances of method 1 (atol > 0) */
 } orc_term;
