@@ -120,9 +120,12 @@ typedef struct {
  *                         An attempt is accepted when the RMS over the 8
  *                         state components of e_i / (atol + rtol max(|y_i|,
  *                         |y5_i|)) is <= 1 (e = fifth- minus fourth-order
- *                         result); the next step is h min(10, max(0.2,
- *                         0.9 err^-1/5)), not above h right after a
- *                         rejection, and max(0.2, 0.9 err^-1/5) h after one.
+ *                         result); the next step is h 2^(j/4) with
+ *                         j = floor(4 log2 0.9 - 0.8 log2 err) (0.9 err^-1/5
+ *                         taken down to a grid, so that the rounding noise
+ *                         of the error estimate does not reach the step
+ *                         sizes), j in [-10, 13], j <= 0 right after a
+ *                         rejection and j <= -1 after one.
  *                         n_steps_cap, the reported steps and the trajectory
  *                         stride count attempts; capture and non-finite are
  *                         tested on every attempt (at its result and its

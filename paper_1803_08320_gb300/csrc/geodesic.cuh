@@ -632,8 +632,14 @@ __device__ __forceinline__ double dopri5_attempt(const BH<double>& bh, double h,
 
 // RMS error norm of an attempt with the scale atol + rtol max(|y|, |y5|)
 // (Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.4), and the step-size
-// factor that follows it: safety 0.9, factor within [0.2, 10], exponent 1/5,
-// no increase right after a rejection.
+// factor that follows it: 0.9 err^(-1/5) taken down to the grid 2^(j/4),
+// j = floor(4 log2 0.9 - 0.8 log2 err) in [-10, 13], j <= 0 after a
+// rejection and j <= -1 for a rejected attempt.  The error estimate is a
+// small difference of O(1) stage terms and carries rounding noise of
+// relative size ~1e-16 / tol; on the grid that noise moves the step only
+// when it carries the exponent across an integer, so the sequence of steps
+// does not depend on rounding (and matches any other correct implementation
+// of the same rule) except at those rare crossings.
 __device__ __forceinline__ double dopri5_norm(const double y[8], const double y5[8], const double e[8], double rtol,
                                               double atol) {
   double s = 0.0;
@@ -646,10 +652,14 @@ __device__ __forceinline__ double dopri5_norm(const double y[8], const double y5
 }
 
 __device__ __forceinline__ double dopri5_factor(double err, bool accepted, bool after_reject) {
-  if (!accepted) return fmax(0.2, 0.9 * pow(err, -0.2));
-  double f = err > 0.0 ? fmin(10.0, fmax(0.2, 0.9 * pow(err, -0.2))) : 10.0;
-  if (after_reject && f > 1.0) f = 1.0;
-  return f;
+  double q = err > 0.0 ? 4.0 * log2(0.9) - 0.8 * log2(err) : 13.0;
+  const double jmax = accepted ? (after_reject ? 0.0 : 13.0) : -1.0;
+  q = fmax(fmin(q, jmax), -10.0);
+  const int j = (int)floor(q);
+  const int r = j & 3;          // j mod 4
+  const int e = (j - r) / 4;    // floor(j / 4)
+  const double quarter = r == 0 ? 1.0 : (r == 1 ? 1.1892071150027210667 : (r == 2 ? 1.4142135623730950488
+                                                                                    : 1.6817928305074290861));
+  return ldexp(quarter, e);
 }
-
 }  // namespace malbec

@@ -42,13 +42,13 @@ def dp_term(mb, tol=1e-10, **kw):
 def test_bound_orbits_match_oracle(mb, orc, W):
     """512 generic bound orbits (per-particle spin), 3000 attempts at
     tolerance 1e-10.  On the orbits whose oracle map is well conditioned
-    (>= 85%): fates and attempt counts equal the oracle's, states and lambda
+    (>= 97%): fates and attempt counts equal the oracle's, states and lambda
     within 1e-9.  The adaptive map is discontinuous where an attempt's error
-    norm sits at the acceptance threshold (reading G23), so on the others a
-    rounding difference can change the sequence of steps: there the result
-    must still be valid -- E, L_z, Q and the norm within 3000 x tol of their
-    initial values, like the oracle's, and the state within 1e-5 of the
-    oracle's."""
+    norm sits at the acceptance threshold or carries a step exponent across
+    an integer (reading G23), so on the others a rounding difference can
+    change the sequence of steps: there the result must still be valid --
+    E, L_z, Q and the norm within 3000 x tol of their initial values, and
+    the state within 1e-5 of the oracle's."""
     wl = W.bound()
     idx = wl.subsample(512)
     ys, spins, _ = orc.bound_samples(wl.M, wl.a_max, wl.seed, idx)
@@ -56,7 +56,7 @@ def test_bound_orbits_match_oracle(mb, orc, W):
     got = gpu_trace(mb, wl.M, 0.0, ys, t, a_per_ray=spins)
     ref, kappa = oracle_kappa(orc, wl.M, 0.0, ys, oracle_term(orc, t), a_per_ray=spins)
     good = kappa <= KAPPA_MAX
-    assert good.mean() >= 0.85
+    assert good.mean() >= 0.97
     assert np.array_equal(got["fate"][good], ref["fate"][good])
     assert np.array_equal(got["steps"][good].astype(np.uint32), ref["steps"][good])
     assert_states_close(got["y"][:, good], ref["y"][:, good], what="Dormand-Prince bound orbits")
