@@ -259,6 +259,9 @@ def run_profile_case(args) -> None:
     form = {"camera_canonical": mb.FORM_HAMILTONIAN, "camera_adm": mb.FORM_ADM}.get(args.profile_case,
                                                                                    mb.FORM_GEODESIC)
     term = mb.term_from(cw.term, form=form)
+    if args.profile_case == "camera_dopri5":
+        term = dataclasses.replace(mb.term_from(cw.term, method=mb.METHOD_DOPRI5, rtol=1e-9, atol=1e-9),
+                                   dl=0.0, dl_r_scale=0.5)
     for _ in range(max(1, args.steps)):
         res = mb.trace_camera(cw.M, cw.a, cam, term, prec)
     torch.cuda.synchronize()
@@ -805,7 +808,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="malbec", choices=["malbec", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", choices=["camera_fp64", "camera_mixed", "camera_canonical", "camera_adm"],
+    ap.add_argument("--profile-case", choices=["camera_fp64", "camera_mixed", "camera_canonical", "camera_adm",
+                                               "camera_dopri5"],
                     default=None,
                     help="small case for ncu: a 512x512 render of the same camera, --steps times")
     ap.add_argument("--workload", choices=["camera", "bundles", "serving", "bound", "paper"], default="camera",
