@@ -55,7 +55,14 @@ def kernel_source_hash() -> str:
 # estimate and 3 FMA each), 1 sincos and 3 stage-angle rotations (angle
 # addition with short Taylor series, about 19 FP64 operations each).
 FLOPS_PER_STEP = {"kerr": 4 * 120 + 102, "schw": 4 * 42 + 102, "kerr_canonical": 4 * 72 + 74,
-                  "kerr_adm": 4 * (65 + 34) + 74}
+                  "kerr_adm": 4 * (65 + 34) + 74,
+                  # Dormand-Prince 5(4) attempt: 6 Kerr right-hand sides, 272 for
+                  # the six stage combinations, 72 + 16 for the stage points and
+                  # the fifth-order result, 6 for the stage-angle offsets, 96 for
+                  # the error estimate, 33 for the error norm (its 8 divisions,
+                  # sqrt and log2 listed apart, like the 6 reciprocals, 1 sincos
+                  # and 6 stage-angle rotations)
+                  "kerr_dopri5": 6 * 120 + 272 + 72 + 16 + 6 + 96 + 33}
 PLUS_PER_STEP = {"reciprocal": 4, "sincos": 1, "stage_angle_rotation": 3}
 
 
@@ -987,6 +994,12 @@ def main():
                   "attempts_per_ray": att_dp / cw.n, "rk4_steps_per_ray": steps_per_render / cw.n,
                   "rhs_per_ray": {"dopri5": 6.0 * att_dp / cw.n + 1.0, "rk4": 4.0 * steps_per_render / cw.n},
                   "fate_agreement_vs_rk4": float((res_dp["fate"] == fate64).float().mean().item()),
+                  "roofline": {"bound": "alu", "peak": peak64, "unit": "GFLOP/s (FP64)",
+                               "flops_per_attempt": FLOPS_PER_STEP["kerr_dopri5"],
+                               "achieved": FLOPS_PER_STEP["kerr_dopri5"] * att_dp / (statistics.mean(times_dp) / 1e3)
+                               / 1e9,
+                               "frac": FLOPS_PER_STEP["kerr_dopri5"] * att_dp / (statistics.mean(times_dp) / 1e3)
+                               / 1e9 / peak64},
                   "tolerance": {"rtol": 1e-9, "atol": 1e-9, "max_step": "0.5 r"},
                   "invariant_drift_65536_pixels": drift,
                   "note": "Dormand-Prince 5(4) (MALBEC_METHOD_DOPRI5), the same camera; accuracy compared by "
