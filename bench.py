@@ -524,6 +524,60 @@ def run_paper_case(mb, torch, stream, stride: int = 10) -> dict:
             "paper_hardware": "GTX 960M (Maxwell), CUDA 7.5; the paper's numbers are context, not a target"}
 
 
+def drift_summary(mb, torch, r) -> dict:
+    """Median and p99 of |inv1 - inv0| (E, L_z, Q, g(u,u)) over the rays that
+    did not end non-finite."""
+    ok = r["fate"] != mb.FATE_NONFINITE
+    out = {}
+    for c, nm in enumerate(("E", "Lz", "Q", "norm")):
+        d = (r["inv1"][c] - r["inv0"][c]).abs()[ok]
+        d = d[torch.isfinite(d)]
+        out[nm] = {"median": float(d.median().item()), "p99": float(torch.quantile(d, 0.99).item())}
+    out["nonfinite"] = int((~ok).sum().item())
+    return out
+
+
+def run_integrators_case(mb, torch, stream, flush, K: int, warmup: int) -> dict:
+    """Work against accuracy on the camera workload (Kerr a = 0.9, 1024^2):
+    RK4 with the camera's step rule against Dormand-Prince 5(4) at several
+    tolerances (steps at most 0.5 r).  Per configuration: ms per render (CUDA
+    events, L2 flushed, K renders after `warmup`), RK4 steps or attempts per
+    ray, right-hand sides per ray, and the drift of the flow's invariants on
+    every 16th pixel traced as a state array."""
+    import numpy as np
+
+    from paper_1803_08320_gb300 import workloads as W
+
+    cw = W.camera()
+    cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
+    L = mb.camera_layout(cam)
+    out = torch.empty(L.total, dtype=torch.uint8, device="cuda")
+    ics_s = mb.ic_camera(cw.M, cw.a, cam, np.arange(0, cw.n, 16), stream=stream)
+    configs = [("rk4_h0.05r", mb.term_from(cw.term))]
+    for tol in (1e-6, 1e-7, 1e-8, 1e-9, 1e-10):
+        t = mb.term_from(cw.term, method=mb.METHOD_DOPRI5, rtol=tol, atol=tol)
+        configs.append((f"dopri5_tol{tol:g}", dataclasses.replace(t, dl=0.0, dl_r_scale=0.5)))
+    rows = {}
+    for name, t in configs:
+        run = CameraRun(cw.M, cw.a, t)
+        for _ in range(warmup):
+            mb.trace_camera(cw.M, cw.a, cam, t, "fp64", stream=stream, out=out)
+        torch.cuda.synchronize()
+        times, res = timed_renders(mb, run, cam, "fp64", K, stream, flush, out=out)
+        steps = int(res["steps"].to(torch.int64).sum().item())
+        rhs = (4.0 * steps if t.method == mb.METHOD_RK4 else 6.0 * steps + cw.n) / cw.n
+        rr = mb.trace(cw.M, cw.a, ics_s, t, precision="fp64", stream=stream)
+        torch.cuda.synchronize()
+        rows[name] = {"ms_per_render": statistics.mean(times), "steps_or_attempts_per_ray": steps / cw.n,
+                      "rhs_per_ray": rhs, "rays_per_s": cw.n / (statistics.mean(times) / 1e3),
+                      "invariant_drift_65536_pixels": drift_summary(mb, torch, rr)}
+    return {"workload": "kerr_camera_a0.9_1024x1024", "renders": K, "rows": rows}
+
+
+def cw_steps_per_s(row) -> float:
+    return row["steps_or_attempts_per_ray"] * row["rays_per_s"]
+
+
 def q_ratio(finals):
     """The paper's self-convergence ratio Q = |y_h - y_h/2| / |y_h/2 - y_h/4|
     (Sec. 6.3, eq. Qt; 2^4 for a fourth-order method), per ray from the max
@@ -742,6 +796,13 @@ def run_workload(args) -> None:
                          "config": {"workload": "paper_sec6.4_kerr_a0.5_h0.1_1e4steps_N10-50000",
                                     "l2": "one launch per N; the inputs fit in L2 for small N"},
                          "gpu_launches": 2 * len(res["rows"]) + 1, "paper": res})
+        elif args.workload == "integrators":
+            res = run_integrators_case(mb, torch, stream, flush, K=args.steps, warmup=args.warmup)
+            rk = res["rows"]["rk4_h0.05r"]
+            line.update({"value": cw_steps_per_s(rk), "ms_per_step": rk["ms_per_render"], "dtype": "f64",
+                         "config": {"workload": "kerr_camera_a0.9_1024x1024_rk4_vs_dopri5_tolerance_sweep",
+                                    "l2": "flushed by a 256 MB device write before every timed render"},
+                         "gpu_launches": args.steps * len(res["rows"]), "integrators": res})
         elif args.workload == "bound":
             res = run_bound_case(mb, torch, stream, flush, args.particles, args.bound_steps,
                                  ["fp64", "fp32_mixed"])
@@ -819,12 +880,15 @@ def main():
                                                "camera_dopri5"],
                     default=None,
                     help="small case for ncu: a 512x512 render of the same camera, --steps times")
-    ap.add_argument("--workload", choices=["camera", "bundles", "serving", "bound", "paper"], default="camera",
+    ap.add_argument("--workload", choices=["camera", "bundles", "serving", "bound", "paper", "integrators"],
+                    default="camera",
                     help="camera: the headline line (with a bundles and a serving sample); bundles: uneven "
                          "bundles, persistent graph launch vs one launch per bundle; serving: Poisson "
                          "arrivals at several rates, continuous batching vs one launch per request; bound: "
                          "2^20 generic bound Kerr orbits x 10^5 steps, FP64 and FP32_MIXED, drift and error "
-                         "vs the oracle on a 1024-particle subsample")
+                         "vs the oracle on a 1024-particle subsample; paper: the paper's timing experiment and "
+                         "its self-convergence test; integrators: RK4 against Dormand-Prince 5(4) at several "
+                         "tolerances on the camera (time, right-hand sides and invariant drift)")
     ap.add_argument("--particles", type=int, default=1 << 20, help="particles for --workload bound")
     ap.add_argument("--bound-steps", type=int, default=100_000, help="step cap for --workload bound")
     ap.add_argument("--bundle-count", type=int, default=None,
