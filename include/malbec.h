@@ -381,8 +381,10 @@ int malbec_trace_bundles(const malbec_bundle* bundles, uint32_t count, malbec_pr
  * buffers must stay valid while it is used.  Plans take the launch
  * configuration in force at creation, or the one malbec_plan_autotune picks:
  * it replays the plan under candidate configurations (block size, blocks per
- * SM, refill granularity, FP64-zone batching) on `stream`, blocking the
- * caller, and keeps the fastest (written to `best` if non-NULL). */
+ * SM, refill granularity, FP64-zone batching, block ray exchange) on
+ * `stream`, blocking the caller -- each once after a warm-up replay, the three
+ * fastest twice more -- and keeps the one with the best replay (written to
+ * `best` if non-NULL). */
 typedef struct malbec_plan malbec_plan;
 int malbec_plan_create(const malbec_bundle* bundles, uint32_t count, malbec_precision prec,
                        malbec_plan** plan);

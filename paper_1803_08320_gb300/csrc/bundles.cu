@@ -366,31 +366,42 @@ int malbec_plan_autotune(malbec_plan* plan, malbec_stream stream, malbec_launch_
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best_ms = 1e30f;
-  malbec_launch_config best_cfg = plan->cfg;
-  int rc = MALBEC_OK;
-  for (const malbec_launch_config& c : cand) {
-    rc = record_plan(plan, c);
-    if (rc) break;
-    cudaError_t e = cudaGraphLaunch(plan->exec, s);  // warm-up replay
+  // one replay of candidate c after `warm` untimed ones: its time in ms
+  auto time_candidate = [&](const malbec_launch_config& c, int warm, float* ms) -> int {
+    int r = record_plan(plan, c);
+    if (r) return r;
+    cudaError_t e = cudaSuccess;
+    for (int w = 0; w < warm && e == cudaSuccess; ++w) e = cudaGraphLaunch(plan->exec, s);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     if (e == cudaSuccess) e = cudaGraphLaunch(plan->exec, s);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    if (e != cudaSuccess) {
-      rc = set_cuda_error(e);
-      break;
+    if (e != cudaSuccess) return set_cuda_error(e);
+    cudaEventElapsedTime(ms, e0, e1);
+    return MALBEC_OK;
+  };
+  // every candidate once (after a warm-up replay), then the three fastest
+  // twice more: a candidate's time is the best of its replays, so a single
+  // disturbed replay does not decide the choice
+  std::vector<float> best_of(cand.size(), 1e30f);
+  int rc = MALBEC_OK;
+  for (size_t i = 0; i < cand.size() && rc == MALBEC_OK; ++i) rc = time_candidate(cand[i], 1, &best_of[i]);
+  std::vector<size_t> order(cand.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return best_of[x] < best_of[y]; });
+  for (size_t k = 0; k < order.size() && k < 3 && rc == MALBEC_OK; ++k)
+    for (int rep = 0; rep < 2 && rc == MALBEC_OK; ++rep) {
+      float ms = 0.f;
+      rc = time_candidate(cand[order[k]], 0, &ms);
+      if (rc == MALBEC_OK && ms < best_of[order[k]]) best_of[order[k]] = ms;
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best_cfg = c;
-    }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
+  size_t bi = 0;
+  for (size_t i = 1; i < cand.size(); ++i)
+    if (best_of[i] < best_of[bi]) bi = i;
+  const malbec_launch_config best_cfg = cand.empty() ? plan->cfg : cand[bi];
   rc = record_plan(plan, best_cfg);
   if (rc == MALBEC_OK && best) *best = best_cfg;
   return rc;
