@@ -107,12 +107,12 @@ __device__ __forceinline__ BH<T> make_bh(double M, double a) {
 // Gamma^r_rr = -M/(r f), Gamma^r_thth = -f, Gamma^r_phph = -f sin^2,
 // Gamma^th_rth = Gamma^ph_rph = 1/r, Gamma^th_phph = -sin cos,
 // Gamma^ph_thph = cot, with f = r - 2M.
-template <typename T>
+template <typename T, bool kFastRcp = true>
 __device__ __forceinline__ void accel_schw(const BH<T>& bh, T r, T s, T c, T ut, T ur, T uth, T uph,
                                            T acc[4]) {
   const T f = r - bh.twoM;
   const T rf = r * f;
-  const T inv = recip<T>(rf * s);  // 1 / (r f sin)
+  const T inv = kFastRcp ? recip<T>(rf * s) : T(1) / (rf * s);  // 1 / (r f sin)
   const T ir = f * s * inv;       // 1/r
   const T i_f = r * s * inv;      // 1/f
   const T cot = c * rf * inv;     // cos/sin
@@ -129,7 +129,7 @@ __device__ __forceinline__ void accel_schw(const BH<T>& bh, T r, T s, T c, T ut,
 //   g_tt = q - 1, g_tph = -a s^2 q, g_phph = s^2 (r^2 + a^2 + a^2 s^2 q),
 //   g_rr = rho^2/Delta, g_thth = rho^2,
 //   d_r q = (2M - 2 r q)/rho^2, d_th q = 2 a^2 s c q / rho^2.
-template <typename T>
+template <typename T, bool kFastRcp = true>
 __device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T s, T c, T ut, T ur, T uth, T uph,
                                            T acc[4]) {
   const T a = bh.a, a2 = bh.a2;
@@ -138,7 +138,7 @@ __device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T s, T c, T ut,
   const T rho2 = fma(a2, c * c, r2);
   const T Delta = fma(r, r - bh.twoM, a2);
   const T Ds2 = Delta * s2;
-  const T inv = recip<T>(rho2 * Ds2);
+  const T inv = kFastRcp ? recip<T>(rho2 * Ds2) : T(1) / (rho2 * Ds2);
   const T irho2 = Ds2 * inv;
   const T iDs2 = rho2 * inv;  // 1 / (Delta sin^2)
   const T iDelta = iDs2 * s2;
@@ -182,13 +182,14 @@ __device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T s, T c, T ut,
   acc[3] = fma(q - T(1), Wp, as2 * q * Wt) * iDs2;
 }
 
-// The acceleration at (r, theta) given s = sin theta, c = cos theta.
-template <bool kKerr, typename T>
+// The acceleration at (r, theta) given s = sin theta, c = cos theta
+// (kFastRcp: the refined hardware reciprocal in FP64, else the division).
+template <bool kKerr, typename T, bool kFastRcp = true>
 __device__ __forceinline__ void accel_sc(const BH<T>& bh, T r, T s, T c, T ut, T ur, T uth, T uph, T acc[4]) {
   if (kKerr)
-    accel_kerr<T>(bh, r, s, c, ut, ur, uth, uph, acc);
+    accel_kerr<T, kFastRcp>(bh, r, s, c, ut, ur, uth, uph, acc);
   else
-    accel_schw<T>(bh, r, s, c, ut, ur, uth, uph, acc);
+    accel_schw<T, kFastRcp>(bh, r, s, c, ut, ur, uth, uph, acc);
 }
 
 template <bool kKerr, typename T>
@@ -206,8 +207,10 @@ __device__ __forceinline__ void accel(const BH<T>& bh, T r, T th, T ut, T ur, T 
 // operations in the same order whether the stage loop is unrolled or not, so
 // both forms give the same bits).  kRolled keeps one copy of the right-hand
 // side in the code (the FP32_MIXED kernels, whose size otherwise costs
-// instruction-cache misses).  Returns the smallest radius among the three
-// intermediate stage points (used by the capture test).
+// instruction-cache misses; there each stage takes its own sincos and the
+// division, which keeps those kernels' register count down: their FP64 steps
+// are rare and their occupancy matters more).  Returns the smallest radius
+// among the three intermediate stage points (used by the capture test).
 template <bool kKerr, typename T, bool kRolled = false>
 __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
   const T hh = T(0.5) * h;
@@ -215,12 +218,18 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
   T u[4] = {y[4], y[5], y[6], y[7]};
   T sx[4], su[4];
   T rmin = T(0);
-  T s0, c0;
-  Trig<T>::sc(y[2], &s0, &c0);
+  T s0 = T(0), c0 = T(1);
+  if constexpr (!kRolled) Trig<T>::sc(y[2], &s0, &c0);
   T sn = s0, cs = c0;
   auto stage = [&](int s) {
     T acc[4];
-    accel_sc<kKerr, T>(bh, r, sn, cs, u[0], u[1], u[2], u[3], acc);
+    if constexpr (kRolled) {
+      T sr, cr;
+      Trig<T>::sc(th, &sr, &cr);
+      accel_sc<kKerr, T, false>(bh, r, sr, cr, u[0], u[1], u[2], u[3], acc);
+    } else {
+      accel_sc<kKerr, T>(bh, r, sn, cs, u[0], u[1], u[2], u[3], acc);
+    }
     if (s == 0) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -239,7 +248,7 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
       const T c = s < 2 ? hh : h;
       r = fma(c, u[1], y[1]);
       th = fma(c, u[2], y[2]);
-      stage_trig<T>(s0, c0, c * u[2], th, &sn, &cs);
+      if constexpr (!kRolled) stage_trig<T>(s0, c0, c * u[2], th, &sn, &cs);
 #pragma unroll
       for (int j = 0; j < 4; ++j) u[j] = fma(c, acc[j], y[4 + j]);
       rmin = s == 0 ? r : fmin(rmin, r);
@@ -270,14 +279,14 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
 // / (2 rho^2), dp_th/dl likewise; p_t and p_ph are constant (H does not
 // depend on t, ph) and are not integrated.  f = (dt, dr, dth, dph, dp_r,
 // dp_th)/dl.  One reciprocal, as in the geodesic form.
-template <typename T>
+template <typename T, bool kFastRcp = true>
 __device__ __forceinline__ void ham_kerr(const BH<T>& bh, T r, T s, T c, T pt, T pr, T pth, T pph, T f[6]) {
   const T a = bh.a, a2 = bh.a2;
   const T s2 = s * s, sc = s * c;
   const T rho2 = fma(a2, c * c, r * r);
   const T Delta = fma(r, r - bh.twoM, a2);
   const T rD = rho2 * Delta;
-  const T inv = recip<T>(rD * s2);
+  const T inv = kFastRcp ? recip<T>(rD * s2) : T(1) / (rD * s2);
   const T irho2 = Delta * s2 * inv;
   const T iDelta = rho2 * s2 * inv;
   const T is2 = rD * inv;
@@ -336,7 +345,7 @@ struct Adm {
 // - a^2 s^2 d_r Delta, d_th Sigma = -2 a^2 Delta s c).  FP64 shares one
 // division among 1/rho^2, 1/Delta, 1/Sigma and 1/sin^2; FP32 takes 1/Sigma
 // apart (the product of all four would overflow near r = 10^4).
-template <typename T>
+template <typename T, bool kFastRcp = true>
 __device__ __forceinline__ void adm_kerr_sc(const BH<T>& bh, T r, T s, T c, Adm<T>& m) {
   const T a2 = bh.a2;
   const T s2 = s * s, sc = s * c;
@@ -348,7 +357,7 @@ __device__ __forceinline__ void adm_kerr_sc(const BH<T>& bh, T r, T s, T c, Adm<
   T irho2, iDelta, iSigma, is2;
   if constexpr (sizeof(T) == 8) {
     const T SS = Sigma * s2;
-    const T inv = recip<T>(rD * SS);
+    const T inv = kFastRcp ? recip<T>(rD * SS) : T(1) / (rD * SS);
     irho2 = Delta * SS * inv;
     iDelta = rho2 * SS * inv;
     iSigma = rD * s2 * inv;
@@ -415,14 +424,14 @@ __device__ __forceinline__ void adm_rhs(const Adm<T>& m, T pt, T pr, T pth, T pp
 
 // The canonical right-hand side of one form: eq. Ham through g^{mu nu} of
 // eq. kerr (kHamKerrBL) or through the 3+1 quantities of Kerr (kHamAdm).
-template <int kForm, typename T>
+template <int kForm, typename T, bool kFastRcp = true>
 __device__ __forceinline__ void ham_rhs_sc(const BH<T>& bh, T r, T s, T c, T pt, T pr, T pth, T pph, T f[6]) {
   if constexpr (kForm == kHamAdm) {
     Adm<T> m;
-    adm_kerr_sc<T>(bh, r, s, c, m);
+    adm_kerr_sc<T, kFastRcp>(bh, r, s, c, m);
     adm_rhs<T>(m, pt, pr, pth, pph, f);
   } else {
-    ham_kerr<T>(bh, r, s, c, pt, pr, pth, pph, f);
+    ham_kerr<T, kFastRcp>(bh, r, s, c, pt, pr, pth, pph, f);
   }
 }
 
@@ -460,12 +469,18 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
   T r = z[1], th = z[2], pr = z[5], pth = z[6];
   T sx[6];
   T rmin = T(0);
-  T s0, c0;
-  Trig<T>::sc(z[2], &s0, &c0);
+  T s0 = T(0), c0 = T(1);
+  if constexpr (!kRolled) Trig<T>::sc(z[2], &s0, &c0);
   T sn = s0, cs = c0;
   auto stage = [&](int s) {
     T f[6];
-    ham_rhs_sc<kForm, T>(bh, r, sn, cs, z[4], pr, pth, z[7], f);
+    if constexpr (kRolled) {
+      T sr, cr;
+      Trig<T>::sc(th, &sr, &cr);
+      ham_rhs_sc<kForm, T, false>(bh, r, sr, cr, z[4], pr, pth, z[7], f);
+    } else {
+      ham_rhs_sc<kForm, T>(bh, r, sn, cs, z[4], pr, pth, z[7], f);
+    }
     if (s == 0) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) sx[j] = f[j];
@@ -478,7 +493,7 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
       const T c = s < 2 ? hh : h;
       r = fma(c, f[1], z[1]);
       th = fma(c, f[2], z[2]);
-      stage_trig<T>(s0, c0, c * f[2], th, &sn, &cs);
+      if constexpr (!kRolled) stage_trig<T>(s0, c0, c * f[2], th, &sn, &cs);
       pr = fma(c, f[4], z[5]);
       pth = fma(c, f[5], z[6]);
       rmin = s == 0 ? r : fmin(rmin, r);
