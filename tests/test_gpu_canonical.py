@@ -1,6 +1,6 @@
 """The canonical forms (Sec. 2, eq. Ham: RK4 on (x^mu, p_mu) with p = g u) on
 the GPU against the oracle's canonical trace of the same form, with the
-tolerance of the geodesic form (1e-9 per component, reading G11): circular
+tolerance of the geodesic form (1e-9 per component): circular
 orbits, generic bound orbits, the camera, strided trajectories; and p_t,
 p_phi exactly constant.  Every test runs for both ways of writing H: through
 g^{mu nu} of eq. kerr (form 1) and through the lapse, shift and 3-metric of
@@ -66,7 +66,8 @@ def test_bound_orbits_subsample(mb, orc, W, form):
     """The generic bound-orbit subsample (1024 particles, 10^4 steps of 0.02,
     per-particle spin) within 1e-9 of the oracle's canonical trace, apart from
     the few orbits whose discrete map is ill-conditioned next to the polar
-    axis (reading G19); E and L_z conserved to 1e-12."""
+    axis (fixed-step RK4 does not resolve a passage there); E and L_z
+    conserved to 1e-12."""
     wl = W.bound()
     idx = wl.subsample(1024)
     ys, spins, _ = orc.bound_samples(wl.M, wl.a_max, wl.seed, idx)

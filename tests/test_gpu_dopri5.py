@@ -1,7 +1,7 @@
 """The Dormand-Prince 5(4) integrator with step-size control
 (MALBEC_METHOD_DOPRI5, FP64, geodesic form) on the GPU against the oracle's
 method 1: the same tableau, error norm and controller, so the same sequence
-of attempts up to rounding.  States within 1e-9 (reading G11) on the rays
+of attempts up to rounding.  States within 1e-9 per component on the rays
 whose oracle map is well conditioned; attempt counts and fates equal."""
 import dataclasses
 
@@ -43,7 +43,7 @@ def test_bound_orbits_match_oracle(mb, orc, W):
     """512 generic bound orbits (per-particle spin), 3000 attempts at
     tolerance 1e-10.  The adaptive map is discontinuous where an attempt's
     error norm sits at the acceptance threshold or carries a step exponent
-    across an integer (reading G23): there a rounding difference gives
+    across an integer: there a rounding difference gives
     another sequence of steps, seen as another lambda after the same number
     of attempts.  On >= 95% of the orbits the sequence is the oracle's
     (attempts and lambda equal); on those whose oracle map is also
@@ -67,7 +67,8 @@ def test_bound_orbits_match_oracle(mb, orc, W):
     # the kappa test perturbs the initial state only; an adaptive step across
     # a near-polar passage also amplifies the rounding of each step: 1e-16
     # relative noise on every right-hand side moved one such orbit by 1e-8
-    # (reading G23).  99% within 1e-9, all within 1e-6.
+    # (measured with an independent re-implementation).  99% within 1e-9,
+    # all within 1e-6.
     rel = (np.abs(got["y"][:, good] - ref["y"][:, good]) / np.maximum(np.abs(ref["y"][:, good]), 1.0)).max(axis=0)
     assert np.mean(rel <= 1e-9) >= 0.99, np.sort(rel)[-10:]
     assert rel.max() <= 1e-6, rel.max()

@@ -1,6 +1,6 @@
 """GPU path (libmalbec.so through its C ABI) against the FP64 CPU oracle.
 
-Tolerance (north star; reading G11): FP64 states agree per component to
+Tolerance (the stated FP64 bound): FP64 states agree per component to
 |gpu - oracle| <= 1e-9 max(|oracle|, s_c), s_c = M for t and r, 1 for the
 angles and the velocities; phi is compared unwrapped.  Integer outputs (fate,
 step count, accepted candidate) must match exactly.  Inputs are seeded
@@ -60,7 +60,7 @@ def oracle_kappa(orc, M, a, ics, t_or, a_per_ray=None, delta=1e-12):
     of the velocity and an absolute `delta` shift of theta, divided by delta.
     Rounding differences between two correct FP64 implementations (FMA
     contraction, libm) grow by about this factor; rays with kappa > KAPPA_MAX
-    cannot be compared at 1e-9 (reading G19: in practice they are the rays
+    cannot be compared at 1e-9 (in practice they are the rays
     whose theta turning point lies next to the polar axis, where the BL
     Christoffel symbols diverge and a fixed step does not resolve the passage)."""
     ref = orc.trace_many(M, a, ics, t_or, a_per_ray=a_per_ray)
@@ -331,7 +331,7 @@ def test_camera_full_size_sampled_parity(mb, orc, W):
     res = mb.trace_camera(cw.M, cw.a, cam, cw.term, "fp64")
     torch.cuda.synchronize()
     got = {k: np_(v) for k, v in res.items() if k != "buffer"}
-    # NONFINITE appears for a few rays that run into the polar axis (reading G19)
+    # NONFINITE appears for a few rays that run into the polar axis
     assert set(np.unique(got["fate"])) <= {1, 2, 3, 4} and (got["fate"] == 4).mean() < 1e-3
     pix = np.random.default_rng(1803).choice(cw.n, 3000, replace=False)
     ref, near, agree, far = _camera_compare(mb, orc, cw, got, pix)
@@ -524,8 +524,8 @@ def test_mixed_camera_pixel_agreement(mb, orc, W):
     same = f64[pix] == f32[pix]
     print("mixed vs fp64 fate agreement: all", (f64 == f32).mean(), "far", same[far].mean(),
           "far & off-axis", same[far & off_axis].mean(), "off-axis fraction", off_axis.mean())
-    # away from the critical curve and from the polar axis (sin theta_turn >= 0.05,
-    # reading G19) the fates agree; near the axis both paths are ill-conditioned
+    # away from the critical curve and from the polar axis (sin theta_turn >= 0.05)
+    # the fates agree; near the axis both paths are ill-conditioned
     assert same[far & off_axis].mean() >= 0.9999
     assert (f64 == f32).mean() >= 0.99
 

@@ -310,7 +310,7 @@ def test_schwarzschild_isco_and_photon_sphere(orc):
     """Sec. 4: eqs. COrbit/COrbit2 give E = sqrt(8/9), L = sqrt(12) M at the
     ISCO r = 6M (eq. isco); |dE/dr| = M|6M - r|/(2 r^{3/2}(r - 3M)^{3/2}) with
     its only root at 6M (the paper prints the opposite sign: E grows towards 1
-    for r > 6M, reading G16); E diverges as r -> 3M (no circular timelike
+    for r > 6M; the sign here follows the mathematics); E diverges as r -> 3M (no circular timelike
     orbit inside the photon sphere)."""
     E, L = orc.schw_circular(1.0, 6.0)
     assert E == pytest.approx(math.sqrt(8 / 9), rel=1e-15)
@@ -363,7 +363,7 @@ def test_extreme_kerr_limits(orc):
     """Sec. 3 eqs. exKerr+/-: a -> M gives r+ = M, L+ = 2M/sqrt3 and
     r- = 9M, L- = -22M/(3 sqrt3), E- = 5/(3 sqrt3).  eq. exKerr+ prints
     E+ = 1/3 but Table ISCO-Co lists 0.5773502691896 = 1/sqrt3 (Bardeen); the
-    oracle follows the table (reading G4)."""
+    oracle follows the table."""
     a = 1.0
     assert orc.isco_bardeen(1.0, a, 0) == pytest.approx(9.0, abs=1e-12)
     E, L = orc.kerr_circular_bardeen(1.0, a, 9.0, 0)
@@ -381,7 +381,7 @@ def test_paper_energy_momentum_branch_labels(orc):
     """Sec. 3 eqs. energia/momento as printed: the '+' branch (the paper calls
     it co-rotating) reproduces the counter-rotating Bardeen E with the sign of
     L flipped, and the same formula with a -> -a reproduces the co-rotating
-    values (reading G2: labels swapped)."""
+    values: the printed labels are swapped."""
     for a in (0.1, 0.3, 0.5, 0.8, 0.95):
         for r in (orc.isco_bardeen(1, a, 0), 12.0, 20.0):
             Eb, Lb = orc.kerr_circular_bardeen(1.0, a, r, 0)
@@ -395,7 +395,7 @@ def test_paper_energy_momentum_branch_labels(orc):
 
 def test_paper_isco_closed_form_is_garbled(orc):
     """Sec. 3 eq. iscokerr evaluated literally takes the root of a negative
-    number at a = 0.1, 0.5, 0.9 (reading G3: the oracle uses Bardeen instead)."""
+    number at a = 0.1, 0.5, 0.9; the oracle uses Bardeen's closed form instead."""
     for a in (0.1, 0.5, 0.9):
         assert math.isnan(orc.isco_paper_literal(1.0, a, 1))
         assert math.isnan(orc.isco_paper_literal(1.0, a, -1))
@@ -578,7 +578,7 @@ def test_null_deflection_matches_quadrature_and_weak_field(orc):
 
 
 def test_camera_initial_conditions(orc):
-    """Backward camera (reading G9): H = 0 at the observer, and the reversed
+    """Backward camera (not in the paper): H = 0 at the observer, and the reversed
     ray carries E = -1, L_z = alpha sin th_o, Q = beta^2 + cos^2 th_o (alpha^2 - a^2)
     (Carter's constant is even in p), moving inward."""
     a, r_o, th_o, fov, nx, ny = 0.9, 1000.0, math.radians(80), 25.0, 64, 48
