@@ -175,3 +175,22 @@ def test_unsupported_combinations_are_rejected(mb):
     with pytest.raises(mb.MalbecError):
         mb.attach_outputs([b], "fp64")
         mb.trace_bundles([b], "fp64")
+
+
+def test_noalloc_entry_point_gives_the_same_bits(mb, W):
+    """The adaptive integrator through malbec_trace_noalloc: the same kernel
+    as malbec_trace, so the same bits; FP32_MIXED is rejected there too."""
+    import torch
+
+    wl = W.bound()
+    ics, spins, _ = mb.ic_bound(wl.M, wl.a_max, wl.seed, 300)
+    t = dp_term(mb, n_steps_cap=500)
+    a = mb.trace(wl.M, 0.0, ics, t, a_per_ray=spins)
+    L = mb.out_layout(mb.OUT_FINAL, "fp64", 300, t.n_steps_cap, 0)
+    out = torch.empty(L.total, dtype=torch.uint8, device="cuda")
+    b = mb.trace_noalloc(wl.M, 0.0, ics, t, out, a_per_ray=spins)
+    torch.cuda.synchronize()
+    for k in ("y", "lambda", "steps", "fate", "inv1"):
+        assert torch.equal(a[k], b[k]), k
+    with pytest.raises(mb.MalbecError):
+        mb.trace_noalloc(wl.M, 0.0, ics, t, out, precision="fp32_mixed", a_per_ray=spins)
