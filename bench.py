@@ -234,9 +234,9 @@ def run_reference(args) -> None:
     print(json.dumps(line))
 
 
-def load_traffic(kind: str):
-    """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+def load_traffic(kind: str, field: str = "dram_bytes_per_launch"):
+    """A figure of the committed ncu summary (dram bytes per launch, FP64 pipe
+    utilisation), if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -247,7 +247,7 @@ def load_traffic(kind: str):
     ent = d.get(kind)
     if not ent or ent.get("source_hash") != kernel_source_hash():
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent.get(field)
 
 
 def run_profile_case(args) -> None:
@@ -260,6 +260,19 @@ def run_profile_case(args) -> None:
     from paper_1803_08320_gb300 import workloads as W
 
     _b.build()
+    if args.profile_case == "traj_mixed":
+        # 65536 bound orbits x 1000 steps, a sample every step, FP32_MIXED:
+        # 2.1 GB of trajectory on the device
+        wl = W.bound(n=1 << 16, n_steps=1000)
+        ics, spins, _ = mb.ic_bound(wl.M, wl.a_max, wl.seed, wl.n)
+        t = W.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=1000, dl=0.02)
+        for _ in range(max(1, args.steps)):
+            res = mb.trace(wl.M, 0.0, ics, t, mode=mb.OUT_STRIDED, stride=1, precision="fp32_mixed",
+                           a_per_ray=spins)
+        torch.cuda.synchronize()
+        steps = int(res["steps"].to(torch.int64).sum().item())
+        print(json.dumps({"profile_case": args.profile_case, "rays": wl.n, "rk4_steps": steps}))
+        return
     cw = W.camera(nx=512, ny=512)
     cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
     prec = "fp32_mixed" if args.profile_case.endswith("mixed") else "fp64"
@@ -547,6 +560,52 @@ def run_paper_case(mb, torch, stream, stride: int = 10) -> dict:
             "paper_hardware": "GTX 960M (Maxwell), CUDA 7.5; the paper's numbers are context, not a target"}
 
 
+def run_trajectory_case(mb, torch, stream, flush, n: int = 1 << 17, n_steps: int = 2000) -> dict:
+    """Trajectory-write mode (OUT_STRIDED) against the final-state mode on
+    generic bound orbits (the config-3 sampler, dtau = 0.02), FP64 and
+    FP32_MIXED, strides 10 and 1: steps/s and the bytes of trajectory samples
+    written per second (64 B per FP64 sample, 32 B per FP32 one) against the
+    measured HBM copy bandwidth.  One timed launch per row after an identical
+    warm-up launch, L2 flushed before it, CUDA events on the stream."""
+    from paper_1803_08320_gb300 import workloads as W
+
+    wl = W.bound(n=n, n_steps=n_steps)
+    ics, spins, _ = mb.ic_bound(wl.M, wl.a_max, wl.seed, n, stream=stream)
+    t = W.Termination(eps_hor=wl.term.eps_hor, r_esc=wl.term.r_esc, n_steps_cap=n_steps, dl=wl.term.dl)
+    hbm = None
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks):
+        hbm = json.load(open(peaks)).get("hbm_gbs")
+    rows = []
+    for prec in ("fp64", "fp32_mixed"):
+        elem = 8 if prec == "fp64" else 4
+        for mode, stride in ((mb.OUT_FINAL, 0), (mb.OUT_STRIDED, 10), (mb.OUT_STRIDED, 1)):
+            L = mb.out_layout(mode, prec, n, n_steps, stride)
+            out = torch.empty(L.total, dtype=torch.uint8, device="cuda")
+            with torch.cuda.stream(stream):
+                mb.trace(wl.M, 0.0, ics, t, mode=mode, stride=stride, precision=prec, a_per_ray=spins,
+                         stream=stream, out=out)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.zero_()
+                e0.record(stream)
+                r = mb.trace(wl.M, 0.0, ics, t, mode=mode, stride=stride, precision=prec, a_per_ray=spins,
+                             stream=stream, out=out)
+                e1.record(stream)
+                stream.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            steps = int(r["steps"].to(torch.int64).sum().item())
+            nbytes = n * int(L.n_samples) * 8 * elem if mode == mb.OUT_STRIDED else 0
+            row = {"precision": prec, "mode": "strided" if mode == mb.OUT_STRIDED else "final", "stride": stride,
+                   "seconds": sec, "steps_per_s": steps / sec, "trajectory_bytes": nbytes,
+                   "write_gb_per_s": nbytes / sec / 1e9}
+            if hbm:
+                row["frac_of_hbm_copy"] = nbytes / sec / 1e9 / hbm
+            rows.append(row)
+            del out, r
+            torch.cuda.empty_cache()
+    return {"particles": n, "rk4_steps_cap": n_steps, "dtau": wl.term.dl, "hbm_gbs_measured": hbm, "rows": rows}
+
+
 def drift_summary(mb, torch, r) -> dict:
     """Median and p99 of |inv1 - inv0| (E, L_z, Q, g(u,u)) over the rays that
     did not end non-finite."""
@@ -819,6 +878,13 @@ def run_workload(args) -> None:
                          "config": {"workload": "paper_sec6.4_kerr_a0.5_h0.1_1e4steps_N10-50000",
                                     "l2": "one launch per N; the inputs fit in L2 for small N"},
                          "gpu_launches": 2 * len(res["rows"]) + 1, "paper": res})
+        elif args.workload == "trajectory":
+            res = run_trajectory_case(mb, torch, stream, flush)
+            top = [r for r in res["rows"] if r["precision"] == "fp32_mixed" and r["stride"] == 1][0]
+            line.update({"value": top["steps_per_s"], "ms_per_step": 1e3 * top["seconds"], "dtype": "f32+f64",
+                         "config": {"workload": "kerr_generic_bound_131072x2000_trajectory_stride1_10",
+                                    "l2": "flushed before every timed launch"},
+                         "gpu_launches": len(res["rows"]), "trajectory": res})
         elif args.workload == "integrators":
             res = run_integrators_case(mb, torch, stream, flush, K=args.steps, warmup=args.warmup)
             rk = res["rows"]["rk4_h0.05r"]
@@ -900,10 +966,11 @@ def main():
     ap.add_argument("--impl", default="malbec", choices=["malbec", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", choices=["camera_fp64", "camera_mixed", "camera_canonical", "camera_adm",
-                                               "camera_dopri5"],
+                                               "camera_dopri5", "traj_mixed"],
                     default=None,
                     help="small case for ncu: a 512x512 render of the same camera, --steps times")
-    ap.add_argument("--workload", choices=["camera", "bundles", "serving", "bound", "paper", "integrators"],
+    ap.add_argument("--workload", choices=["camera", "bundles", "serving", "bound", "paper", "integrators",
+                                           "trajectory"],
                     default="camera",
                     help="camera: the headline line (with a bundles and a serving sample); bundles: uneven "
                          "bundles, persistent graph launch vs one launch per bundle; serving: Poisson "
@@ -911,7 +978,8 @@ def main():
                          "2^20 generic bound Kerr orbits x 10^5 steps, FP64 and FP32_MIXED, drift and error "
                          "vs the oracle on a 1024-particle subsample; paper: the paper's timing experiment and "
                          "its self-convergence test; integrators: RK4 against Dormand-Prince 5(4) at several "
-                         "tolerances on the camera (time, right-hand sides and invariant drift)")
+                         "tolerances on the camera (time, right-hand sides and invariant drift); trajectory: "
+                         "strided trajectory output against the final-state mode, write bandwidth vs HBM")
     ap.add_argument("--particles", type=int, default=1 << 20, help="particles for --workload bound")
     ap.add_argument("--bound-steps", type=int, default=100_000, help="step cap for --workload bound")
     ap.add_argument("--bundle-count", type=int, default=None,
@@ -1147,6 +1215,11 @@ def main():
                    "samples": cl["samples"]},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "GFLOP/s (FP64)",
                      "frac": achieved / peak64, "traffic": load_traffic("camera_fp64"),
+                     "fp64_pipe_utilization": {
+                         "pct_of_peak": load_traffic("camera_fp64", "fp64_pipe_pct_of_peak"),
+                         "source": "ncu sm__inst_executed_pipe_fp64 of this kernel (512x512 case, committed "
+                                   "summary of the current source); the FP64-peak criterion read as pipe "
+                                   "utilisation, beside the algorithmic-flop fraction above"},
                      "peak_note": "measured FP64 FMA loop on this GPU (malbec_measure_fma_peak), of measured",
                      "flops_per_rk4_step": FLOPS_PER_STEP["kerr"],
                      "plus_per_rk4_step": PLUS_PER_STEP,
