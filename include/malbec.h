@@ -473,6 +473,14 @@ int malbec_ic_bound(double M, double a_max, int spin_fixed, uint64_t seed, uint6
                     uint64_t n, double* ics, double* spins, int32_t* accepted,
                     malbec_stream stream);
 
+/* The paper's initial-condition rows (Sec. 5: columns t, r, theta, phi, p_t,
+ * p_r, p_theta, p_phi, where the p_t column holds E > 0) to states: with
+ * p = (-E, p_r, p_theta, p_phi), x is copied and u = g^{-1} p (eq. kerr),
+ * per-ray spins from m.a_per_ray if given.  rows and ics: device
+ * double[8][n] (SoA, the transpose of the paper's row layout), distinct
+ * buffers; MALBEC_EINVAL for a bad metric, n = 0, NULL or aliased buffers. */
+int malbec_ic_from_paper(malbec_metric m, const double* rows, uint64_t n, double* ics, malbec_stream stream);
+
 /* E, L_z, Q (Carter), norm g(u,u) of n states (device double[8][n]) into
  * inv (device double[4][n]), in FP64. */
 int malbec_invariants(malbec_metric m, const double* states, uint64_t n, double* inv,

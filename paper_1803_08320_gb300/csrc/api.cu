@@ -457,6 +457,14 @@ int malbec_invariants(malbec_metric m, const double* states, uint64_t n, double*
   return e == cudaSuccess ? MALBEC_OK : set_cuda_error(e);
 }
 
+int malbec_ic_from_paper(malbec_metric m, const double* rows, uint64_t n, double* ics, malbec_stream stream) {
+  int rc = check_metric(m);
+  if (rc) return rc;
+  if (!rows || !ics || n == 0 || rows == ics) return MALBEC_EINVAL;
+  cudaError_t e = launch_ic_from_paper(m.M, m.a, m.a_per_ray, rows, n, ics, (cudaStream_t)stream);
+  return e == cudaSuccess ? MALBEC_OK : set_cuda_error(e);
+}
+
 const char* malbec_build_info(void) {
 #define MALBEC_S2(x) #x
 #define MALBEC_S(x) MALBEC_S2(x)

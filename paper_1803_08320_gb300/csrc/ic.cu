@@ -8,6 +8,7 @@
 //  - generic bound Kerr orbits drawn with the SplitMix64 counter-based
 //    generator and solved by Newton's method with the analytic Jacobian of
 //    the radial potential R(r);
+//  - the paper's own initial-condition rows (p_t column = E) to states;
 //  - E, L_z, Q, g(u,u) of arrays of states.
 #include <math.h>
 
@@ -79,6 +80,25 @@ __global__ void invariants_kernel(double M, double a, const double* __restrict__
   for (int c = 0; c < 4; ++c) inv[(size_t)c * n + i] = v[c];
 }
 
+// The paper's initial-condition rows (Sec. 5: t, r, theta, phi and the
+// momenta p_t, p_r, p_theta, p_phi, with the p_t column holding E > 0) to
+// states (x, u): p = (-E, p_r, p_theta, p_phi), u = g^{-1} p (eq. kerr).
+__global__ void ic_from_paper_kernel(double M, double a, const double* __restrict__ a_per_ray,
+                                     const double* __restrict__ rows, uint64_t n, double* __restrict__ ics) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double z[8], u[4];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) z[c] = rows[(size_t)c * n + i];
+  z[4] = -z[4];
+  raise_momentum(M, a_per_ray ? a_per_ray[i] : a, z, u);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    ics[(size_t)c * n + i] = z[c];
+    ics[(size_t)(4 + c) * n + i] = u[c];
+  }
+}
+
 unsigned grid_for(uint64_t n) { return (unsigned)((n + kTPB - 1) / kTPB); }
 
 }  // namespace
@@ -98,6 +118,12 @@ cudaError_t launch_ic_camera(double M, double a, const CameraConst& cam, const u
 cudaError_t launch_ic_bound(double M, double a_max, int spin_fixed, uint64_t seed, uint64_t index0, uint64_t n,
                             double* ics, double* spins, int32_t* accepted, cudaStream_t stream) {
   ic_bound_kernel<<<grid_for(n), kTPB, 0, stream>>>(M, a_max, spin_fixed, seed, index0, n, ics, spins, accepted);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ic_from_paper(double M, double a, const double* a_per_ray, const double* rows, uint64_t n,
+                                 double* ics, cudaStream_t stream) {
+  ic_from_paper_kernel<<<grid_for(n), kTPB, 0, stream>>>(M, a, a_per_ray, rows, n, ics);
   return cudaGetLastError();
 }
 

@@ -121,6 +121,8 @@ cudaError_t launch_ic_camera(double M, double a, const CameraConst& cam, const u
 cudaError_t launch_ic_bound(double M, double a_max, int spin_fixed, uint64_t seed, uint64_t index0,
                             uint64_t n, double* ics, double* spins, int32_t* accepted,
                             cudaStream_t stream);
+cudaError_t launch_ic_from_paper(double M, double a, const double* a_per_ray, const double* rows, uint64_t n,
+                                 double* ics, cudaStream_t stream);
 cudaError_t launch_invariants(double M, double a, const double* a_per_ray, const double* states,
                               uint64_t n, double* inv, cudaStream_t stream);
 

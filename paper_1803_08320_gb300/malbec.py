@@ -128,6 +128,7 @@ def _declare(L):
     sig("malbec_trace_camera", ctypes.c_int, Metric, ctypes.POINTER(Camera), Term, ctypes.c_int, _VP, _VP)
     sig("malbec_ic_camera", ctypes.c_int, Metric, ctypes.POINTER(Camera), _VP, _U64, _VP, _VP)
     sig("malbec_ic_circular", ctypes.c_int, Metric, _VP, _U64, ctypes.c_int, _VP, _VP)
+    sig("malbec_ic_from_paper", ctypes.c_int, Metric, _VP, _U64, _VP, _VP)
     sig("malbec_ic_bound", ctypes.c_int, _D, _D, ctypes.c_int, _U64, _U64, _U64, _VP, _VP, _VP, _VP)
     sig("malbec_invariants", ctypes.c_int, Metric, _VP, _U64, _VP, _VP)
     sig("malbec_measure_fma_peak", ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D))
@@ -485,6 +486,38 @@ def ic_camera(M: float, a: float, cam: Camera, pixels, stream=None):
     ics = torch.empty((8, n), dtype=torch.float64, device="cuda")
     _check(lib().malbec_ic_camera(Metric(float(M), float(a), None), ctypes.byref(cam), _ptr(px), n, _ptr(ics),
                                   _stream(stream)), "malbec_ic_camera")
+    return ics
+
+
+def read_paper_rows(path: str) -> np.ndarray:
+    """Initial-condition rows in the paper's text layout (Sec. 5: one ray per
+    line, t r theta phi p_t p_r p_theta p_phi, the p_t column holding E > 0;
+    blank lines and '#' comments skipped): a (8, n) float64 array."""
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            vals = [float(v) for v in line.split()]
+            if len(vals) != 8:
+                raise ValueError(f"{path}: expected 8 columns, got {len(vals)}: {line!r}")
+            rows.append(vals)
+    if not rows:
+        raise ValueError(f"{path}: no rows")
+    return np.ascontiguousarray(np.array(rows, dtype=np.float64).T)
+
+
+def ic_from_paper(M: float, a: float, rows, a_per_ray=None, stream=None):
+    """States (x, u) on the device from the paper's rows ((8, n), p_t column =
+    E): malbec_ic_from_paper."""
+    torch = _torch()
+    r = _dev_f64(rows)
+    n = r.shape[1]
+    ics = torch.empty((8, n), dtype=torch.float64, device="cuda")
+    apr = None if a_per_ray is None else _dev_f64(a_per_ray)
+    _check(lib().malbec_ic_from_paper(Metric(float(M), float(a), _ptr(apr)), _ptr(r), n, _ptr(ics),
+                                      _stream(stream)), "malbec_ic_from_paper")
     return ics
 
 

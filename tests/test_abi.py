@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from conftest import ROOT
@@ -183,3 +184,28 @@ def test_launch_config_setting(mb):
     bad = mb.LaunchConfig(512, 0, 0, 0, 0)
     assert mb.lib().malbec_set_launch_config(ctypes.byref(bad)) == mb.EINVAL
     assert mb.set_launch_config(reset=True).as_dict()["threads_per_block"] == 0
+
+
+def test_paper_rows_reader(mb, tmp_path):
+    """The paper's initial-condition text layout (Sec. 5: t r theta phi p_t
+    p_r p_theta p_phi per line): the three rows of the golden file parse to
+    an (8, 3) array; a malformed line is an error."""
+    import os
+
+    rows = mb.read_paper_rows(os.path.join(os.path.dirname(__file__), "golden", "ic_rows.txt"))
+    assert rows.shape == (8, 3) and rows.dtype == np.float64
+    assert rows[1].tolist() == [6.0, 3.5, 4.0] and rows[4, 0] == 0.9428 and rows[7, 2] == 4.0
+    bad = tmp_path / "bad.txt"
+    bad.write_text("0 6 1.5708 0 0.9428 0 0\n")
+    with pytest.raises(ValueError):
+        mb.read_paper_rows(str(bad))
+
+
+def test_ic_from_paper_validation(mb):
+    lib = mb.lib()
+    fake, other = ctypes.c_void_p(256), ctypes.c_void_p(512)
+    good = mb.Metric(1.0, 0.0, None)
+    assert lib.malbec_ic_from_paper(good, fake, 0, other, None) == mb.EINVAL
+    assert lib.malbec_ic_from_paper(good, None, 3, other, None) == mb.EINVAL
+    assert lib.malbec_ic_from_paper(good, fake, 3, fake, None) == mb.EINVAL   # rows and ics alias
+    assert lib.malbec_ic_from_paper(mb.Metric(1.0, 1.0, None), fake, 3, other, None) == mb.EINVAL

@@ -566,3 +566,20 @@ def test_self_convergence_every_config(mb, W, config):
     assert ok.sum() >= 0.5 * d1.size
     assert 14.0 < np.median(q) < 18.0, np.median(q)
     assert np.mean((q > 13.0) & (q < 19.0)) > 0.6, np.sort(q)
+
+
+def test_ic_from_paper_rows(mb, orc):
+    """The paper's ic.txt rows (Sec. 5; p_t column = E) converted on the GPU
+    equal the oracle's conversion within 1e-13, and the first row (the
+    Schwarzschild circular orbit at r = 6M, the ISCO) stays at r = 6 over
+    10^3 steps of 0.01 with FP64 RK4."""
+    import os
+
+    rows = mb.read_paper_rows(os.path.join(os.path.dirname(__file__), "golden", "ic_rows.txt"))
+    got = np_(mb.ic_from_paper(1.0, 0.0, rows))
+    ref = np.stack([orc.paper_to_state(1.0, 0.0, rows[:, i]) for i in range(rows.shape[1])], axis=1)
+    assert_states_close(got, ref, rtol=1e-13, what="paper rows")
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=1000, dl=0.01)
+    res = gpu_trace(mb, 1.0, 0.0, got[:, :1], t)
+    # the rows carry 4 decimals, so the orbit is circular to ~1e-4 only
+    assert res["fate"][0] == mb.FATE_CAPPED and abs(res["y"][1, 0] - 6.0) < 1e-2
