@@ -130,8 +130,9 @@ typedef struct {
  *                         stride count attempts; capture and non-finite are
  *                         tested on every attempt (at its result and its
  *                         stage points, as for RK4), escape on accepted
- *                         steps.  Requires atol > 0, rtol >= 0, form
- *                         MALBEC_FORM_GEODESIC and MALBEC_FP64; malbec_trace,
+ *                         steps.  Any form (in the canonical forms p_t and
+ *                         p_ph stay exactly constant, as with RK4).  Requires
+ *                         atol > 0, rtol >= 0 and MALBEC_FP64; malbec_trace,
  *                         malbec_trace_noalloc and malbec_trace_camera only.
  * rtol, atol: the tolerances of MALBEC_METHOD_DOPRI5 (ignored by RK4). */
 #define MALBEC_FORM_GEODESIC 0

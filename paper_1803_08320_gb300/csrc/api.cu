@@ -42,7 +42,6 @@ int check_term(const malbec_term& t, const malbec_metric& m) {
   if (!isfinite(t.r_esc) || !(t.r_esc > (1.0 + t.eps_hor) * rp)) return MALBEC_EINVAL;
   if (t.method != MALBEC_METHOD_RK4 && t.method != MALBEC_METHOD_DOPRI5) return MALBEC_EINVAL;
   if (t.method == MALBEC_METHOD_DOPRI5) {
-    if (t.form != MALBEC_FORM_GEODESIC) return MALBEC_EINVAL;
     if (!finite_pos(t.atol) || !isfinite(t.rtol) || t.rtol < 0.0) return MALBEC_EINVAL;
     if (scaled && (!isfinite(t.dl) || t.dl < 0.0)) return MALBEC_EINVAL;
   }

@@ -584,11 +584,13 @@ namespace malbec {
 // 19-26), one of the further Runge-Kutta methods the paper's conclusions
 // name: seven stages, the seventh taken at the fifth-order result, so that
 // it is the first stage of the next step (k1 = k7 of the last accepted
-// attempt).  One attempt of size h from y (geodesic form) with k1 = f(y):
-// y5 (fifth order), e = y5 - y4 (the embedded fourth-order result), k7 =
-// f(y5); returns the smallest radius among the stage points 2..7.  One sincos
-// per attempt: the stage angles are reached by stage_trig.
-template <bool kKerr>
+// attempt).  One attempt of size h from y with k1 = f(y): y5 (fifth order),
+// e = y5 - y4 (the embedded fourth-order result), k7 = f(y5); returns the
+// smallest radius among the stage points 2..7.  One sincos per attempt: the
+// stage angles are reached by stage_trig.  kForm: the geodesic form on
+// y = (x, u), or a canonical form on z = (x, p), whose p_t and p_ph have zero
+// derivative (their k components are 0, so they never change).
+template <bool kKerr, int kForm = 0>
 __device__ __forceinline__ double dopri5_attempt(const BH<double>& bh, double h, const double y[8],
                                                  const double k1[8], double y5[8], double e[8], double k7[8]) {
   double s0, c0;
@@ -602,9 +604,22 @@ __device__ __forceinline__ double dopri5_attempt(const BH<double>& bh, double h,
     const double th = fma(h, d[2], y[2]);
     double sn, cs;
     stage_trig<double>(s0, c0, h * d[2], th, &sn, &cs);
+    if constexpr (kForm == 0) {
+      // k = (u, -Gamma u u) at the stage point
 #pragma unroll
-    for (int j = 0; j < 4; ++j) k[j] = fma(h, d[4 + j], y[4 + j]);
-    accel_sc<kKerr, double>(bh, r, sn, cs, k[0], k[1], k[2], k[3], k + 4);
+      for (int j = 0; j < 4; ++j) k[j] = fma(h, d[4 + j], y[4 + j]);
+      accel_sc<kKerr, double>(bh, r, sn, cs, k[0], k[1], k[2], k[3], k + 4);
+    } else {
+      // k = (dH/dp, -dH/dx) at the stage point; p_t, p_ph stay y[4], y[7]
+      double f[6];
+      ham_rhs_sc<kForm, double>(bh, r, sn, cs, y[4], fma(h, d[5], y[5]), fma(h, d[6], y[6]), y[7], f);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[j] = f[j];
+      k[4] = 0.0;
+      k[5] = f[4];
+      k[6] = f[5];
+      k[7] = 0.0;
+    }
     rmin = first ? r : fmin(rmin, r);
   };
 #pragma unroll

@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
   constexpr bool kHam = kForm != MALBEC_FORM_GEODESIC;
   static_assert(!kHam || kKerr, "the canonical forms use the Kerr Hamiltonian (a = 0 included)");
   constexpr bool kDopri = kMethod == MALBEC_METHOD_DOPRI5;
-  static_assert(!kDopri || (!kMixed && !kHam), "Dormand-Prince: FP64, geodesic form");
+  static_assert(!kDopri || !kMixed, "Dormand-Prince: FP64");
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const float k6h = (float)(1.0 / 6.0), k6l = (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0));
@@ -810,9 +810,20 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
           // first trial step; k1 = f(y) for the first attempt
           h_next = dl > 0.0 ? dl : dl_scale * y[1];
           after_reject = false;
+          if constexpr (kHam) {
+            double f[6];
+            ham_rhs<kForm, double>(bh64, y[1], y[2], y[4], y[5], y[6], y[7], f);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) k1d[c] = y[4 + c];
-          accel<kKerr, double>(bh64, y[1], y[2], y[4], y[5], y[6], y[7], k1d + 4);
+            for (int c = 0; c < 4; ++c) k1d[c] = f[c];
+            k1d[4] = 0.0;
+            k1d[5] = f[4];
+            k1d[6] = f[5];
+            k1d[7] = 0.0;
+          } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) k1d[c] = y[4 + c];
+            accel<kKerr, double>(bh64, y[1], y[2], y[4], y[5], y[6], y[7], k1d + 4);
+          }
         }
       }
       continue;
@@ -882,7 +893,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         if (dl_scale > 0.0) h_next = fmin(h_next, dl_scale * y[1]);
         const double h = h_next;
         double y5[8], e[8], k7[8];
-        const double rmin = dopri5_attempt<kKerr>(bh64, h, y, k1d, y5, e, k7);
+        const double rmin = dopri5_attempt<kKerr, kForm>(bh64, h, y, k1d, y5, e, k7);
         captured = (y5[1] <= r_cap) | (rmin <= r_cap);
         finite = finite8(y5);
         escaped = false;
@@ -1057,16 +1068,23 @@ const void* kernel_ptr() {
 // block ray exchange (two instantiations, so that the one without carries
 // none of its code).
 const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, int form, int method) {
-  // Dormand-Prince 5(4): FP64, geodesic form (the Kerr right-hand side,
-  // a = 0 included), state arrays and cameras
+  // Dormand-Prince 5(4): FP64, every form (the Kerr right-hand sides, a = 0
+  // included), state arrays and cameras
   if (method == MALBEC_METHOD_DOPRI5) {
-    if (mixed || form != MALBEC_FORM_GEODESIC) return nullptr;
-    if (src == kSrcStates && sink == kSinkFinal)
-      return kernel_ptr<true, false, kSrcStates, kSinkFinal, false, MALBEC_FORM_GEODESIC, MALBEC_METHOD_DOPRI5>();
-    if (src == kSrcStates && sink == kSinkStrided)
-      return kernel_ptr<true, false, kSrcStates, kSinkStrided, false, MALBEC_FORM_GEODESIC, MALBEC_METHOD_DOPRI5>();
-    if (src == kSrcCamera && sink == kSinkCamera)
-      return kernel_ptr<true, false, kSrcCamera, kSinkCamera, false, MALBEC_FORM_GEODESIC, MALBEC_METHOD_DOPRI5>();
+    if (mixed) return nullptr;
+#define MALBEC_PICK_DP(F)                                                                  \
+  if (form == F) {                                                                         \
+    if (src == kSrcStates && sink == kSinkFinal)                                           \
+      return kernel_ptr<true, false, kSrcStates, kSinkFinal, false, F, MALBEC_METHOD_DOPRI5>();   \
+    if (src == kSrcStates && sink == kSinkStrided)                                         \
+      return kernel_ptr<true, false, kSrcStates, kSinkStrided, false, F, MALBEC_METHOD_DOPRI5>(); \
+    if (src == kSrcCamera && sink == kSinkCamera)                                          \
+      return kernel_ptr<true, false, kSrcCamera, kSinkCamera, false, F, MALBEC_METHOD_DOPRI5>();  \
+  }
+    MALBEC_PICK_DP(MALBEC_FORM_GEODESIC)
+    MALBEC_PICK_DP(MALBEC_FORM_HAMILTONIAN)
+    MALBEC_PICK_DP(MALBEC_FORM_ADM)
+#undef MALBEC_PICK_DP
     return nullptr;
   }
   // canonical forms (Sec. 2, eq. Ham, with g of eq. kerr or of eq. ADM):

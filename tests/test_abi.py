@@ -106,7 +106,6 @@ def test_trace_validation_rejects_before_any_cuda_call(mb):
         (mb.Metric(1.0, 0.5, None), _term(method=2)),  # no such integrator
         (mb.Metric(1.0, 0.5, None), _term(method=1, rtol=1e-9, atol=0.0)),   # Dormand-Prince: atol > 0
         (mb.Metric(1.0, 0.5, None), _term(method=1, rtol=-1.0, atol=1e-9)),
-        (mb.Metric(1.0, 0.5, None), _term(method=1, rtol=1e-9, atol=1e-9, form=1)),  # geodesic form only
         (mb.Metric(1.0, 0.5, None), _term(method=1, rtol=1e-9, atol=1e-9, dl=-1.0, dl_r_scale=0.5)),
     ]
     for m, t in cases:

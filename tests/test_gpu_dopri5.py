@@ -1,7 +1,8 @@
 """The Dormand-Prince 5(4) integrator with step-size control
-(MALBEC_METHOD_DOPRI5, FP64, geodesic form) on the GPU against the oracle's
-method 1: the same tableau, error norm and controller, so the same sequence
-of attempts up to rounding.  States within 1e-9 per component on the rays
+(MALBEC_METHOD_DOPRI5, FP64) on the GPU against the oracle's method 1 in
+each form (the geodesic equation, and the canonical equations through
+g^{mu nu} of eq. kerr or the 3+1 quantities of eq. ADM): the same tableau,
+error norm and controller, so the same sequence of attempts up to rounding.  States within 1e-9 per component on the rays
 whose oracle map is well conditioned; attempt counts and fates equal."""
 import dataclasses
 
@@ -33,13 +34,18 @@ def W():
     return workloads
 
 
+@pytest.fixture(scope="module", params=[0, 1, 2], ids=["geodesic", "kerr_bl", "adm"])
+def form(request):
+    return request.param
+
+
 def dp_term(mb, tol=1e-10, **kw):
     base = dict(eps_hor=0.01, r_esc=1100.0, n_steps_cap=3000, dl=0.02, method=mb.METHOD_DOPRI5, rtol=tol, atol=tol)
     base.update(kw)
     return mb.Termination(**base)
 
 
-def test_bound_orbits_match_oracle(mb, orc, W):
+def test_bound_orbits_match_oracle(mb, orc, W, form):
     """512 generic bound orbits (per-particle spin), 3000 attempts at
     tolerance 1e-10.  The adaptive map is discontinuous where an attempt's
     error norm sits at the acceptance threshold or carries a step exponent
@@ -54,7 +60,7 @@ def test_bound_orbits_match_oracle(mb, orc, W):
     wl = W.bound()
     idx = wl.subsample(512)
     ys, spins, _ = orc.bound_samples(wl.M, wl.a_max, wl.seed, idx)
-    t = dp_term(mb)
+    t = dp_term(mb, form=form)
     got = gpu_trace(mb, wl.M, 0.0, ys, t, a_per_ray=spins)
     ref, kappa = oracle_kappa(orc, wl.M, 0.0, ys, oracle_term(orc, t), a_per_ray=spins)
     # with a fixed first step and no r-proportional cap every step is
@@ -95,7 +101,7 @@ def test_circular_orbits_and_step_growth(mb, W):
     assert d.max() < 1e-9
 
 
-def test_camera_small_image(mb, orc, W):
+def test_camera_small_image(mb, orc, W, form):
     """48 x 48 Kerr a = 0.9 camera with the adaptive integrator (tolerance
     1e-9, steps at most 0.5 r): fates and attempt counts of well-conditioned
     pixels away from the critical curve equal the oracle's; escaped (theta,
@@ -103,7 +109,7 @@ def test_camera_small_image(mb, orc, W):
     import torch
 
     cw = W.camera(nx=48, ny=48)
-    cw = dataclasses.replace(cw, term=dp_term(mb, tol=1e-9, dl=0.0, dl_r_scale=0.5, n_steps_cap=20_000))
+    cw = dataclasses.replace(cw, term=dp_term(mb, tol=1e-9, dl=0.0, dl_r_scale=0.5, n_steps_cap=20_000, form=form))
     cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
     res = mb.trace_camera(cw.M, cw.a, cam, cw.term, "fp64")
     torch.cuda.synchronize()
@@ -119,7 +125,7 @@ def test_camera_small_image(mb, orc, W):
     assert_states_close(got["phi"][esc], ref["y"][3][esc], what="phi")
 
 
-def test_strided_samples(mb, orc):
+def test_strided_samples(mb, orc, form):
     """Samples every `stride` attempts (a rejected attempt repeats the last
     accepted state) of eccentric orbits (circular ones with u^r = 0.01) equal
     the oracle's within 1e-9 where the sequence of steps is the oracle's;
@@ -127,7 +133,7 @@ def test_strided_samples(mb, orc):
     rng = np.random.default_rng(5)
     ys = np.stack([orc.circular_state(1.0, 0.5, r, 1) for r in rng.uniform(7.0, 12.0, 24)], axis=1)
     ys[5] = 0.01
-    t = dp_term(mb, tol=1e-9, r_esc=40.0, n_steps_cap=600, dl=0.5)
+    t = dp_term(mb, tol=1e-9, r_esc=40.0, n_steps_cap=600, dl=0.5, form=form)
     got = gpu_trace(mb, 1.0, 0.5, ys, t, mode=mb.OUT_STRIDED, stride=25)
     ref = orc.trace_many(1.0, 0.5, ys, oracle_term(orc, t), stride=25, want_traj=True)
     same = (got["steps"].astype(np.uint32) == ref["steps"]) & (got["lambda"] == ref["lambda"])
@@ -169,8 +175,6 @@ def test_unsupported_combinations_are_rejected(mb):
     ics[4] = 1.2
     with pytest.raises(mb.MalbecError):
         gpu_trace(mb, 1.0, 0.5, ics, dp_term(mb), precision="fp32_mixed")
-    with pytest.raises(mb.MalbecError):
-        gpu_trace(mb, 1.0, 0.5, ics, dp_term(mb, form=mb.FORM_HAMILTONIAN))
     b = mb.make_bundle(mb.BUNDLE_BOUND, 4, 1.0, 0.5, dp_term(mb), seed=1)
     with pytest.raises(mb.MalbecError):
         mb.attach_outputs([b], "fp64")
@@ -194,3 +198,24 @@ def test_noalloc_entry_point_gives_the_same_bits(mb, W):
         assert torch.equal(a[k], b[k]), k
     with pytest.raises(mb.MalbecError):
         mb.trace_noalloc(wl.M, 0.0, ics, t, out, precision="fp32_mixed", a_per_ray=spins)
+
+
+def test_every_form_conserves_the_invariants(mb, W):
+    """With the adaptive integrator at tolerance 1e-11 every form keeps the
+    flow's invariants: Q and the norm within 1500 x tol after 1500 attempts
+    on >= 95% of the bound-orbit sample, and in the canonical forms E and L_z
+    to the rounding of the conversions at the two ends.  (The forms take
+    different step sequences, so their end states sit at different lambda.)"""
+    import torch
+
+    wl = W.bound()
+    ics, spins, _ = mb.ic_bound(wl.M, wl.a_max, wl.seed, 1024)
+    for f in (0, 1, 2):
+        r = mb.trace(wl.M, 0.0, ics, dp_term(mb, tol=1e-11, n_steps_cap=1500, form=f), a_per_ray=spins)
+        torch.cuda.synchronize()
+        ok = r["fate"] == mb.FATE_CAPPED
+        assert ok.float().mean().item() > 0.95
+        d = (r["inv1"][:, ok] - r["inv0"][:, ok]).abs() / r["inv0"][:, ok].abs().clamp(min=1.0)
+        assert (d[2:].amax(dim=0) <= 1500 * 1e-11).float().mean().item() >= 0.95, f
+        if f != 0:
+            assert d[:2].max().item() < 1e-12, f
