@@ -115,7 +115,7 @@ def test_camera_small_image(mb, orc, W, form):
     torch.cuda.synchronize()
     got = {k: np_(v) for k, v in res.items() if k != "buffer"}
     pix = np.arange(cw.n)
-    ref, near, agree, far = _camera_compare(mb, orc, cw, got, pix)
+    ref, near, agree, far = _camera_compare(mb, orc, cw, got, pix, form=form)
     good = ref["kappa"] <= KAPPA_MAX
     assert agree[far & good].all()
     assert np.array_equal(got["steps"][far & good].astype(np.uint32), ref["steps"][far & good])

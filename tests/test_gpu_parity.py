@@ -224,8 +224,9 @@ def _pixel_ab(cw, pix):
     return al, be
 
 
-def _camera_compare(mb, orc, cw, got, pix, exclusion=0.098, form=0):
-    """Per-pixel comparison with the oracle on the pixels `pix`."""
+def _camera_compare(mb, orc, cw, got, pix, exclusion=0.098, form=None):
+    """Per-pixel comparison with the oracle on the pixels `pix` (the form of
+    cw.term unless `form` is given)."""
     ics = orc.camera_ics(cw.M, cw.a, cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny, pix)
     ref, kappa = oracle_kappa(orc, cw.M, cw.a, ics, oracle_term(orc, cw.term, form))
     near = np.array([orc.critical_curve_distance(cw.M, cw.a, cw.incl, *_pixel_ab(cw, p)) < exclusion for p in pix])
