@@ -202,7 +202,7 @@ int malbec_get_mixed_zone(malbec_mixed_zone* zone);
  *                      sub-partition saturates the FP64 unit --, 8 for
  *                      FP32_MIXED);
  *   refill_min         a warp takes new rays once this many lanes are idle
- *                      (automatic: 1);
+ *                      (automatic: 2 for FP64, 1 for FP32_MIXED);
  *   zone_batch         FP32_MIXED: an FP64-zone warp step waits for this many
  *                      lanes (automatic: 8 with the exchange below, 32
  *                      without) ...
