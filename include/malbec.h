@@ -39,7 +39,9 @@ typedef struct CUstream_st* malbec_stream; /* == cudaStream_t */
 
 /* ---------------------------------------------------------------- errors */
 #define MALBEC_OK 0
-#define MALBEC_EINVAL (-1)    /* bad argument (a >= M, M <= 0, r0 <= r_+, NaN, n == 0 with out, ...) */
+#define MALBEC_EINVAL (-1)    /* bad argument (a >= M, M <= 0, a camera observer inside the capture
+                                 radius, a NaN parameter, n == 0, ...); device initial states are
+                                 not read on the host: a bad ray ends with its own fate */
 #define MALBEC_ENOMEM (-2)    /* over the HBM budget, or a device allocation failed */
 #define MALBEC_EBUSY (-3)     /* admission queue full: retry later */
 #define MALBEC_ETIMEDOUT (-4) /* a bounded device-side wait gave up */
@@ -256,10 +258,11 @@ size_t malbec_out_bytes(malbec_out_mode mode, malbec_precision prec, uint64_t n,
 
 /* ---------------------------------------------------------------- tracing */
 /* Integrate n rays from the initial states `ics` (device, double[8][n] SoA)
- * until each terminates (see fates).  The right-hand side is the geodesic
- * equation du^mu/dl = -Gamma^mu_ab u^a u^b (the second-order form of the
- * canonical equations, Sec. 2 eq. Ham) specialised for Schwarzschild or
- * Kerr; each RK4 step is the classical 4-stage scheme.  Rays are pulled from
+ * until each terminates (see fates).  The right-hand side is the one of
+ * term.form: by default the geodesic equation du^mu/dl = -Gamma^mu_ab u^a u^b
+ * (the second-order form of the canonical equations, Sec. 2 eq. Ham)
+ * specialised for Schwarzschild or Kerr; the integrator is term.method's
+ * (by default the classical 4-stage RK4).  Rays are pulled from
  * a device work queue by persistent warps, and a lane whose ray ends takes
  * the next one, so uneven step counts do not idle lanes.
  * out: device, layout.total bytes (malbec_out_layout), caller-owned.
