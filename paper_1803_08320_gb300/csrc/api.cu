@@ -118,11 +118,17 @@ int choose_shape_cfg(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, c
   const uint64_t blocks_needed = (warps_needed + (tpb / 32) - 1) / (tpb / 32);
   shape->threads_per_block = tpb;
   shape->blocks = (int)(blocks_needed < max_blocks ? blocks_needed : max_blocks);
-  // refill granularity: FP64 warps wait for 2 dead lanes (the new rays' set-up
-  // then runs on two lanes at once; measured on the 1024^2 camera: 196.7 ms
-  // against 198.0 ms for 1, 197.0 for 4, 200.9 for 8); FP32_MIXED refills
-  // every dead lane
-  *refill_min = cfg.refill_min ? (int)cfg.refill_min : (mixed ? 1 : 2);
+  // refill granularity.  FP64: a warp waits for 2 dead lanes (the new rays'
+  // set-up then runs on two lanes at once; 1024^2 camera: 196.7 ms against
+  // 198.0 for 1, 197.0 for 4, 200.9 for 8).  FP32_MIXED cameras: a warp takes
+  // 32 new rays at once, so it holds 32 neighbouring pixels that reach their
+  // FP64 zones together (zone steps with full warps instead of ~5 lanes) and
+  // share one pass of the FP64 set-up (11.4 ms against 20.2 for 1, 15.0 for
+  // 8).  Other FP32_MIXED sources refill every dead lane.
+  if (cfg.refill_min)
+    *refill_min = (int)cfg.refill_min;
+  else
+    *refill_min = !mixed ? 2 : (src == kSrcCamera ? 32 : 1);
   return MALBEC_OK;
 }
 

@@ -346,8 +346,9 @@ int malbec_plan_autotune(malbec_plan* plan, malbec_stream stream, malbec_launch_
   if (!plan) return MALBEC_EINVAL;
   // Candidates: block size x blocks per SM (4 or 8 resident warps per SM for
   // FP64; 8 or 12 for the FP32 path), refill granularity (dead lanes a warp
-  // waits for before it claims new rays) and, for FP32_MIXED, the FP64-zone
-  // batch and the block ray exchange on or off.
+  // waits for before it claims new rays: 1, 4, or 32 for whole-warp refills)
+  // and, for FP32_MIXED, the FP64-zone batch and the block ray exchange on or
+  // off.
   std::vector<malbec_launch_config> cand;
   if (!plan->mixed) {
     for (uint32_t rm : {1u, 4u}) cand.push_back({128u, 1u, rm, 0u, 0u, 0u});
@@ -361,6 +362,9 @@ int malbec_plan_autotune(malbec_plan* plan, malbec_stream stream, malbec_launch_
       for (uint32_t z = 0; z < 2; ++z)
         for (uint32_t x = 1; x <= 2; ++x) cand.push_back({sh[0], sh[1], 1u, z ? 16u : 8u, z ? 256u : 64u, x});
     cand.push_back({128u, 2u, 4u, 8u, 64u, 1u});
+    // whole-warp refills: 32 neighbouring rays of a job start together
+    cand.push_back({128u, 2u, 32u, 8u, 64u, 2u});
+    cand.push_back({128u, 2u, 32u, 16u, 256u, 1u});
   }
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
