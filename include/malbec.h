@@ -204,10 +204,11 @@ int malbec_get_mixed_zone(malbec_mixed_zone* zone);
  *                      sub-partition saturates the FP64 unit --, 8 for
  *                      FP32_MIXED);
  *   refill_min         a warp takes new rays once this many lanes are idle
- *                      (automatic: 2 for FP64; for FP32_MIXED 32 on
- *                      whole-image cameras -- neighbouring pixels stay
- *                      together and take their FP64 zone steps together --
- *                      and 1 otherwise);
+ *                      (automatic: 2 for FP64; for FP32_MIXED whole-image
+ *                      cameras 32, 8 or 1 for >= 16, >= 4 or fewer rays per
+ *                      resident lane -- neighbouring pixels taken together
+ *                      take their FP64 zone steps together --, and 1 for
+ *                      other FP32_MIXED sources);
  *   zone_batch         FP32_MIXED: an FP64-zone warp step waits for this many
  *                      lanes (automatic: 8 with the exchange below, 32
  *                      without) ...

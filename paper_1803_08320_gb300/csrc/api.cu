@@ -120,15 +120,25 @@ int choose_shape_cfg(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, c
   shape->blocks = (int)(blocks_needed < max_blocks ? blocks_needed : max_blocks);
   // refill granularity.  FP64: a warp waits for 2 dead lanes (the new rays'
   // set-up then runs on two lanes at once; 1024^2 camera: 196.7 ms against
-  // 198.0 for 1, 197.0 for 4, 200.9 for 8).  FP32_MIXED cameras: a warp takes
-  // 32 new rays at once, so it holds 32 neighbouring pixels that reach their
-  // FP64 zones together (zone steps with full warps instead of ~5 lanes) and
-  // share one pass of the FP64 set-up (11.4 ms against 20.2 for 1, 15.0 for
-  // 8).  Other FP32_MIXED sources refill every dead lane.
-  if (cfg.refill_min)
+  // 198.0 for 1, 197.0 for 4, 200.9 for 8).  FP32_MIXED cameras: a warp that
+  // takes many new rays at once holds neighbouring pixels, which reach their
+  // FP64 zones together (zone steps with fuller warps) and share one pass of
+  // the FP64 set-up; but it also waits for the slowest of them, which pays
+  // only when each lane slot sees many rays.  By rays per resident lane g:
+  // 32 for g >= 16, 8 for g >= 4, else 1 (measured, ms: 256^2, g = 1.7:
+  // 3.29 / 3.53 / 5.88 for 1 / 8 / 32; 512^2, g = 6.7: 6.54 / 5.64 / 7.72;
+  // 1024^2, g = 27: 20.2 / 15.1 / 11.4; 2048^2, g = 108: 70.0 / 50.5 / 42.4).
+  // Other FP32_MIXED sources refill every dead lane.
+  if (cfg.refill_min) {
     *refill_min = (int)cfg.refill_min;
-  else
-    *refill_min = !mixed ? 2 : (src == kSrcCamera ? 32 : 1);
+  } else if (!mixed) {
+    *refill_min = 2;
+  } else if (src == kSrcCamera) {
+    const double g = (double)n / ((double)shape->blocks * (double)shape->threads_per_block);
+    *refill_min = g >= 16.0 ? 32 : (g >= 4.0 ? 8 : 1);
+  } else {
+    *refill_min = 1;
+  }
   return MALBEC_OK;
 }
 
