@@ -6,7 +6,6 @@ p_phi exactly constant.  Every test runs for both ways of writing H: through
 g^{mu nu} of eq. kerr (form 1) and through the lapse, shift and 3-metric of
 eq. ADM (form 2)."""
 import dataclasses
-import math
 
 import numpy as np
 import pytest
