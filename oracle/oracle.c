@@ -7,9 +7,13 @@
  *   - the geodesic equation; the paper integrates the canonical form (Sec. 2,
  *     eq. Ham); the oracle integrates the equivalent second-order form
  *     d2x/dl2 = -Gamma u u with Gamma built generically from analytic metric
- *     derivatives in plain 4x4x4 loops, and keeps eq. Ham as a cross-form;
- *   - classical RK4 (Sec. 5: "traditional fourth order Runge-Kutta"; tableau
- *     c = (0, 1/2, 1/2, 1), b = (1, 2, 2, 1)/6, the paper does not print it);
+ *     derivatives in plain 4x4x4 loops (form 0), and the canonical equations
+ *     themselves with g of eq. kerr (form 1) or with g assembled from the
+ *     lapse, shift and 3-metric of eq. ADM (form 2);
+ *   - classical RK4 (Sec. 5 names the classical fourth-order method without
+ *     printing its tableau: c = (0, 1/2, 1/2, 1), b = (1, 2, 2, 1)/6), and,
+ *     as method 1, the Dormand-Prince 5(4) pair with step-size control (the
+ *     paper's conclusions name further Runge-Kutta methods) [not in paper];
  *   - the per-ray horizon stop (Sec. 5), generalised to r <= (1+eps) r_+, plus
  *     escape r >= r_esc, a non-finite check and a step cap;
  *   - circular equatorial orbits: Schwarzschild eqs. COrbit, COrbit2,
