@@ -97,3 +97,33 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
+
+
+def test_self_convergence_ratio_and_drift_summary():
+    """bench.q_ratio is the paper's Q = |y_h - y_h/2| / |y_h/2 - y_h/4| per ray
+    (largest component difference), leaving out non-finite and vanishing
+    differences; bench.drift_summary reports |inv1 - inv0| without the
+    non-finite rays."""
+    sys.path.insert(0, ROOT)
+    import torch
+
+    import bench
+
+    base = np.zeros((8, 4))
+    f1, f2, f3 = base.copy(), base.copy(), base.copy()
+    f1[1] = [16e-6, 8e-6, 1.0, np.nan]
+    f2[1] = [1e-6, 1e-6, 1.0, 0.0]
+    f3[1] = [0.0, 0.0, 1.0, 0.0]
+    q = bench.q_ratio([f1, f2, f3])
+    assert q["rays"] == 2 and q["of"] == 4
+    assert abs(q["median"] - 11.0) < 1e-9 and q["frac_13_19"] == 0.5  # Q = 15 and 7
+
+    class FakeMb:
+        FATE_NONFINITE = 4
+
+    r = {"fate": torch.tensor([3, 3, 4, 2]),
+         "inv0": torch.ones((4, 4), dtype=torch.float64),
+         "inv1": torch.ones((4, 4), dtype=torch.float64)}
+    r["inv1"][2] += torch.tensor([1e-9, 3e-9, 1e3, 2e-9], dtype=torch.float64)
+    d = bench.drift_summary(FakeMb, torch, r)
+    assert d["nonfinite"] == 1 and abs(d["Q"]["median"] - 2e-9) < 1e-15 and d["E"]["median"] == 0.0
