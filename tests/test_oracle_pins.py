@@ -1032,3 +1032,20 @@ def test_dopri5_step_control_and_capture(orc):
     a = orc.trace_one(1.0, 0.0, yi, orc.make_term(n_steps_cap=10000, dl=0.01, method=1, rtol=1e-9, atol=1e-9))
     b = orc.trace_one(1.0, 0.0, yi, orc.make_term(n_steps_cap=10000, dl=0.01))
     assert a["fate"] == b["fate"] == 1
+
+
+def test_dopri5_canonical_forms_keep_pt_pphi_and_follow_the_flow(orc):
+    """Dormand-Prince in the canonical forms (eq. Ham through eq. kerr, and
+    through eq. ADM): p_t and p_phi have zero derivative, so E and L_z come
+    back to the conversions' rounding; Q and the norm drift within attempts x
+    tol, as in the geodesic form."""
+    ys, spins, _ = orc.bound_samples(1.0, 0.9, 13, np.arange(6), spin_fixed=True)
+    for form in (1, 2):
+        t = orc.make_term(n_steps_cap=800, dl=0.02, form=form, method=1, rtol=1e-10, atol=1e-10)
+        for i in range(ys.shape[1]):
+            res = orc.trace_one(1.0, 0.9, ys[:, i], t)
+            assert res["fate"] == 3
+            i0, i1 = orc.invariants(1.0, 0.9, ys[:, i]), orc.invariants(1.0, 0.9, res["y"])
+            d = np.abs(i1 - i0) / np.maximum(np.abs(i0), 1.0)
+            assert d[:2].max() < 1e-12, (form, d)
+            assert d[2:].max() < 800 * 1e-10, (form, d)
