@@ -208,3 +208,12 @@ def test_ic_from_paper_validation(mb):
     assert lib.malbec_ic_from_paper(good, None, 3, other, None) == mb.EINVAL
     assert lib.malbec_ic_from_paper(good, fake, 3, fake, None) == mb.EINVAL   # rows and ics alias
     assert lib.malbec_ic_from_paper(mb.Metric(1.0, 1.0, None), fake, 3, other, None) == mb.EINVAL
+
+
+def test_diagnostics_validate_before_any_cuda_call(mb):
+    lib = mb.lib()
+    v = ctypes.c_double()
+    assert lib.malbec_measure_step_loop(7, ctypes.byref(v)) == mb.EINVAL
+    assert lib.malbec_measure_step_loop(0, None) == mb.EINVAL
+    assert lib.malbec_check_fp64_helpers(None) == mb.EINVAL
+    assert lib.malbec_measure_fma_peak(5, ctypes.byref(v)) == mb.EINVAL
