@@ -1087,3 +1087,57 @@ def test_kerr_equatorial_escape_angle_matches_quadrature(orc):
         assert res["fate"] == orc.FATE_ESCAPED
         assert res["y"][2] == math.pi / 2
         assert abs(res["y"][3] - (leg(r_obs) + leg(res["y"][1]))) < 1e-9, b
+
+
+def test_kerr_escape_theta_matches_mino_time_integrals(orc):
+    """The final theta of escaped off-equatorial null rays, pinned directly
+    [not in paper]: in Mino time (dl = rho^2 dl_M) Kerr null geodesics obey
+    dr/dl_M = +-sqrt(R(r)) and du/dl_M = -+sqrt(a^2 (u+^2 - u^2)(u^2 + u-^2))
+    with u = cos(theta), so the Mino time spent on the radial path (in to the
+    periapsis, out to the final radius) fixes where u is on its oscillation
+    between -u+ and u+; with u = u+ sin(psi) that oscillation's time is the
+    smooth integral of 1 / (a sqrt(u+^2 sin^2 psi + u-^2)).  The oracle's
+    trace (h = 5e-4 r) ends at the theta so predicted within 1e-9, for both
+    initial directions of theta and two inclinations (a = 0.9, E = 1)."""
+    from scipy.integrate import quad
+    from scipy.optimize import brentq
+
+    M, a, r_obs, E = 1.0, 0.9, 1000.0, 1.0
+    for L, Q, th0, sgn in ((3.0, 20.0, math.radians(80), 1), (-5.0, 30.0, math.radians(80), -1),
+                           (8.0, 50.0, math.radians(60), 1), (2.0, 60.0, math.radians(80), -1)):
+        Delta = lambda r: r * r - 2 * M * r + a * a  # noqa: E731
+        P = lambda r: E * (r * r + a * a) - a * L  # noqa: E731
+        R = lambda r: P(r) ** 2 - Delta(r) * ((L - a * E) ** 2 + Q)  # noqa: E731
+        grid = np.linspace(1.5, 60.0, 40000)
+        vals = np.array([R(x) for x in grid])
+        k = np.where((vals[:-1] < 0) & (vals[1:] >= 0))[0][-1]
+        rp = brentq(R, grid[k], grid[k + 1], xtol=1e-15)
+
+        def leg(r1):
+            f = lambda v: 2 * v / math.sqrt(max(R(rp + v * v), 1e-300))  # noqa: E731
+            return quad(f, 0.0, math.sqrt(r1 - rp), epsabs=1e-14, epsrel=1e-14, limit=500)[0]
+
+        A, B = a * a, Q + L * L - a * a
+        up2 = (-B + math.sqrt(B * B + 4 * A * Q)) / (2 * A)
+        um2 = (B + math.sqrt(B * B + 4 * A * Q)) / (2 * A)
+        up = math.sqrt(up2)
+
+        def Phi(psi):
+            return quad(lambda s: 1.0 / (a * math.sqrt(up2 * math.sin(s) ** 2 + um2)), 0.0, psi,
+                        epsabs=1e-14, epsrel=1e-14)[0]
+
+        half = Phi(math.pi / 2)
+        Theta = Q + a * a * E * E * math.cos(th0) ** 2 - L * L / math.tan(th0) ** 2
+        gi = orc.inverse_metric(M, a, r_obs, th0)
+        p = np.array([-E, -math.sqrt(R(r_obs)) / Delta(r_obs), sgn * math.sqrt(Theta), L])
+        y0 = np.concatenate([[0.0, r_obs, th0, 0.0], gi @ p])
+        res = orc.trace_one(M, a, y0, orc.make_term(0.01, 1100.0, 10**6, 0.0, 5e-4))
+        assert res["fate"] == orc.FATE_ESCAPED
+        G = leg(r_obs) + leg(res["y"][1])
+        # phase on the oscillation: [0, 2 half) u falling from u+, [2 half, 4 half) rising from -u+
+        psi0 = math.asin(math.cos(th0) / up)
+        s0 = half - Phi(psi0) if sgn > 0 else 3 * half + Phi(psi0)
+        s = (s0 + G) % (4 * half)
+        target = half - s if s < 2 * half else s - 3 * half
+        psi = brentq(lambda x: Phi(x) - target, -math.pi / 2, math.pi / 2, xtol=1e-15)
+        assert abs(res["y"][2] - math.acos(up * math.sin(psi))) < 1e-9, (L, Q)
