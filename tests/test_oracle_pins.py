@@ -1089,16 +1089,19 @@ def test_kerr_equatorial_escape_angle_matches_quadrature(orc):
         assert abs(res["y"][3] - (leg(r_obs) + leg(res["y"][1]))) < 1e-9, b
 
 
-def test_kerr_escape_theta_matches_mino_time_integrals(orc):
-    """The final theta of escaped off-equatorial null rays, pinned directly
-    [not in paper]: in Mino time (dl = rho^2 dl_M) Kerr null geodesics obey
-    dr/dl_M = +-sqrt(R(r)) and du/dl_M = -+sqrt(a^2 (u+^2 - u^2)(u^2 + u-^2))
-    with u = cos(theta), so the Mino time spent on the radial path (in to the
-    periapsis, out to the final radius) fixes where u is on its oscillation
-    between -u+ and u+; with u = u+ sin(psi) that oscillation's time is the
-    smooth integral of 1 / (a sqrt(u+^2 sin^2 psi + u-^2)).  The oracle's
-    trace (h = 5e-4 r) ends at the theta so predicted within 1e-9, for both
-    initial directions of theta and two inclinations (a = 0.9, E = 1)."""
+def test_kerr_escape_angles_match_mino_time_integrals(orc):
+    """The final (theta, phi) of escaped off-equatorial null rays, pinned
+    directly [not in paper]: in Mino time (dl = rho^2 dl_M) Kerr null
+    geodesics obey dr/dl_M = +-sqrt(R(r)), du/dl_M = -+sqrt(a^2 (u+^2 - u^2)
+    (u^2 + u-^2)) with u = cos(theta), and dphi/dl_M = aP/Delta + L/(1 - u^2)
+    - aE.  The Mino time spent on the radial path (in to the periapsis, out to
+    the final radius) fixes where u is on its oscillation between -u+ and u+
+    (with u = u+ sin(psi) the oscillation's time is the smooth integral of
+    1 / (a sqrt(u+^2 sin^2 psi + u-^2))), and phi is the r-part integrated
+    along the radial path plus the u-part integrated along that oscillation.
+    The oracle's trace (h = 5e-4 r) ends at the predicted angles within 1e-9,
+    for both initial directions of theta and two inclinations (a = 0.9,
+    E = 1)."""
     from scipy.integrate import quad
     from scipy.optimize import brentq
 
@@ -1113,31 +1116,54 @@ def test_kerr_escape_theta_matches_mino_time_integrals(orc):
         k = np.where((vals[:-1] < 0) & (vals[1:] >= 0))[0][-1]
         rp = brentq(R, grid[k], grid[k + 1], xtol=1e-15)
 
-        def leg(r1):
-            f = lambda v: 2 * v / math.sqrt(max(R(rp + v * v), 1e-300))  # noqa: E731
+        def leg(r1, g=lambda r: 1.0):
+            f = lambda v: 2 * v * g(rp + v * v) / math.sqrt(max(R(rp + v * v), 1e-300))  # noqa: E731
             return quad(f, 0.0, math.sqrt(r1 - rp), epsabs=1e-14, epsrel=1e-14, limit=500)[0]
 
         A, B = a * a, Q + L * L - a * a
         up2 = (-B + math.sqrt(B * B + 4 * A * Q)) / (2 * A)
         um2 = (B + math.sqrt(B * B + 4 * A * Q)) / (2 * A)
         up = math.sqrt(up2)
+        w = lambda x: 1.0 / (a * math.sqrt(up2 * math.sin(x) ** 2 + um2))  # noqa: E731
 
         def Phi(psi):
-            return quad(lambda s: 1.0 / (a * math.sqrt(up2 * math.sin(s) ** 2 + um2)), 0.0, psi,
-                        epsabs=1e-14, epsrel=1e-14)[0]
+            return quad(w, 0.0, psi, epsabs=1e-14, epsrel=1e-14)[0]
+
+        def Jphi(p1, p2):
+            f = lambda x: (L / (1.0 - up2 * math.sin(x) ** 2) - a * E) * w(x)  # noqa: E731
+            return quad(f, p1, p2, epsabs=1e-13, epsrel=1e-13, limit=200)[0]
 
         half = Phi(math.pi / 2)
+
+        def psi_of(target):
+            if target >= half:
+                return math.pi / 2
+            if target <= -half:
+                return -math.pi / 2
+            return brentq(lambda x: Phi(x) - target, -math.pi / 2, math.pi / 2, xtol=1e-15)
+
         Theta = Q + a * a * E * E * math.cos(th0) ** 2 - L * L / math.tan(th0) ** 2
         gi = orc.inverse_metric(M, a, r_obs, th0)
         p = np.array([-E, -math.sqrt(R(r_obs)) / Delta(r_obs), sgn * math.sqrt(Theta), L])
         y0 = np.concatenate([[0.0, r_obs, th0, 0.0], gi @ p])
         res = orc.trace_one(M, a, y0, orc.make_term(0.01, 1100.0, 10**6, 0.0, 5e-4))
         assert res["fate"] == orc.FATE_ESCAPED
-        G = leg(r_obs) + leg(res["y"][1])
+        rf = res["y"][1]
+        G = leg(r_obs) + leg(rf)
+        phi = leg(r_obs, lambda r: a * P(r) / Delta(r)) + leg(rf, lambda r: a * P(r) / Delta(r))
         # phase on the oscillation: [0, 2 half) u falling from u+, [2 half, 4 half) rising from -u+
         psi0 = math.asin(math.cos(th0) / up)
-        s0 = half - Phi(psi0) if sgn > 0 else 3 * half + Phi(psi0)
-        s = (s0 + G) % (4 * half)
-        target = half - s if s < 2 * half else s - 3 * half
-        psi = brentq(lambda x: Phi(x) - target, -math.pi / 2, math.pi / 2, xtol=1e-15)
-        assert abs(res["y"][2] - math.acos(up * math.sin(psi))) < 1e-9, (L, Q)
+        s = half - Phi(psi0) if sgn > 0 else 3 * half + Phi(psi0)
+        rem = G
+        while rem > 0:
+            sm = s % (4 * half)
+            falling = sm < 2 * half
+            psi_now = psi_of(half - sm if falling else sm - 3 * half)
+            step = min(rem, (2 * half - sm) if falling else (4 * half - sm))
+            sm2 = sm + step
+            psi_next = psi_of(half - sm2 if falling else sm2 - 3 * half)
+            phi += Jphi(min(psi_now, psi_next), max(psi_now, psi_next))
+            rem -= step
+            s += step
+        assert abs(res["y"][2] - math.acos(up * math.sin(psi_next))) < 1e-9, (L, Q)
+        assert abs(res["y"][3] - phi) < 1e-9, (L, Q)
