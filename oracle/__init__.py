@@ -120,6 +120,7 @@ def _declare(L):
     sig("orc_circular_state", None, _D, _D, _D, ctypes.c_int, _PD)
     sig("orc_camera_ic", None, _D, _D, _D, _D, _D, _U32, _U32, _U64, _PD)
     sig("orc_critical_curve_distance", _D, _D, _D, _D, _D, _D)
+    sig("orc_critical_curve_polyline", None, _D, _D, _D, ctypes.c_int, _PD, _PD)
     sig("orc_splitmix64", _U64, _U64, _U64)
     sig("orc_uniform", _D, _U64, _U64)
     sig("orc_bound_orbit_solve", ctypes.c_int, _D, _D, _D, _D, _D, _PD, _PD, _PD, _PD)
@@ -400,6 +401,45 @@ def camera_ics(M, a, r_o, th_o, fov_half, nx, ny, pixels):
 
 def critical_curve_distance(M, a, th_o, alpha, beta):
     return lib().orc_critical_curve_distance(M, a, th_o, alpha, beta)
+
+
+def critical_curve_polyline(M, a, th_o, n=200_000):
+    """The Kerr critical curve as a closed polyline of 2n (alpha, beta) points
+    (orc_critical_curve_polyline)."""
+    al = np.empty(2 * n)
+    be = np.empty(2 * n)
+    lib().orc_critical_curve_polyline(M, a, th_o, int(n), _p(al), _p(be))
+    return al, be
+
+
+def critical_curve_distance_many(M, a, th_o, alpha, beta, n=20_000, upper=0.25):
+    """Distance of many (alpha, beta) points to the critical curve at once:
+    the nearest vertex of the dense polyline (k-d tree), then the exact
+    distance to the two polyline segments at that vertex.  Agrees with
+    critical_curve_distance to well below the polyline spacing.  Points
+    farther than `upper` from every vertex get +inf (a nearest-neighbour
+    search from far away is slow, and callers only compare with a small
+    exclusion distance)."""
+    from scipy.spatial import cKDTree
+
+    cal, cbe = critical_curve_polyline(M, a, th_o, n)
+    pts = np.stack([cal, cbe], axis=1)
+    q = np.stack([np.asarray(alpha, dtype=np.float64).ravel(), np.asarray(beta, dtype=np.float64).ravel()], axis=1)
+    d, k = cKDTree(pts).query(q, distance_upper_bound=upper)
+    far = ~np.isfinite(d)
+    k = np.where(far, 0, k)
+    m = len(pts)
+    best = d
+    for nb in ((k - 1) % m, (k + 1) % m):
+        p0, p1 = pts[k], pts[nb]
+        seg = p1 - p0
+        L2 = np.einsum("ij,ij->i", seg, seg)
+        t = np.where(L2 > 0, np.einsum("ij,ij->i", q - p0, seg) / np.where(L2 > 0, L2, 1.0), 0.0)
+        t = np.clip(t, 0.0, 1.0)
+        proj = p0 + t[:, None] * seg
+        best = np.minimum(best, np.hypot(q[:, 0] - proj[:, 0], q[:, 1] - proj[:, 1]))
+    best[far] = np.inf
+    return best.reshape(np.shape(alpha))
 
 
 def splitmix64(seed, counter):

@@ -905,41 +905,106 @@ void orc_camera_ic(double M, double a, double r_o, double th_o, double fov_half,
   momenta_to_state(M, a, x, p, y);
 }
 
-/* Distance in the (alpha, beta) plane from a point to the Kerr critical curve
- * (boundary of the shadow) [not in paper; Bardeen 1973]:
+/* The Kerr critical curve (boundary of the shadow) [not in paper; Bardeen
+ * 1973], the image of the spherical photon orbits of radius r:
  *   xi(r) = (r^2 (3M - r) - a^2 (r + M)) / (a (r - M)),
  *   eta(r) = r^3 (4 a^2 M - r (r - 3M)^2) / (a^2 (r - M)^2),
- *   alpha = -xi / sin th_o, beta = +- sqrt(eta + a^2 cos^2 th_o - xi^2 cot^2 th_o),
- * for r between the prograde and retrograde photon orbits; for a = 0 a circle
- * of radius 3 sqrt(3) M.  Plain dense sampling of r plus a local refinement. */
-static double cc_dist_at(double M, double a, double th_o, double r, double al, double be) {
+ *   alpha = -xi / sin th_o, beta = +- sqrt(b2), b2 = eta + a^2 cos^2 th_o - xi^2 cot^2 th_o,
+ * over the r where b2 >= 0 (the orbits whose polar range reaches th_o), a
+ * sub-interval [r_a, r_b] of the photon-orbit band [r_ph,pro, r_ph,retro]; for
+ * a = 0 a circle of radius 3 sqrt(3) M.  Near r_a and r_b, beta grows like
+ * sqrt(r - r_a), so the curve is sampled at r = r_a + (r_b - r_a)(1 - cos(pi u))/2
+ * with u uniform in [0, 1], which spaces the points evenly along beta there. */
+static double cc_b2(double M, double a, double so, double co, double r, double* xi_out) {
   double xi = (r * r * (3.0 * M - r) - a * a * (r + M)) / (a * (r - M));
   double eta = r * r * r * (4.0 * a * a * M - r * (r - 3.0 * M) * (r - 3.0 * M)) / (a * a * (r - M) * (r - M));
-  double so = sin(th_o), co = cos(th_o);
-  double b2 = eta + a * a * co * co - xi * xi * co * co / (so * so);
-  if (b2 < 0.0) return INFINITY;
-  double ac = -xi / so, bc = sqrt(b2);
-  double d1 = hypot(al - ac, be - bc), d2 = hypot(al - ac, be + bc);
-  return d1 < d2 ? d1 : d2;
+  if (xi_out) *xi_out = xi;
+  return eta + a * a * co * co - xi * xi * co * co / (so * so);
 }
+
+/* [r_a, r_b]: bisection for b2 = 0 on each side of the polar orbit
+ * (xi = 0, where b2 = eta + a^2 cos^2 th_o > 0). */
+static void cc_range(double M, double a, double so, double co, double* ra, double* rb) {
+  double r1 = orc_photon_orbit(M, a, 1), r2 = orc_photon_orbit(M, a, 0);
+  double lo = r1, hi = r2, r0;
+  for (int k = 0; k < 200; ++k) { /* xi decreases from xi(r1) > 0 to xi(r2) < 0 */
+    double mid = 0.5 * (lo + hi), xi;
+    cc_b2(M, a, so, co, mid, &xi);
+    if (xi > 0.0) lo = mid; else hi = mid;
+  }
+  r0 = 0.5 * (lo + hi);
+  *ra = r1;
+  if (cc_b2(M, a, so, co, r1, NULL) < 0.0) {
+    lo = r1; hi = r0;
+    for (int k = 0; k < 200; ++k) {
+      double mid = 0.5 * (lo + hi);
+      if (cc_b2(M, a, so, co, mid, NULL) < 0.0) lo = mid; else hi = mid;
+    }
+    *ra = hi;
+  }
+  *rb = r2;
+  if (cc_b2(M, a, so, co, r2, NULL) < 0.0) {
+    lo = r0; hi = r2;
+    for (int k = 0; k < 200; ++k) {
+      double mid = 0.5 * (lo + hi);
+      if (cc_b2(M, a, so, co, mid, NULL) < 0.0) hi = mid; else lo = mid;
+    }
+    *rb = lo;
+  }
+}
+
+/* The point of the upper branch (beta >= 0) at curve parameter u in [0, 1]. */
+static void cc_point(double M, double a, double so, double co, double ra, double rb, double u,
+                     double* al, double* be) {
+  double r = ra + (rb - ra) * 0.5 * (1.0 - cos(M_PI * u)), xi;
+  double b2 = cc_b2(M, a, so, co, r, &xi);
+  *al = -xi / so;
+  *be = b2 > 0.0 ? sqrt(b2) : 0.0;
+}
+
 double orc_critical_curve_distance(double M, double a, double th_o, double alpha, double beta) {
   if (fabs(a) < 1e-12) return fabs(hypot(alpha, beta) - 3.0 * sqrt(3.0) * M);
-  double r1 = orc_photon_orbit(M, fabs(a), 1), r2 = orc_photon_orbit(M, fabs(a), 0);
+  double so = sin(th_o), co = cos(th_o), ra, rb;
+  cc_range(M, fabs(a), so, co, &ra, &rb);
+  double bab = fabs(beta); /* the curve is symmetric under beta -> -beta */
   int N = 20000;
-  double best = INFINITY, rbest = r1;
+  double best = INFINITY, ubest = 0.0;
   for (int k = 0; k <= N; ++k) {
-    double r = r1 + (r2 - r1) * k / N;
-    double d = cc_dist_at(M, a, th_o, r, alpha, beta);
-    if (d < best) { best = d; rbest = r; }
+    double u = (double)k / N, al, be;
+    cc_point(M, fabs(a), so, co, ra, rb, u, &al, &be);
+    double d = hypot(alpha - al, bab - be);
+    if (d < best) { best = d; ubest = u; }
   }
-  double lo = rbest - (r2 - r1) / N, hi = rbest + (r2 - r1) / N;
-  if (lo < r1) lo = r1;
-  if (hi > r2) hi = r2;
+  double lo = ubest - 1.0 / N, hi = ubest + 1.0 / N;
+  if (lo < 0.0) lo = 0.0;
+  if (hi > 1.0) hi = 1.0;
   for (int k = 0; k <= 2000; ++k) {
-    double d = cc_dist_at(M, a, th_o, lo + (hi - lo) * k / 2000.0, alpha, beta);
+    double al, be;
+    cc_point(M, fabs(a), so, co, ra, rb, lo + (hi - lo) * k / 2000.0, &al, &be);
+    double d = hypot(alpha - al, bab - be);
     if (d < best) best = d;
   }
   return best;
+}
+
+/* The curve as a closed polyline of 2n points: the upper branch for
+ * u = k/(n-1), k = 0..n-1, then the lower branch back (beta -> -beta). */
+void orc_critical_curve_polyline(double M, double a, double th_o, int n, double* alpha, double* beta) {
+  double so = sin(th_o), co = cos(th_o), ra = 0.0, rb = 0.0;
+  if (fabs(a) >= 1e-12) cc_range(M, fabs(a), so, co, &ra, &rb);
+  for (int k = 0; k < n; ++k) {
+    double u = n > 1 ? (double)k / (n - 1) : 0.0, al, be;
+    if (fabs(a) < 1e-12) {
+      al = -3.0 * sqrt(3.0) * M * cos(M_PI * u);
+      be = 3.0 * sqrt(3.0) * M * sin(M_PI * u);
+    } else {
+      cc_point(M, fabs(a), so, co, ra, rb, u, &al, &be);
+    }
+    alpha[k] = al;
+    beta[k] = be;
+    alpha[2 * n - 1 - k] = al;
+    beta[2 * n - 1 - k] = -be;
+  }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -118,6 +118,7 @@ void orc_circular_state(double M, double a, double r, int prograde, double y[8])
 void orc_camera_ic(double M, double a, double r_o, double th_o, double fov_half,
                    uint32_t nx, uint32_t ny, uint64_t pix, double y[8]);
 double orc_critical_curve_distance(double M, double a, double th_o, double alpha, double beta);
+void orc_critical_curve_polyline(double M, double a, double th_o, int n, double* alpha, double* beta);
 
 /* -------- generic bound orbits (counter-based sampler) -------- */
 uint64_t orc_splitmix64(uint64_t seed, uint64_t counter);

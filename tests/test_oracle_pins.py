@@ -628,6 +628,109 @@ def test_camera_fates_match_radial_potential(orc):
     assert checked > 0.8 * nx * ny
 
 
+def _min_radial_potential(a, Lz, Q, r_lo, r_hi=60.0):
+    """Smallest value of the photon radial potential (E = 1)
+    R(r) = ((r^2 + a^2) - a L_z)^2 - Delta (Q + (L_z - a)^2) on [r_lo, r_hi]:
+    a dense grid, then a bounded scalar minimisation around the grid minimum.
+    Beyond 60 M, R ~ r^4 stays positive for the impact parameters used here."""
+    from scipy.optimize import minimize_scalar
+
+    def R(r):
+        Delta = r * r - 2 * r + a * a
+        return ((r * r + a * a) - a * Lz) ** 2 - Delta * (Q + (Lz - a) ** 2)
+
+    r = np.linspace(r_lo, r_hi, 6000)
+    k = int(np.argmin(R(r)))
+    lo, hi = r[max(k - 1, 0)], r[min(k + 1, len(r) - 1)]
+    res = minimize_scalar(R, bounds=(lo, hi), method="bounded", options={"xatol": 1e-13})
+    return min(float(res.fun), float(R(r[k])))
+
+
+def _shadow_edge(a, th_o, centre, phi, t_max=15.0):
+    """Point of the capture boundary on the ray centre + t (cos phi, sin phi):
+    the zero of t -> min_r R(r; L_z, Q), positive while the photon is captured
+    (R stays positive down to the horizon) and negative once it has a turning
+    point; L_z = -alpha sin th_o, Q = beta^2 + cos^2 th_o (alpha^2 - a^2)."""
+    from scipy.optimize import brentq
+
+    r_lo = 1.0 + math.sqrt(1.0 - a * a)
+    so, co = math.sin(th_o), math.cos(th_o)
+
+    def g(t):
+        al = centre[0] + t * math.cos(phi)
+        be = centre[1] + t * math.sin(phi)
+        return _min_radial_potential(a, -al * so, be * be + co * co * (al * al - a * a), r_lo)
+
+    assert g(0.0) > 0 and g(t_max) < 0
+    t = brentq(g, 0.0, t_max, xtol=1e-13, rtol=1e-15, maxiter=200)
+    return centre[0] + t * math.cos(phi), centre[1] + t * math.sin(phi)
+
+
+@pytest.mark.parametrize("a,incl_deg", [(0.9, 80.0), (0.5, 30.0), (0.998, 60.0)])
+def test_critical_curve_distance_on_the_capture_boundary(orc, a, incl_deg):
+    """The critical curve (Bardeen's xi(r), eta(r) of the spherical photon
+    orbits) is the edge of the set of impact parameters whose photons the
+    black hole captures.  That edge is found here without the curve's
+    formulas: along 16 rays from a captured centre, the zero of min_r R(r) of
+    the radial potential; the oracle's distance from every such point to its
+    curve must vanish (a 1% error in xi or eta moves the curve by about
+    0.03-0.07 M and fails this)."""
+    th_o = math.radians(incl_deg)
+    centre = (2.0 * a * math.sin(th_o), 0.0)  # inside the shadow (shifted towards retrograde alpha > 0)
+    worst = 0.0
+    for k in range(16):
+        phi = (k + 0.5) * 2 * math.pi / 16
+        al, be = _shadow_edge(a, th_o, centre, phi)
+        d = orc.critical_curve_distance(1.0, a, th_o, al, be)
+        worst = max(worst, d)
+    assert worst < 1e-5, worst
+
+
+def test_critical_curve_distance_at_the_equatorial_photon_orbits(orc):
+    """Edge-on observer (th_o = 90 deg): the curve crosses beta = 0 at
+    alpha = -b, b = L/E of the prograde and retrograde circular equatorial
+    photon orbits.  b follows from R(r) = 0 on Q = 0 at the photon-orbit radius
+    (Bardeen's r_ph, pinned against the paper's photon orbits above):
+    r^2 + a^2 - a b = s sqrt(Delta) (b - a), so
+    b = (r^2 + a^2 + s a sqrt(Delta)) / (a + s sqrt(Delta)); R'(r) = 0 there
+    is checked too.  Schwarzschild's circle of radius 3 sqrt(3) M is the a = 0
+    case."""
+    th_o = math.pi / 2
+    assert orc.critical_curve_distance(1.0, 0.0, th_o, 3 * math.sqrt(3.0), 0.0) < 1e-12
+    for a in (0.3, 0.7, 0.9, 0.998):
+        for prograde, s in ((1, 1.0), (0, -1.0)):
+            r = orc.photon_orbit(1.0, a, prograde)
+            Delta = r * r - 2 * r + a * a
+            sD = math.sqrt(Delta)
+            b = (r * r + a * a + s * a * sD) / (a + s * sD)
+            dR = 4 * r * (r * r + a * a - a * b) - (2 * r - 2) * (b - a) ** 2
+            assert abs(dR) < 1e-9 * (1 + abs(b)) ** 2 * r
+            assert (b > 0) == bool(prograde)
+            assert orc.critical_curve_distance(1.0, a, th_o, -b, 0.0) < 1e-5
+            # a point 1% further out along alpha is about 0.01 |b| away
+            assert orc.critical_curve_distance(1.0, a, th_o, -1.01 * b, 0.0) > 0.004 * abs(b)
+
+
+def test_critical_curve_polyline_distance_matches_pointwise(orc):
+    """The vectorised distance (k-d tree on the curve as a polyline, used to
+    mask whole images) agrees with the pointwise distance near the curve and
+    reports +inf beyond its search radius."""
+    r_ = rng(31)
+    for a, incl in ((0.9, 80.0), (0.5, 30.0), (0.0, 45.0), (0.998, 5.0)):
+        th_o = math.radians(incl)
+        al, be = orc.critical_curve_polyline(1.0, a, th_o, 2000)
+        # points scattered around the curve and far from it
+        k = r_.integers(0, len(al), 200)
+        pa = np.concatenate([al[k] + r_.normal(0, 0.08, 200), r_.uniform(-25, 25, 100)])
+        pb = np.concatenate([be[k] + r_.normal(0, 0.08, 200), r_.uniform(-25, 25, 100)])
+        d_many = orc.critical_curve_distance_many(1.0, a, th_o, pa, pb)
+        d_one = np.array([orc.critical_curve_distance(1.0, a, th_o, x, y) for x, y in zip(pa, pb)])
+        near = d_one < 0.2
+        assert near.sum() > 150
+        np.testing.assert_allclose(d_many[near], d_one[near], atol=1e-6)
+        assert np.all(np.isinf(d_many[d_one > 0.3]))
+
+
 # --------------------------------------------------------------------------- generic bound orbits
 def test_splitmix64_published_vector(orc):
     """SplitMix64 from state 0: the generator's published first outputs."""
