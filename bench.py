@@ -46,15 +46,17 @@ def kernel_source_hash() -> str:
 
 # algorithmic flops per RK4 step, counted from the kernel source expressions
 # (FMA = 2, add/mul = 1, a product or sum written once and reused counted
-# once): 120 per Kerr right-hand side of the geodesic form, 42 per
-# Schwarzschild one, 102 for the RK4 stage points and weighted sums; the
+# once): 89 per Kerr right-hand side of the geodesic form (42 products, 20
+# FMA, 7 sums: the contraction written through q = 2Mr/rho^2 and
+# v = u^t - a sin^2 u^phi), 42 per Schwarzschild one, 102 for the RK4 stage
+# points and weighted sums; the
 # canonical form (eq. Ham): 72 per Kerr right-hand side, 74 for its RK4
 # (p_t, p_ph fixed); the 3+1 form: 65 for Kerr's lapse, shift, 3-metric and
 # their logarithmic derivatives plus 34 for the 3+1 right-hand side, the same
 # 74 for its RK4.  Listed separately per step: 4 reciprocals (a hardware
 # estimate and 3 FMA each), 1 sincos and 3 stage-angle rotations (angle
-# addition with short Taylor series, about 19 FP64 operations each).
-FLOPS_PER_STEP = {"kerr": 4 * 120 + 102, "schw": 4 * 42 + 102, "kerr_canonical": 4 * 72 + 74,
+# addition with short Taylor series, 17 FP64 operations each: 3 products, 14 FMA).
+FLOPS_PER_STEP = {"kerr": 4 * 89 + 102, "schw": 4 * 42 + 102, "kerr_canonical": 4 * 72 + 74,
                   "kerr_adm": 4 * (65 + 34) + 74,
                   # Dormand-Prince 5(4) attempt: 6 Kerr right-hand sides, 272 for
                   # the six stage combinations, 72 + 16 for the stage points and
@@ -62,7 +64,7 @@ FLOPS_PER_STEP = {"kerr": 4 * 120 + 102, "schw": 4 * 42 + 102, "kerr_canonical":
                   # the error estimate, 33 for the error norm (its 8 divisions,
                   # sqrt and log2 listed apart, like the 6 reciprocals, 1 sincos
                   # and 6 stage-angle rotations)
-                  "kerr_dopri5": 6 * 120 + 272 + 72 + 16 + 6 + 96 + 33}
+                  "kerr_dopri5": 6 * 89 + 272 + 72 + 16 + 6 + 96 + 33}
 PLUS_PER_STEP = {"reciprocal": 4, "sincos": 1, "stage_angle_rotation": 3}
 
 

@@ -9,9 +9,11 @@
 //   = (d_a g_{nu b}) u^a u^b - 1/2 (d_nu g_ab) u^a u^b,
 // which only needs the five metric components, their r- and theta-
 // derivatives along u (the metric depends on r and theta alone) and the
-// closed-form inverse of the (t, phi) block (det = -Delta sin^2).  It is the
-// same bilinear form as the twenty second-kind symbols of BL Kerr, with far
-// fewer operations.  Schwarzschild uses its nine non-zero second-kind symbols
+// closed-form inverse of the (t, phi) block (det = -Delta sin^2); written
+// through q = 2Mr/rho^2 and v = u^t - a sin^2 u^phi, the terms of the (t, phi)
+// block collapse (see accel_kerr).  It is the same bilinear form as the twenty
+// second-kind symbols of BL Kerr, with far fewer operations.  Schwarzschild
+// uses its nine non-zero second-kind symbols
 // directly.  One reciprocal per evaluation: 1/rho^2, 1/Delta and 1/sin^2 are
 // products of 1/(rho^2 Delta sin^2).  In FP64 one sincos per RK4 step: the
 // later stage angles take the angle-addition formulas (stage_trig).
@@ -63,10 +65,14 @@ template <typename T>
 __device__ __forceinline__ void stage_trig(T s0, T c0, T d, T th, T* s, T* c) {
   Trig<T>::sc(th, s, c);
 }
+// The range test |d| < 1/4 reads the exponent bits on the integer pipe (an
+// FP64 compare would take an issue of the FP64 unit, which costs as much as
+// an FMA there); sin th = s0 + c0 sin d + s0 (cos d - 1) and likewise cos th
+// are two FMAs each.
 template <>
 __device__ __forceinline__ void stage_trig<double>(double s0, double c0, double d, double th, double* s,
                                                    double* c) {
-  if (fabs(d) <= 0.25) {
+  if ((__double2hiint(d) & 0x7fffffff) < 0x3fd00000) {  // |d| < 0.25 (NaN: no)
     const double z = d * d;
     double ps = fma(z, -1.0 / 39916800.0, 1.0 / 362880.0);
     ps = fma(z, ps, -1.0 / 5040.0);
@@ -79,12 +85,26 @@ __device__ __forceinline__ void stage_trig<double>(double s0, double c0, double 
     pc = fma(z, pc, 1.0 / 24.0);
     pc = fma(z, pc, -0.5);
     const double cm1 = z * pc;  // cos d - 1
-    *s = s0 + fma(s0, cm1, c0 * sd);
-    *c = c0 + fma(c0, cm1, -s0 * sd);
+    *s = fma(s0, cm1, fma(c0, sd, s0));
+    *c = fma(c0, cm1, fma(-s0, sd, c0));
   } else {
     sincos(th, s, c);
   }
 }
+
+// Ordering key of a radius for the termination tests, on the integer pipe:
+// the signed 64-bit view of its bits, with every NaN mapped above all
+// numbers.  For r_ref > 0 finite and any r: key(r) <= bits(r_ref) exactly
+// when r <= r_ref holds in IEEE arithmetic, and key(r) >= bits(r_ref)
+// exactly when r >= r_ref or r is NaN (termination tests non-finite states
+// before escape, so the NaN case never decides an escape).  The minimum of
+// several keys is <= bits(r_ref) exactly when one of the radii is <= r_ref.
+__device__ __forceinline__ long long radius_key(double r) {
+  const long long b = __double_as_longlong(r);
+  return (b & 0x7fffffffffffffffll) > 0x7ff0000000000000ll ? 0x7ff8000000000000ll : b;
+}
+__device__ __forceinline__ bool key_le(long long k, double ref) { return k <= __double_as_longlong(ref); }
+__device__ __forceinline__ bool key_ge(long long k, double ref) { return k >= __double_as_longlong(ref); }
 
 template <typename T>
 struct BH {
@@ -125,61 +145,69 @@ __device__ __forceinline__ void accel_schw(const BH<T>& bh, T r, T s, T c, T ut,
 }
 
 // ---------------------------------------------------------------------------
-// Kerr (see the file header).  q = 2Mr/rho^2, so that
-//   g_tt = q - 1, g_tph = -a s^2 q, g_phph = s^2 (r^2 + a^2 + a^2 s^2 q),
+// Kerr (see the file header).  With q = 2Mr/rho^2 the metric is
+//   g_tt = q - 1, g_tph = -a s^2 q, g_phph = s^2 (r^2 + a^2) + a^2 s^4 q,
 //   g_rr = rho^2/Delta, g_thth = rho^2,
-//   d_r q = (2M - 2 r q)/rho^2, d_th q = 2 a^2 s c q / rho^2.
+//   d_r q = (2M - 2 r q)/rho^2, d_th q = 2 a^2 s c q / rho^2,
+// and q enters the (t, phi) block only through g_tt u^t u^t + 2 g_tph u^t u^ph
+// + g_phph u^ph u^ph = (q - 1)(u^t)^2 + ... whose q-part is q v^2 with
+// v = u^t - a s^2 u^ph.  Collecting terms of the first-kind contraction
+// W_nu = (d_a g_{nu b}) u^a u^b - 1/2 (d_nu g_ab) u^a u^b, D = u^r d_r + u^th d_th:
+//   W_t = (D q) v - 2 a q s c u^th u^ph,
+//   X = a s^2 W_t + W_ph = 2 s c u^th B + 2 r s^2 u^r u^ph,  B = (r^2 + a^2) u^ph - a q v
+//   (the D q terms cancel in X),
+//   2 W_r = (u^r)^2 d_r g_rr + 2 u^r u^th d_th g_rr - K_r,
+//   K_r = (d_r q) v^2 + 2 r (s^2 (u^ph)^2 + (u^th)^2),
+//   2 W_th = 4 r u^r u^th - 2 a^2 s c (u^th)^2 - K_th,
+//   K_th = (d_th q) v^2 + 2 s c u^ph (B - a q v) + (d_th g_rr) (u^r)^2,
+// and acc^mu = -g^{mu nu} W_nu with g^tt = -(r^2 + a^2 + a^2 s^2 q)/Delta,
+// g^tph = -a q/Delta, g^phph = (1 - q)/(Delta s^2), g^rr = Delta/rho^2,
+// g^thth = 1/rho^2:
+//   acc^t = ((r^2 + a^2) W_t + a q X) / Delta,  acc^ph = ((q - 1) X + a s^2 W_t) / (Delta s^2),
+//   acc^r = -Delta W_r / rho^2,                  acc^th = -W_th / rho^2.
+// The same bilinear form as the twenty second-kind symbols of BL Kerr, in 71
+// FP64 operations plus one reciprocal.
 template <typename T, bool kFastRcp = true>
 __device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T s, T c, T ut, T ur, T uth, T uph,
                                            T acc[4]) {
   const T a = bh.a, a2 = bh.a2;
   const T s2 = s * s, sc = s * c;
-  const T r2 = r * r;
-  const T rho2 = fma(a2, c * c, r2);
-  const T Delta = fma(r, r - bh.twoM, a2);
+  const T r2a2 = fma(r, r, a2);
+  const T rho2 = fma(-a2, s2, r2a2);
+  const T tMr = bh.twoM * r;
+  const T Delta = r2a2 - tMr;
   const T Ds2 = Delta * s2;
   const T inv = kFastRcp ? recip<T>(rho2 * Ds2) : T(1) / (rho2 * Ds2);
   const T irho2 = Ds2 * inv;
   const T iDs2 = rho2 * inv;  // 1 / (Delta sin^2)
   const T iDelta = iDs2 * s2;
-  const T r_2 = T(2) * r;
-  const T q = bh.twoM * r * irho2;
-  const T qi = q * irho2;
+  const T q = tMr * irho2;
+  const T r_2 = r + r;
   const T dq_r = fma(-r_2, q, bh.twoM) * irho2;
-  const T a2sc_2 = bh.two_a2 * sc;  // 2 a^2 sin cos
-  const T dq_th = a2sc_2 * qi;
-  const T r2a2 = fma(r, r, a2);
-  const T s4 = s2 * s2;
+  const T a2sc2 = bh.two_a2 * sc;  // 2 a^2 sin cos
+  const T dq_th = a2sc2 * (q * irho2);
+  const T Dq = fma(ur, dq_r, uth * dq_th);
   const T as2 = a * s2;
-  // d_r and d_theta of g_tt, g_tph, g_phph, g_rr, g_thth
-  const T dtp_r = -as2 * dq_r;
-  const T dtp_th = -a * fma(T(2) * sc, q, s2 * dq_th);
-  const T dpp_r = fma(a2 * s4, dq_r, r_2 * s2);
-  const T dpp_th = fma(T(2) * sc, r2a2, a2 * fma(T(4) * s2 * sc, q, s4 * dq_th));
-  const T drr_r = fma(-rho2 * T(2) * (r - bh.M), iDelta, r_2) * iDelta;
-  const T drr_th = -a2sc_2 * iDelta;
-  const T dhh_r = r_2;
-  const T dhh_th = -a2sc_2;
-  // derivatives along u: D = u^r d_r + u^th d_th
-  const T Dtt = fma(ur, dq_r, uth * dq_th);
-  const T Dtp = fma(ur, dtp_r, uth * dtp_th);
-  const T Dpp = fma(ur, dpp_r, uth * dpp_th);
-  const T Drr = fma(ur, drr_r, uth * drr_th);
-  const T Dhh = fma(ur, dhh_r, uth * dhh_th);
-  // W_nu = Gamma_{nu ab} u^a u^b
-  const T Wt = fma(Dtt, ut, Dtp * uph);
-  const T Wp = fma(Dtp, ut, Dpp * uph);
-  const T ut2 = ut * ut, uph2 = uph * uph, utp2 = T(2) * ut * uph, ur2 = ur * ur, uth2 = uth * uth;
-  const T Kr = fma(dq_r, ut2, fma(dtp_r, utp2, fma(dpp_r, uph2, fma(drr_r, ur2, dhh_r * uth2))));
-  const T Kth = fma(dq_th, ut2, fma(dtp_th, utp2, fma(dpp_th, uph2, fma(drr_th, ur2, dhh_th * uth2))));
-  const T Wr = fma(Drr, ur, T(-0.5) * Kr);
-  const T Wth = fma(Dhh, uth, T(-0.5) * Kth);
-  // raise with g^{mu nu}: (t, phi) block inverse has det = -Delta sin^2
-  acc[1] = -Wr * Delta * irho2;
-  acc[2] = -Wth * irho2;
-  const T gpp_s2 = fma(a * as2, q, r2a2);
-  acc[0] = fma(gpp_s2, Wt, a * q * Wp) * iDelta;
-  acc[3] = fma(q - T(1), Wp, as2 * q * Wt) * iDs2;
+  const T v = fma(-as2, uph, ut);
+  const T aq = a * q;
+  const T aqv = aq * v;
+  const T B = fma(r2a2, uph, -aqv);
+  const T sc2 = sc + sc;
+  const T sc2uth = sc2 * uth;
+  const T X = fma(sc2uth, B, (r_2 * s2) * (ur * uph));
+  const T Wt = fma(Dq, v, -(aq * sc2uth) * uph);
+  acc[0] = fma(r2a2, Wt, aq * X) * iDelta;
+  acc[3] = fma(q, X, fma(as2, Wt, -X)) * iDs2;
+  const T v2 = v * v;
+  const T Kr = fma(dq_r, v2, r_2 * fma(s2 * uph, uph, uth * uth));
+  const T drr_r = fma(-(r_2 - bh.twoM) * rho2, iDelta, r_2) * iDelta;  // d_r g_rr
+  const T drr_th = -a2sc2 * iDelta;                                       // d_th g_rr
+  const T Wr2 = fma(ur, fma(ur, drr_r, (uth + uth) * drr_th), -Kr);      // 2 W_r
+  const T Kth = fma(dq_th, v2, fma(sc2 * uph, B - aqv, drr_th * (ur * ur)));
+  const T Wth2 = fma(uth, fma(-a2sc2, uth, (r_2 + r_2) * ur), -Kth);     // 2 W_th
+  const T hirho2 = T(0.5) * irho2;
+  acc[1] = -Wr2 * (Delta * hirho2);
+  acc[2] = -Wth2 * hirho2;
 }
 
 // The acceleration at (r, theta) given s = sin theta, c = cos theta
@@ -210,14 +238,19 @@ __device__ __forceinline__ void accel(const BH<T>& bh, T r, T th, T ut, T ur, T 
 // instruction-cache misses; there each stage takes its own sincos and the
 // division, which keeps those kernels' register count down: their FP64 steps
 // are rare and their occupancy matters more).  Returns the smallest radius
-// among the three intermediate stage points (used by the capture test).
+// among the three intermediate stage points (used by the capture test; NaN
+// radii are passed over).  FP64 unrolled: the minimum is taken over
+// radius_key on the integer pipe and the radius returned is the one whose
+// key is smallest, which decides "some stage radius <= r_cap" identically.
 template <bool kKerr, typename T, bool kRolled = false>
 __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
+  constexpr bool kKeys = sizeof(T) == 8 && !kRolled;
   const T hh = T(0.5) * h;
   T r = y[1], th = y[2];
   T u[4] = {y[4], y[5], y[6], y[7]};
   T sx[4], su[4];
   T rmin = T(0);
+  long long kmin = 0;
   T s0 = T(0), c0 = T(1);
   if constexpr (!kRolled) Trig<T>::sc(y[2], &s0, &c0);
   T sn = s0, cs = c0;
@@ -251,7 +284,12 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
       if constexpr (!kRolled) stage_trig<T>(s0, c0, c * u[2], th, &sn, &cs);
 #pragma unroll
       for (int j = 0; j < 4; ++j) u[j] = fma(c, acc[j], y[4 + j]);
-      rmin = s == 0 ? r : fmin(rmin, r);
+      if constexpr (kKeys) {
+        const long long k = radius_key(r);
+        kmin = s == 0 ? k : min(kmin, k);
+      } else {
+        rmin = s == 0 ? r : fmin(rmin, r);
+      }
     }
   };
   if constexpr (kRolled) {
@@ -267,6 +305,7 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
     y[j] = fma(h6, sx[j], y[j]);
     y[4 + j] = fma(h6, su[j], y[4 + j]);
   }
+  if constexpr (kKeys) rmin = __longlong_as_double(kmin);
   return rmin;
 }
 
@@ -462,13 +501,16 @@ __device__ __forceinline__ void adm_raise(const Adm<double>& m, const double p[4
 
 // One classical RK4 step of the canonical state z (same tableau and the same
 // stage-by-stage sums as rk4_step); p_t = z[4] and p_ph = z[7] stay fixed.
-// Returns the smallest radius among the three intermediate stage points.
+// Returns the smallest radius among the three intermediate stage points (as
+// rk4_step, by radius_key in the FP64 unrolled case).
 template <typename T, bool kRolled = false, int kForm = kHamKerrBL>
 __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
+  constexpr bool kKeys = sizeof(T) == 8 && !kRolled;
   const T hh = T(0.5) * h;
   T r = z[1], th = z[2], pr = z[5], pth = z[6];
   T sx[6];
   T rmin = T(0);
+  long long kmin = 0;
   T s0 = T(0), c0 = T(1);
   if constexpr (!kRolled) Trig<T>::sc(z[2], &s0, &c0);
   T sn = s0, cs = c0;
@@ -496,7 +538,12 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
       if constexpr (!kRolled) stage_trig<T>(s0, c0, c * f[2], th, &sn, &cs);
       pr = fma(c, f[4], z[5]);
       pth = fma(c, f[5], z[6]);
-      rmin = s == 0 ? r : fmin(rmin, r);
+      if constexpr (kKeys) {
+        const long long k = radius_key(r);
+        kmin = s == 0 ? k : min(kmin, k);
+      } else {
+        rmin = s == 0 ? r : fmin(rmin, r);
+      }
     }
   };
   if constexpr (kRolled) {
@@ -511,6 +558,7 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
   for (int j = 0; j < 4; ++j) z[j] = fma(h6, sx[j], z[j]);
   z[5] = fma(h6, sx[4], z[5]);
   z[6] = fma(h6, sx[5], z[6]);
+  if constexpr (kKeys) rmin = __longlong_as_double(kmin);
   return rmin;
 }
 

@@ -337,7 +337,6 @@ __device__ __forceinline__ unsigned nsmid() {
 // in place).
 constexpr unsigned long long kZoneWarpWaitNs = 600ull * 1000000000ull;
 
-// Launch bounds: at most kMaxTPB threads, one block per SM guaranteed.  The
 static_assert(kHamKerrBL == MALBEC_FORM_HAMILTONIAN && kHamAdm == MALBEC_FORM_ADM, "form codes");
 
 // (x, u) -> (x, p): p = g u, with g of eq. kerr or of the 3+1 quantities.
@@ -364,12 +363,25 @@ __device__ __forceinline__ void to_velocity(double M, double a, const double z[8
   }
 }
 
-// kernel runs one to eight warps per SM (see choose_shape), so the register
-// budget is not the occupancy limit; without the minimum-blocks argument the
-// compiler capped some instantiations (the request-loop ones) at 128
-// registers and spilled.
+// Launch bounds: at most kMaxTPB threads per block, one block per SM
+// guaranteed.  The kernel runs one to eight warps per SM (see choose_shape),
+// so the register budget is not the occupancy limit; without the
+// minimum-blocks argument the compiler gives every instantiation fewer
+// registers (the FP32_MIXED camera kernel 146 instead of 190, and 1.9x slower:
+// 20.5 against 10.8 ms per 1024^2 render; some request-loop instantiations
+// were capped at 128 and spilled).  The one exception is the FP32_MIXED
+// job-table kernel with the block ray exchange, whose autotuned shape is three
+// 128-thread blocks per SM: it is held to 168 registers (3 x 128 x 168 <=
+// 65536; with 176 registers it ran on two blocks per SM, and the 4096 uneven
+// bundles took 32.7 s against 27.4 s).
+template <bool kMixed, int kSrc, bool kBanks>
+constexpr int trace_reg_cap() {
+  return (kMixed && kBanks && kSrc == kSrcJobs) ? 168 : 255;
+}
+
 template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, int kForm, int kMethod>
-__global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) {
+__global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed, kSrc, kBanks>()))
+    trace_kernel(const TraceParams p) {
   static_assert(!kBanks || kMixed, "block banks exist for FP32_MIXED only");
   constexpr bool kHam = kForm != MALBEC_FORM_GEODESIC;
   static_assert(!kHam || kKerr, "the canonical forms use the Kerr Hamiltonian (a = 0 included)");
@@ -922,8 +934,10 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         else
           rmin = rk4_step<kKerr, double>(bh64, h, y);
         lam += h;
-        captured = (y[1] <= r_cap) | (rmin <= r_cap);
-        escaped = y[1] >= r_esc;
+        // the radius tests on the integer pipe (radius_key)
+        const long long k1 = radius_key(y[1]);
+        captured = key_le(k1, r_cap) | key_le(radius_key(rmin), r_cap);
+        escaped = key_ge(k1, r_esc);
         finite = finite8(y);
       } else if (in_zone) {
         // FP64 zone (horizon, photon orbits, polar axis)
@@ -938,8 +952,9 @@ __global__ void __launch_bounds__(kMaxTPB, 1) trace_kernel(const TraceParams p) 
         flush_lam();
         lam += h;
         split_pair(y, hi, lo);
-        captured = (y[1] <= r_cap) | (rmin <= r_cap);
-        escaped = y[1] >= r_esc;
+        const long long k1 = radius_key(y[1]);
+        captured = key_le(k1, r_cap) | key_le(radius_key(rmin), r_cap);
+        escaped = key_ge(k1, r_esc);
         finite = finite8(y);
       } else {
         float hf, h6h, h6l;
