@@ -293,14 +293,20 @@ int malbec_trace(malbec_metric m, const double* ics, uint64_t n, malbec_term t,
  * that loads the library until the process exits.  No cudaMalloc, cudaFree,
  * stream-ordered or library allocation is made: the call enqueues a memset of
  * the block (it keeps the previous call's contents) and the kernel.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
+ *  - The first call in a CUDA context (in practice the first call on each
+ *    device, with that device current) looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it under the context's id; a context
+ *    made after cudaDeviceReset looks it up again.  Make that first call
  *    before any stream capture.
  *  - Every call on a device shares the one array: calls whose work overlaps
  *    on the GPU (different streams, or graphs replayed concurrently) race on
  *    the work queue and give wrong results.  Serialise them.
- *  - A call whose scratch would exceed MALBEC_NOALLOC_SCRATCH_BYTES returns
- *    MALBEC_ESCRATCH; a trace needs one 256-byte block whatever n is. */
+ *  - A trace needs one 256-byte block whatever n is, so this call never
+ *    returns MALBEC_ESCRATCH (the code is kept for entry points whose
+ *    scratch grows with their arguments).
+ *  - The buffers are not checked on the host beyond NULL and alignment (the
+ *    library sees raw pointers): ics must hold 8 n doubles, a_per_ray n
+ *    doubles, out layout.total bytes, all on the current device. */
 #define MALBEC_NOALLOC_SCRATCH_BYTES 256
 int malbec_trace_noalloc(malbec_metric m, const double* ics, uint64_t n, malbec_term t,
                          malbec_out_mode mode, uint32_t stride, malbec_precision prec, void* out,

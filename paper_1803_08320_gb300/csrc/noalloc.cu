@@ -21,32 +21,87 @@ namespace malbec {
 namespace {
 
 // The kernel's work-queue block lives here.  In host code this name is only
-// a stand-in for the device object: its device address is looked up once
-// per device with cudaGetSymbolAddress.
+// a stand-in for the device object: its device address is looked up with
+// cudaGetSymbolAddress once per CUDA context (in practice once per device,
+// in the device's primary context).
 __device__ __align__(256) unsigned char g_noalloc_scratch[MALBEC_NOALLOC_SCRATCH_BYTES];
 
 // Scratch one trace launch needs: the work-queue counter block (the same
-// size malbec_trace allocates), independent of the number of rays.
+// size malbec_trace allocates), independent of the number of rays.  It fits
+// the static block by construction, so this call never returns
+// MALBEC_ESCRATCH; the code is kept for entry points with larger scratch.
 constexpr size_t kTraceScratchBytes = 256;
+static_assert(kTraceScratchBytes <= MALBEC_NOALLOC_SCRATCH_BYTES, "the work-queue block fits the static array");
 
 std::mutex g_mu;
-void* g_scratch_ptr[64];
 
-// Device address of g_noalloc_scratch on the current device, looked up on
-// the first call for that device (with that device current).
-int scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return set_cuda_error(e);
-  if (dev < 0 || dev >= 64) return MALBEC_EINVAL;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return set_cuda_error(e);
-    g_scratch_ptr[dev] = p;
+// The address is cached per CUDA context, keyed by the context's id
+// (cuCtxGetId: unique over the life of the process), so that a context
+// created after cudaDeviceReset -- which unloads this library's device code
+// and with it the array -- looks the address up again instead of reusing a
+// stale one.  The two driver calls are reached through the runtime
+// (cudaGetDriverEntryPointByVersion), so the library does not link libcuda.
+struct CtxScratch {
+  unsigned long long ctx_id;
+  void* ptr;
+};
+constexpr int kCtxSlots = 64;
+CtxScratch g_slots[kCtxSlots];
+int g_next_slot = 0;
+
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+
+// The id of the calling thread's current context, creating the device's
+// primary context first if there is none yet (cudaGetSymbolAddress does that
+// as a side effect: no allocation call is made).
+int current_ctx_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess || !f1)
+      return set_cuda_error(e != cudaSuccess ? e : cudaErrorNotSupported);
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess || q2 != cudaDriverEntryPointSuccess || !f2)
+      return set_cuda_error(e != cudaSuccess ? e : cudaErrorNotSupported);
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
   }
-  *out = g_scratch_ptr[dev];
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0) return set_cuda_error(cudaErrorDeviceUninitialized);
+  if (!ctx) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (get_current(&ctx) != 0 || !ctx) return set_cuda_error(cudaErrorDeviceUninitialized);
+  }
+  if (get_id(ctx, id) != 0) return set_cuda_error(cudaErrorDeviceUninitialized);
+  return MALBEC_OK;
+}
+
+// Device address of g_noalloc_scratch in the current context, looked up on
+// the first call in that context (with its device current).
+int scratch_address(void** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  unsigned long long id = 0;
+  int rc = current_ctx_id(&id);
+  if (rc) return rc;
+  for (int k = 0; k < kCtxSlots; ++k) {
+    if (g_slots[k].ptr && g_slots[k].ctx_id == id) {
+      *out = g_slots[k].ptr;
+      return MALBEC_OK;
+    }
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  g_slots[g_next_slot] = CtxScratch{id, p};
+  g_next_slot = (g_next_slot + 1) % kCtxSlots;
+  *out = p;
   return MALBEC_OK;
 }
 
@@ -69,7 +124,6 @@ extern "C" int malbec_trace_noalloc(malbec_metric m, const double* ics, uint64_t
   rc = malbec_out_layout(mode, prec, n, t.n_steps_cap, stride, &L);
   if (rc) return rc;
   if (((uintptr_t)out & 255u) != 0) return MALBEC_EINVAL;
-  if (kTraceScratchBytes > MALBEC_NOALLOC_SCRATCH_BYTES) return MALBEC_ESCRATCH;
   char* o = static_cast<char*>(out);
   TraceParams p;
   memset(&p, 0, sizeof(p));

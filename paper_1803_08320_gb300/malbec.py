@@ -262,11 +262,44 @@ def _views_final(buf, L: Layout, n: int, mode: int, precision):
     return out
 
 
+def check_device_tensor(t, name: str, dtype, numel_min: int = None, numel: int = None, shape=None,
+                        device_type: str = "cuda", device_index=None):
+    """Raise ValueError unless `t` is a contiguous tensor of `dtype` on the
+    given device with the given shape or element count.  The library sees raw
+    pointers only and cannot check sizes: a short or misplaced buffer would
+    make a kernel read or write out of bounds, so the binding checks before
+    any call."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch.Tensor, got {type(t).__name__}")
+    if t.device.type != device_type:
+        raise ValueError(f"{name}: expected a {device_type} tensor, got one on {t.device}")
+    if device_index is not None and t.device.index != device_index:
+        raise ValueError(f"{name}: on {t.device}, but the current device is {device_type}:{device_index}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+    if numel_min is not None and t.numel() < numel_min:
+        raise ValueError(f"{name}: needs at least {numel_min} elements, got {t.numel()}")
+
+
+def _current_device_index():
+    torch = _torch()
+    return torch.cuda.current_device() if torch.cuda.is_available() else None
+
+
 def trace(M: float, a: float, ics, term, mode: int = OUT_FINAL, stride: int = 0, precision="fp64",
           a_per_ray=None, stream=None, out=None):
     """Integrate the rays `ics` ((8, n) float64 on the GPU, SoA).  Returns a
     dict of views: y (8, n), lambda, inv0 (4, n), inv1 (4, n), steps (int32
-    view of the uint32 field), fate, [traj (n, n_samples, 8)]."""
+    view of the uint32 field), fate, [traj (n, n_samples, 8)].  `out`, if
+    given, is a contiguous uint8 CUDA tensor of at least out_layout(...).total
+    bytes on the same device as `ics`."""
     torch = _torch()
     ics = _dev_f64(ics)
     n = ics.shape[1]
@@ -274,7 +307,11 @@ def trace(M: float, a: float, ics, term, mode: int = OUT_FINAL, stride: int = 0,
     L = out_layout(mode, precision, n, t.n_steps_cap, stride if mode == OUT_STRIDED else 0)
     if out is None:
         out = torch.empty(L.total, dtype=torch.uint8, device=ics.device)
+    else:
+        check_device_tensor(out, "out", torch.uint8, numel_min=int(L.total), device_index=ics.device.index)
     apr = None if a_per_ray is None else _dev_f64(a_per_ray)
+    if apr is not None:
+        check_device_tensor(apr, "a_per_ray", torch.float64, numel=n, device_index=ics.device.index)
     m = Metric(float(M), float(a), _ptr(apr))
     _check(lib().malbec_trace(m, _ptr(ics), n, t.c(), mode, stride if mode == OUT_STRIDED else 0,
                               _prec(precision), _ptr(out), _stream(stream)), "malbec_trace")
@@ -286,13 +323,24 @@ def trace(M: float, a: float, ics, term, mode: int = OUT_FINAL, stride: int = 0,
 def trace_noalloc(M: float, a: float, ics, term, out, mode: int = OUT_FINAL, stride: int = 0,
                   precision="fp64", a_per_ray=None, stream=None):
     """`trace` through malbec_trace_noalloc, for callers that cannot allocate
-    device memory: `out` (a uint8 CUDA tensor of out_layout(...).total bytes)
-    and `ics` must already be on the device; the library uses its static
+    device memory: `out` (a contiguous uint8 CUDA tensor of at least
+    out_layout(...).total bytes), `ics` (contiguous float64, shape (8, n)) and
+    `a_per_ray` (contiguous float64, n elements, or None) must already be on
+    the current device; they are checked here, without copies, and a bad one
+    raises ValueError before anything runs.  The library uses its static
     work-queue block and allocates nothing.  Calls that overlap on the GPU
     share that block and race: serialise them."""
+    torch = _torch()
+    dev = _current_device_index()
+    check_device_tensor(ics, "ics", torch.float64, device_index=dev)
+    if ics.dim() != 2 or ics.shape[0] != 8 or ics.shape[1] < 1:
+        raise ValueError(f"ics: expected shape (8, n) with n >= 1, got {tuple(ics.shape)}")
     t = term_from(term)
     n = ics.shape[1]
     L = out_layout(mode, precision, n, t.n_steps_cap, stride if mode == OUT_STRIDED else 0)
+    check_device_tensor(out, "out", torch.uint8, numel_min=int(L.total), device_index=dev)
+    if a_per_ray is not None:
+        check_device_tensor(a_per_ray, "a_per_ray", torch.float64, numel=n, device_index=dev)
     m = Metric(float(M), float(a), _ptr(a_per_ray))
     _check(lib().malbec_trace_noalloc(m, _ptr(ics), n, t.c(), mode, stride if mode == OUT_STRIDED else 0,
                                       _prec(precision), _ptr(out), _stream(stream)), "malbec_trace_noalloc")

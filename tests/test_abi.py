@@ -217,3 +217,41 @@ def test_diagnostics_validate_before_any_cuda_call(mb):
     assert lib.malbec_measure_step_loop(0, None) == mb.EINVAL
     assert lib.malbec_check_fp64_helpers(None) == mb.EINVAL
     assert lib.malbec_measure_fma_peak(5, ctypes.byref(v)) == mb.EINVAL
+
+
+def test_binding_tensor_checks_reject_bad_buffers(mb):
+    """The library sees raw pointers only, so the binding checks every buffer
+    it hands over (device, dtype, contiguity, size) before any call; each bad
+    case raises ValueError.  Checked here on CPU tensors with the device type
+    the check expects set to "cpu"."""
+    import torch
+
+    chk = mb.check_device_tensor
+    good = torch.zeros((8, 5), dtype=torch.float64)
+    chk(good, "ics", torch.float64, shape=(8, 5), device_type="cpu")
+    with pytest.raises(ValueError, match="float64"):
+        chk(good.float(), "ics", torch.float64, device_type="cpu")
+    with pytest.raises(ValueError, match="contiguous"):
+        chk(torch.zeros((5, 8), dtype=torch.float64).t(), "ics", torch.float64, device_type="cpu")
+    with pytest.raises(ValueError, match="shape"):
+        chk(good, "ics", torch.float64, shape=(8, 6), device_type="cpu")
+    with pytest.raises(ValueError, match="4 elements"):
+        chk(torch.zeros(5, dtype=torch.float64), "a_per_ray", torch.float64, numel=4, device_type="cpu")
+    with pytest.raises(ValueError, match="at least 1000"):
+        chk(torch.zeros(999, dtype=torch.uint8), "out", torch.uint8, numel_min=1000, device_type="cpu")
+    with pytest.raises(ValueError, match="cuda"):
+        chk(good, "ics", torch.float64)
+    with pytest.raises(ValueError, match="torch.Tensor"):
+        chk(np.zeros((8, 5)), "ics", torch.float64, device_type="cpu")
+
+
+def test_noalloc_binding_rejects_host_buffers_before_any_call(mb):
+    """trace_noalloc never copies: host tensors are refused with ValueError
+    (a raw host pointer handed to the kernel would fault)."""
+    import torch
+
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=10, dl=0.01)
+    ics = torch.zeros((8, 4), dtype=torch.float64)
+    out = torch.zeros(1 << 16, dtype=torch.uint8)
+    with pytest.raises(ValueError, match="ics"):
+        mb.trace_noalloc(1.0, 0.5, ics, t, out)

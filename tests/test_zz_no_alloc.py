@@ -71,3 +71,56 @@ def test_noalloc_rejects_invalid_arguments(mb):
                                     None) == mb.EINVAL
     assert lib.malbec_trace_noalloc(mb.Metric(1.0, 0.5, None), fake, 0, t, mb.OUT_FINAL, 0, mb.FP64, fake,
                                     None) == mb.EINVAL
+
+
+def _default_pool_used_high():
+    """USED_MEM_HIGH of the current device's default stream-ordered memory
+    pool (driver API through ctypes), after resetting the watermark to the
+    current use; returns (reset, read) callables."""
+    cu = ctypes.CDLL("libcuda.so.1")
+    dev = ctypes.c_int()
+    assert cu.cuCtxGetDevice(ctypes.byref(dev)) == 0
+    pool = ctypes.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    used_high = 8  # CU_MEMPOOL_ATTR_USED_MEM_HIGH
+
+    def reset():
+        zero = ctypes.c_uint64(0)
+        assert cu.cuMemPoolSetAttribute(pool, used_high, ctypes.byref(zero)) == 0
+
+    def read():
+        v = ctypes.c_uint64()
+        assert cu.cuMemPoolGetAttribute(pool, used_high, ctypes.byref(v)) == 0
+        return v.value
+
+    return reset, read
+
+
+def test_noalloc_takes_nothing_from_the_stream_ordered_pool(mb):
+    """The property the entry point exists for: malbec_trace takes its
+    work-queue block from the device's default stream-ordered pool (the
+    watermark of the pool's used bytes rises), malbec_trace_noalloc takes
+    nothing (the watermark stays where it was reset)."""
+    import torch
+
+    from paper_1803_08320_gb300 import workloads as W
+
+    wl = W.bound()
+    ics, spins, _ = mb.ic_bound(wl.M, wl.a_max, wl.seed, 512)
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=200, dl=0.02)
+    L = mb.out_layout(mb.OUT_FINAL, "fp64", 512, t.n_steps_cap, 0)
+    out = torch.empty(L.total, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    reset, read = _default_pool_used_high()
+    reset()
+    base = read()
+    mb.trace(wl.M, 0.0, ics, t, a_per_ray=spins)
+    torch.cuda.synchronize()
+    assert read() >= base + 256, "the control call should show its scratch block in the pool"
+    torch.cuda.synchronize()
+    reset()
+    base = read()
+    mb.trace_noalloc(wl.M, 0.0, ics, t, out, a_per_ray=spins)
+    mb.trace_noalloc(wl.M, 0.0, ics, t, out, a_per_ray=spins)
+    torch.cuda.synchronize()
+    assert read() == base
