@@ -254,7 +254,9 @@ def load_traffic(kind: str, field: str = "dram_bytes_per_launch"):
 
 def run_profile_case(args) -> None:
     """The same camera at 512 x 512 (a quarter of the rays, same physics):
-    small enough for a multi-pass ncu capture to end in seconds."""
+    small enough for a multi-pass ncu capture to end in seconds; the
+    *_1024 cases are the benchmark's own 1024 x 1024 image (for captures of
+    a few metrics)."""
     import torch
 
     from paper_1803_08320_gb300 import build as _b
@@ -275,9 +277,10 @@ def run_profile_case(args) -> None:
         steps = int(res["steps"].to(torch.int64).sum().item())
         print(json.dumps({"profile_case": args.profile_case, "rays": wl.n, "rk4_steps": steps}))
         return
-    cw = W.camera(nx=512, ny=512)
+    side = 1024 if args.profile_case.endswith("1024") else 512
+    cw = W.camera(nx=side, ny=side)
     cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
-    prec = "fp32_mixed" if args.profile_case.endswith("mixed") else "fp64"
+    prec = "fp32_mixed" if "mixed" in args.profile_case else "fp64"
     form = {"camera_canonical": mb.FORM_HAMILTONIAN, "camera_adm": mb.FORM_ADM}.get(args.profile_case,
                                                                                    mb.FORM_GEODESIC)
     term = mb.term_from(cw.term, form=form)
@@ -474,10 +477,9 @@ def run_bound_case(mb, torch, stream, flush, n: int, n_steps: int, precisions, w
         sec = e0.elapsed_time(e1) / 1e3
         steps = int(r["steps"].to(torch.int64).sum().item())
         ent = {"value": steps / sec, "unit": UNIT, "seconds": sec, "rk4_steps": steps,
-               "fates": {k: int((r["fate"] == v).sum().item()) for k, v in
-                         (("captured", 1), ("escaped", 2), ("capped", 3), ("nonfinite", 4))},
+               "fates": fate_counts(mb, r["fate"]),
                "drift_all_particles": drift_stats(r["inv0"].cpu().numpy(), r["inv1"].cpu().numpy())}
-        capped = (r["fate"] == mb.FATE_CAPPED).cpu().numpy()
+        capped = ((r["fate"] & mb.FATE_MASK) == mb.FATE_CAPPED).cpu().numpy()
         ent["drift_capped_particles"] = drift_stats(r["inv0"].cpu().numpy()[:, capped],
                                                     r["inv1"].cpu().numpy()[:, capped])
         ent["drift_note"] = ("particles that end before the cap are orbits that pass next to the polar axis, where "
@@ -611,7 +613,7 @@ def run_trajectory_case(mb, torch, stream, flush, n: int = 1 << 17, n_steps: int
 def drift_summary(mb, torch, r) -> dict:
     """Median and p99 of |inv1 - inv0| (E, L_z, Q, g(u,u)) over the rays that
     did not end non-finite."""
-    ok = r["fate"] != mb.FATE_NONFINITE
+    ok = (r["fate"] & mb.FATE_MASK) != mb.FATE_NONFINITE
     out = {}
     for c, nm in enumerate(("E", "Lz", "Q", "norm")):
         d = (r["inv1"][c] - r["inv0"][c]).abs()[ok]
@@ -709,7 +711,7 @@ def run_convergence_case(mb, torch, stream) -> dict:
                 t = W.Termination(eps_hor=0.01, r_esc=1e9, n_steps_cap=int(round(lam_end / h)), dl=h)
                 r = mb.trace(1.0, a, y0, t, precision="fp64", stream=stream, a_per_ray=spins)
                 stream.synchronize()
-                keep = (r["fate"] == mb.FATE_CAPPED)
+                keep = (r["fate"] & mb.FATE_MASK) == mb.FATE_CAPPED
                 y = r["y"].clone()
                 y[:, ~keep] = float("nan")
                 finals.append(y.cpu().numpy())
@@ -722,18 +724,19 @@ def serving_bundle(mb, r):
 
 
 def run_serving_case(mb, torch, rate: float, n_req: int, precision: str, budget: int = 150 * 10**9,
-                     timeout_s: float = 300.0) -> dict:
-    """Poisson arrivals at `rate` req/s (the first n_req of the seeded stream),
-    replayed in wall-clock time against (a) the continuous-batching server and
-    (b) one launch per request, in arrival order, on one stream.  Latency =
-    scheduled arrival -> the host sees the job's results complete in HBM.
-    Throughput = all RK4 steps / (first arrival -> last completion)."""
-    from collections import deque
-
+                     timeout_s: float = 300.0, stretch: float = 1.0, baseline_streams=(1,)) -> dict:
+    """Poisson arrivals at `rate` req/s (the first n_req of the seeded stream;
+    with `stretch` > 1 the same requests arrive that many times further
+    apart), replayed in wall-clock time against (a) the continuous-batching
+    server and (b) one launch per request, in arrival order, round-robin on
+    k streams for each k in `baseline_streams`.  Latency = scheduled arrival
+    -> the host sees the job's results complete in HBM.  Throughput = all RK4
+    steps / (first arrival -> last completion)."""
     from paper_1803_08320_gb300 import workloads as W
 
     reqs = W.serving(rate, duration=50.0 * n_req / rate)[:n_req]
     n_req = len(reqs)
+    t_arr = [stretch * (r.t_arrival - reqs[0].t_arrival) for r in reqs]
     cams = sum(1 for r in reqs if r.kind == "camera")
 
     def summarise(lat, steps, span):
@@ -751,7 +754,7 @@ def run_serving_case(mb, torch, rate: float, n_req: int, precision: str, budget:
     while len(done_at) < n_req:
         now = time.perf_counter() - t0
         assert now < timeout_s, "serving run exceeded its time limit"
-        while i < n_req and reqs[i].t_arrival <= now:
+        while i < n_req and t_arr[i] <= now:
             ids[srv.submit(bundles[i])] = i
             i += 1
         for jid, k in list(ids.items()):
@@ -764,50 +767,92 @@ def run_serving_case(mb, torch, rate: float, n_req: int, precision: str, budget:
         steps += int(v["steps"].to(torch.int64).sum().item())
         srv.release(jid)
     srv.close()
-    lat = [done_at[k] - reqs[k].t_arrival for k in range(n_req)]
-    served = summarise(lat, steps, max(done_at.values()) - reqs[0].t_arrival)
+    lat = [done_at[k] - t_arr[k] for k in range(n_req)]
+    served = summarise(lat, steps, max(done_at.values()))
     served["gpu_launches"] = int(stats["kernel_launches"])
 
-    # (b) one launch per request, FIFO on one stream
-    stream = torch.cuda.Stream()
-    bundles = [serving_bundle(mb, r) for r in reqs]
-    inflight, bufs, done_at = deque(), [], {}
-    i = 0
-    t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
+    # (b) one launch per request, round-robin on k streams
+    singles = {}
+    for k_streams in baseline_streams:
+        streams = [torch.cuda.Stream() for _ in range(k_streams)]
+        bundles = [serving_bundle(mb, r) for r in reqs]
+        inflight, bufs, done_at = {}, [], {}
+        i = 0
+        t0 = time.perf_counter()
         while len(done_at) < n_req:
             now = time.perf_counter() - t0
             assert now < timeout_s, "one-launch-per-request run exceeded its time limit"
-            while i < n_req and reqs[i].t_arrival <= now:
-                (v,) = mb.attach_outputs([bundles[i]], precision)
-                mb.trace_bundles([bundles[i]], precision, stream=stream)
+            while i < n_req and t_arr[i] <= now:
+                st = streams[i % k_streams]
+                with torch.cuda.stream(st):
+                    (v,) = mb.attach_outputs([bundles[i]], precision)
+                mb.trace_bundles([bundles[i]], precision, stream=st)
                 ev = torch.cuda.Event()
-                ev.record(stream)
-                inflight.append((i, ev))
+                ev.record(st)
+                inflight[i] = ev
                 bufs.append(v)
                 i += 1
-            while inflight and inflight[0][1].query():
-                k, _ = inflight.popleft()
-                done_at[k] = time.perf_counter() - t0
-    stream.synchronize()
-    steps_b = steps_of(bufs)
-    lat = [done_at[k] - reqs[k].t_arrival for k in range(n_req)]
-    single = summarise(lat, steps_b, max(done_at.values()) - reqs[0].t_arrival)
-    single["gpu_launches"] = n_req
-    offered = n_req / max(reqs[-1].t_arrival - reqs[0].t_arrival, 1e-9)
-    return {"rate_req_s": rate, "requests": n_req, "camera_requests": cams, "precision": precision,
-            "arrival_span_s": reqs[-1].t_arrival - reqs[0].t_arrival, "offered_req_s": offered,
-            "hbm_budget_bytes": budget, "continuous_batching": served, "one_launch_per_request": single,
-            "p50_speedup": single["p50_ms"] / served["p50_ms"], "p99_speedup": single["p99_ms"] / served["p99_ms"],
-            "throughput_ratio": served["steps_per_s"] / single["steps_per_s"]}
+            for k, ev in list(inflight.items()):
+                if ev.query():
+                    done_at[k] = time.perf_counter() - t0
+                    del inflight[k]
+        torch.cuda.synchronize()
+        steps_b = steps_of(bufs)
+        lat = [done_at[k] - t_arr[k] for k in range(n_req)]
+        single = summarise(lat, steps_b, max(done_at.values()))
+        single["gpu_launches"] = n_req
+        single["streams"] = k_streams
+        singles[k_streams] = single
+    single = singles[baseline_streams[0]]
+    span = max(t_arr[-1], 1e-9)
+    out = {"rate_req_s": rate / stretch, "requests": n_req, "camera_requests": cams, "precision": precision,
+           "arrival_span_s": span, "offered_req_s": n_req / span, "offered_steps_per_s": steps / span,
+           "hbm_budget_bytes": budget, "continuous_batching": served, "one_launch_per_request": single,
+           "p50_speedup": single["p50_ms"] / served["p50_ms"], "p99_speedup": single["p99_ms"] / served["p99_ms"],
+           "throughput_ratio": served["steps_per_s"] / single["steps_per_s"]}
+    if len(singles) > 1:
+        out["one_launch_per_request_streams"] = {str(k): v for k, v in singles.items()}
+    return out
+
+
+def run_serving_low_load(mb, torch, saturated: dict, n_req: int, precision: str, utilization: float = 0.7) -> dict:
+    """The same requests as a saturated run, arriving further apart so that
+    the offered work (their RK4 steps per second of arrivals) is `utilization`
+    of the continuous-batching throughput measured under saturation: latency
+    below capacity, against one launch per request on 1 and 4 streams."""
+    capacity = saturated["continuous_batching"]["steps_per_s"]
+    stretch = max(1.0, saturated["offered_steps_per_s"] / (utilization * capacity))
+    res = run_serving_case(mb, torch, rate=saturated["rate_req_s"], n_req=n_req, precision=precision,
+                           stretch=stretch, baseline_streams=(1, 4))
+    res["offered_utilization"] = res["offered_steps_per_s"] / capacity
+    res["capacity_steps_per_s"] = capacity
+    res["note"] = ("the requests of the saturated sample, arrival times stretched x%.2f so that the offered "
+                   "work is %.0f%% of the saturated continuous-batching throughput" % (stretch, 100 * utilization))
+    return res
+
+
+def fate_counts(mb, fate) -> dict:
+    """Rays per termination (fate & FATE_MASK) and how many of them carry the
+    validity flag (FATE_DRIFTED: the norm g(u,u) drifted by more than
+    NORM_DRIFT_TOL max(E^2, |g|); set on ESCAPED and CAPPED rays only)."""
+    base = fate & mb.FATE_MASK
+    flag = (fate & mb.FATE_DRIFTED) != 0
+    out = {}
+    for k, v in (("captured", 1), ("escaped", 2), ("capped", 3), ("nonfinite", 4)):
+        sel = base == v
+        out[k] = int(sel.sum().item())
+        if v in (2, 3):
+            out[k + "_drifted"] = int((sel & flag).sum().item())
+    out["drifted_fraction"] = float(flag.float().mean().item())
+    return out
 
 
 def err_stats(torch, dth, dph) -> dict:
     """|FP32_MIXED - FP64| of the final (theta, phi) of rays both runs call
-    ESCAPED: quantiles, maximum and the count above 1e-6 rad.  Rays that pass
-    within a step of the polar axis are ill-conditioned in both precisions
-    (fixed-step RK4 in Boyer-Lindquist coordinates), so the maximum is
-    dominated by them; the quantiles describe the rest."""
+    ESCAPED without the validity flag: quantiles, maximum and the count above
+    1e-6 rad.  The flag removes the rays whose norm a fixed step broke (passages
+    next to the polar axis, ill-conditioned in both precisions), so the
+    maximum is finite and describes rays with a trustworthy result."""
     out = {"rays": int(dth.numel())}
     if dth.numel() == 0:
         return out
@@ -968,9 +1013,10 @@ def main():
     ap.add_argument("--impl", default="malbec", choices=["malbec", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", choices=["camera_fp64", "camera_mixed", "camera_canonical", "camera_adm",
-                                               "camera_dopri5", "traj_mixed"],
+                                               "camera_dopri5", "traj_mixed", "camera_fp64_1024",
+                                               "camera_mixed_1024"],
                     default=None,
-                    help="small case for ncu: a 512x512 render of the same camera, --steps times")
+                    help="case for ncu: a 512x512 render of the same camera (1024x1024 for *_1024), --steps times")
     ap.add_argument("--workload", choices=["camera", "bundles", "serving", "bound", "paper", "integrators",
                                            "trajectory"],
                     default="camera",
@@ -1052,8 +1098,7 @@ def main():
         st = res["steps"].to(torch.float64)
         step_dist = {"mean": float(st.mean().item()), "p99": float(torch.quantile(st[::16], 0.99).item()),
                      "max": int(res["steps"].max().item()),
-                     "fates": {k: int((res["fate"] == v).sum().item()) for k, v in
-                               (("captured", 1), ("escaped", 2), ("capped", 3), ("nonfinite", 4))}}
+                     "fates": fate_counts(mb, res["fate"])}
         fate64 = res["fate"].clone()
         theta64, phi64 = res["theta"].clone(), res["phi"].clone()
         t_total = max_over_ranks(sum(times64) / 1e3)
@@ -1075,7 +1120,7 @@ def main():
             steps_c = int(res_c["steps"].to(torch.int64).sum().item())
             t_c = max_over_ranks(sum(times_c) / 1e3)
             value_c = world * steps_c * args.steps / t_c
-            agree_c = float((res_c["fate"] == fate64).float().mean().item())
+            agree_c = float(((res_c["fate"] & mb.FATE_MASK) == (fate64 & mb.FATE_MASK)).float().mean().item())
             esc_c = (fate64 == mb.FATE_ESCAPED) & (res_c["fate"] == mb.FATE_ESCAPED)
             dth_c = (res_c["theta"][esc_c] - theta64[esc_c]).abs()
             dph_c = (res_c["phi"][esc_c] - phi64[esc_c]).abs()
@@ -1102,8 +1147,10 @@ def main():
             t_cm = max_over_ranks(sum(times_cm) / 1e3)
             arm["fp32_mixed"] = {"value": world * steps_cm * args.steps / t_cm, "unit": UNIT,
                                  "ms_per_step": 1e3 * t_cm / args.steps,
-                                 "fate_agreement_vs_fp64_same_form": float((res_cm["fate"] == fate_c).float().mean()
-                                                                           .item())}
+                                 "fate_agreement_vs_fp64_same_form": float(((res_cm["fate"] & mb.FATE_MASK) ==
+                                                                            (fate_c & mb.FATE_MASK)).float().mean()
+                                                                           .item()),
+                                 "flagged": fate_counts(mb, res_cm["fate"])["drifted_fraction"]}
             return arm, fate_c, theta_c
 
         canonical, fate_bl, theta_bl = canonical_arm(
@@ -1137,7 +1184,7 @@ def main():
         for name, tt in (("rk4_h0.05r", cw.term), ("dopri5_tol1e-9", term_dp)):
             rr = mb.trace(cw.M, cw.a, ics_s, tt, precision="fp64", stream=stream)
             torch.cuda.synchronize()
-            ok = rr["fate"] != mb.FATE_NONFINITE
+            ok = (rr["fate"] & mb.FATE_MASK) != mb.FATE_NONFINITE
             dd = {}
             for c, nm in enumerate(("E", "Lz", "Q", "norm")):
                 d = (rr["inv1"][c] - rr["inv0"][c]).abs()[ok]
@@ -1150,7 +1197,9 @@ def main():
                   "rays_per_s_rk4": world * cw.n * args.steps / t_total,
                   "attempts_per_ray": att_dp / cw.n, "rk4_steps_per_ray": steps_per_render / cw.n,
                   "rhs_per_ray": {"dopri5": 6.0 * att_dp / cw.n + 1.0, "rk4": 4.0 * steps_per_render / cw.n},
-                  "fate_agreement_vs_rk4": float((res_dp["fate"] == fate64).float().mean().item()),
+                  "fate_agreement_vs_rk4": float(((res_dp["fate"] & mb.FATE_MASK) == (fate64 & mb.FATE_MASK))
+                                                 .float().mean().item()),
+                  "flagged": fate_counts(mb, res_dp["fate"])["drifted_fraction"],
                   "roofline": {"bound": "alu", "peak": peak64, "unit": "GFLOP/s (FP64)",
                                "flops_per_attempt": FLOPS_PER_STEP["kerr_dopri5"],
                                "achieved": FLOPS_PER_STEP["kerr_dopri5"] * att_dp / (statistics.mean(times_dp) / 1e3)
@@ -1185,7 +1234,8 @@ def main():
         t32 = max_over_ranks(sum(times32) / 1e3)
         value32 = world * steps32 * args.steps / t32
         f32 = res32["fate"]
-        agree = float((f32 == fate64).float().mean().item())
+        agree = float(((f32 & mb.FATE_MASK) == (fate64 & mb.FATE_MASK)).float().mean().item())
+        fates32 = fate_counts(mb, f32)
         esc = (fate64 == mb.FATE_ESCAPED) & (f32 == mb.FATE_ESCAPED)
         dth = (res32["theta"][esc] - theta64[esc]).abs()
         dph = (res32["phi"][esc] - phi64[esc]).abs()
@@ -1233,7 +1283,7 @@ def main():
         "adm_form": adm_form,
         "dopri5": dopri5,
         "fp32_mixed": {"value": value32, "unit": UNIT, "ms_per_step": 1e3 * t32 / args.steps,
-                       "speedup_vs_fp64": value32 / value, "fate_agreement_vs_fp64": agree,
+                       "speedup_vs_fp64": value32 / value, "fate_agreement_vs_fp64": agree, "fates": fates32,
                        "escaped_error_vs_fp64": err_stats(torch, dth, dph),
                        "roofline": {"bound": "alu", "peak": peak32, "unit": "GFLOP/s (FP32)",
                                     "achieved_fp32_equiv": FLOPS_PER_STEP["kerr"] * steps32 /
@@ -1247,6 +1297,8 @@ def main():
         line["bundles_sample"] = run_bundles_case(mb, torch, stream, flush, args.bundle_count or 128,
                                                   args.precision, K=2, warmup=1)
         line["serving_sample"] = run_serving_case(mb, torch, rate=200.0, n_req=32, precision=args.precision)
+        line["serving_below_saturation"] = run_serving_low_load(mb, torch, line["serving_sample"], n_req=32,
+                                                                precision=args.precision)
         line["gpu_launches_note"] = ("gpu_launches counts the timed FP64 renders; the samples report their own "
                                      "launch counts")
     if rank == 0:

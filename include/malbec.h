@@ -68,6 +68,24 @@ const char* malbec_last_cuda_error(void);
 #define MALBEC_FATE_ESCAPED 2
 #define MALBEC_FATE_CAPPED 3
 #define MALBEC_FATE_NONFINITE 4
+/* Validity flag, or-ed into the fate byte of every output (state arrays,
+ * cameras, bundles, server jobs): the ray's norm g(u,u), evaluated in FP64 at
+ * its end, departs from its value at the start by more than
+ *   MALBEC_NORM_DRIFT_TOL * max(E^2, |g(u,u)|)   (E = -p_t, both at the start).
+ * The geodesic flow keeps g(u,u) exactly constant (Sec. 2 eq. geo: 0 for
+ * null rays, -1 for timelike ones), so such a ray's end state and angles are
+ * not a solution to trust: typically a fixed step much too long for a
+ * passage next to the polar axis, where the BL right-hand side diverges (the
+ * fixed-step RK4 of the Kerr a = 0.9 camera at 80 degrees flags about 4.5% of
+ * its escaped rays; about a third of those have blown up, |dg| > E^2).
+ * Set on ESCAPED and CAPPED rays only, the ones whose end state and angles
+ * are results: a CAPTURED ray ends at the capture radius, where u^t ~ 1/Delta
+ * grows without bound in BL coordinates and its norm says nothing about the
+ * path, and a NONFINITE ray is already invalid.
+ * fate & MALBEC_FATE_MASK is the termination itself. */
+#define MALBEC_FATE_DRIFTED 0x80
+#define MALBEC_FATE_MASK 0x7f
+#define MALBEC_NORM_DRIFT_TOL 1e-3
 
 /* ---------------------------------------------------------------- parameters */
 /* Black hole.  Kerr metric in BL coordinates, Sec. 2 eq. kerr; a = 0 is
@@ -155,8 +173,13 @@ typedef struct {
 } malbec_term;
 
 typedef enum {
-  MALBEC_OUT_FINAL = 0,  /* final state, lambda, invariants, steps, fate */
-  MALBEC_OUT_STRIDED = 1 /* FINAL plus a trajectory sample every `stride` steps */
+  MALBEC_OUT_FINAL = 0,   /* final state, lambda, invariants, steps, fate */
+  MALBEC_OUT_STRIDED = 1, /* FINAL plus a trajectory sample every `stride` steps */
+  MALBEC_OUT_STRIDED_CARTESIAN = 2 /* FINAL plus a sample (t, x, y, z) every `stride` steps:
+                                      the paper's output records (Sec. 5), with
+                                      x = sqrt(r^2 + a^2) sin th cos ph,
+                                      y = sqrt(r^2 + a^2) sin th sin ph, z = r cos th
+                                      (Sec. 2 eq. coord) */
 } malbec_out_mode;
 
 typedef enum {
@@ -219,7 +242,14 @@ int malbec_get_mixed_zone(malbec_mixed_zone* zone);
  *                      back (zone steps run with fuller warps), 2 = every
  *                      ray stays in its warp (automatic: 2 for whole-image
  *                      cameras, whose rays spend few steps in the zone, 1
- *                      otherwise).
+ *                      otherwise);
+ *   zone_wait_limit_us with the exchange, the longest a block's zone warp,
+ *                      once it has no ray left, waits for the other warps of
+ *                      its block before it closes its bank and leaves (the
+ *                      others then take their FP64-zone steps in place);
+ *                      measured on the device clock from the moment the zone
+ *                      warp ran out of work (automatic: 2 s).  A wait that
+ *                      runs out is counted: see malbec_wait_status.
  * The choice changes speed only: every ray's arithmetic is the same.
  * NULL restores all-automatic.  Thread-safe. */
 typedef struct {
@@ -229,6 +259,7 @@ typedef struct {
   uint32_t zone_batch;
   uint32_t zone_wait;
   uint32_t exchange;
+  uint32_t zone_wait_limit_us;
 } malbec_launch_config;
 
 int malbec_set_launch_config(const malbec_launch_config* cfg);
@@ -242,12 +273,15 @@ int malbec_get_launch_config(malbec_launch_config* cfg);
  *   inv0    double[4][n]     E = -p_t, L_z = p_phi, Carter Q, norm g(u,u) at the start
  *   inv1    double[4][n]     the same at the end (always FP64)
  *   steps   uint32[n]        RK4 steps taken
- *   fate    uint8[n]         MALBEC_FATE_*
- *   traj    STRIDED only: per ray `n_samples` samples of 8 components,
- *           ray-major: traj[(i * n_samples + k) * 8 + c]; double for FP64,
- *           float (the hi word) for FP32_MIXED.  Sample k is the state after
- *           k * stride steps (sample 0 = initial state); samples after the
- *           ray terminated are NaN.  n_samples = n_steps_cap / stride + 1. */
+ *   fate    uint8[n]         MALBEC_FATE_*, with MALBEC_FATE_DRIFTED or-ed in when set
+ *   traj    STRIDED modes only: per ray `n_samples` samples of C components
+ *           (C = 8, the state, for MALBEC_OUT_STRIDED; C = 4, (t, x, y, z),
+ *           for MALBEC_OUT_STRIDED_CARTESIAN), ray-major:
+ *           traj[(i * n_samples + k) * C + c]; double for FP64, float for
+ *           FP32_MIXED (the hi word of the state, or (t, x, y, z) from it).
+ *           Sample k is taken after k * stride steps (sample 0 = initial
+ *           state); samples after the ray terminated are NaN.
+ *           n_samples = n_steps_cap / stride + 1. */
 typedef struct {
   size_t y, lambda, inv0, inv1, steps, fate, traj;
   uint64_t n_samples;
@@ -526,6 +560,17 @@ int malbec_measure_step_loop(uint32_t form, double* steps_per_s);
  * relative error of the hardware reciprocal estimate before refinement.
  * Blocks the calling thread. */
 int malbec_check_fp64_helpers(double err[4]);
+
+/* Bounded device-side waits (not in the paper).  The one wait a trace
+ * kernel makes on other warps is the zone warp's wait for the rest of its
+ * block (launch configuration, zone_wait_limit_us); when it runs out the
+ * zone warp leaves, the other warps take their FP64-zone steps in place, and
+ * results are unchanged.  Every expiry on the current device increments a
+ * device-wide counter.  This call waits for the current device's work
+ * (cudaDeviceSynchronize), writes the counter's total to *timeouts (if not
+ * NULL), and returns MALBEC_ETIMEDOUT if the total grew since the previous
+ * call in this process, MALBEC_OK otherwise. */
+int malbec_wait_status(uint64_t* timeouts);
 
 /* Library build information (static string). */
 const char* malbec_build_info(void);

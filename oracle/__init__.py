@@ -24,6 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 FATE_CAPTURED, FATE_ESCAPED, FATE_CAPPED, FATE_NONFINITE = 1, 2, 3, 4
+FATE_DRIFTED, FATE_MASK, NORM_DRIFT_TOL = 0x80, 0x7F, 1e-3  # validity flag or-ed into a fate
 
 _D = ctypes.c_double
 _PD = ctypes.POINTER(ctypes.c_double)
@@ -44,6 +45,7 @@ class Term(ctypes.Structure):
         ("method", _U32),
         ("rtol", _D),
         ("atol", _D),
+        ("rhs_noise", _D),
     ]
 
 
@@ -137,12 +139,14 @@ def _vp(a):
 
 
 def make_term(eps_hor=0.01, r_esc=1e30, n_steps_cap=1000, dl=0.01, dl_r_scale=0.0, form=0, method=0, rtol=0.0,
-              atol=0.0) -> Term:
+              atol=0.0, rhs_noise=0.0) -> Term:
     """form 0: geodesic equation (eq. geo); 1: canonical equations (eq. Ham)
     with g of eq. kerr; 2: the same equations with g from eq. ADM.  method 0:
-    classical RK4; 1: Dormand-Prince 5(4) with step-size control (rtol, atol)."""
+    classical RK4; 1: Dormand-Prince 5(4) with step-size control (rtol, atol).
+    rhs_noise (tests only): relative +- perturbation of every right-hand-side
+    component, to measure a ray's sensitivity to rounding."""
     return Term(float(eps_hor), float(r_esc), int(n_steps_cap), float(dl), float(dl_r_scale), int(form),
-                int(method), float(rtol), float(atol))
+                int(method), float(rtol), float(atol), float(rhs_noise))
 
 
 # ---------------------------------------------------------------- geometry

@@ -563,6 +563,27 @@ static void canonical_to_state(double M, double a, int form, const double z[8], 
   }
 }
 
+/* The rhs_noise option: wrap a right-hand side so that every component of
+ * every evaluation is scaled by 1 +- noise (sign from SplitMix64 seeded with
+ * the bits of `noise`, on the evaluation counter and the component index). */
+typedef struct {
+  orc_rhs_fn fn;
+  const void* ctx;
+  double noise;
+  uint64_t count;
+} noisy_rhs;
+static void noisy_fn(const void* c, const double* y, double* f) {
+  noisy_rhs* n = (noisy_rhs*)c;
+  n->fn(n->ctx, y, f);
+  uint64_t seed;
+  memcpy(&seed, &n->noise, sizeof(seed)); /* another noise value, another sign pattern */
+  for (int i = 0; i < 8; ++i) {
+    uint64_t b = orc_splitmix64(seed, n->count * 8u + (uint64_t)i);
+    f[i] *= 1.0 + ((b >> 63) ? n->noise : -n->noise);
+  }
+  n->count++;
+}
+
 int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, double y[8],
                   double* lambda, uint32_t* steps, double* traj, uint32_t stride) {
   double r_cap = (1.0 + t->eps_hor) * orc_r_plus(M, a);
@@ -590,6 +611,12 @@ int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, dou
   }
   if (ns) memcpy(traj, y, 8 * sizeof(double));
   orc_bh bh = {M, a};
+  const void* rctx = &bh;
+  noisy_rhs noisy = {rhs, &bh, t->rhs_noise, 0u};
+  if (t->rhs_noise != 0.0) {
+    rhs = noisy_fn;
+    rctx = &noisy;
+  }
   if (t->method == 1) {
     /* Dormand-Prince 5(4) with step-size control; n counts attempts; the
      * termination tests follow every attempt (capture and non-finite on the
@@ -597,11 +624,11 @@ int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, dou
     double h = t->dl > 0.0 ? t->dl : t->dl_r_scale * z[1];
     double k1[8], y5[8], e[8], k7[8];
     int after_reject = 0;
-    rhs(&bh, z, k1);
+    rhs(rctx, z, k1);
     while (n < t->n_steps_cap) {
       if (t->dl_r_scale > 0.0 && h > t->dl_r_scale * z[1]) h = t->dl_r_scale * z[1];
       double r_stage_min;
-      dopri5_attempt(rhs, &bh, 8, h, z, k1, y5, e, k7, 1, &r_stage_min);
+      dopri5_attempt(rhs, rctx, 8, h, z, k1, y5, e, k7, 1, &r_stage_min);
       ++n;
       int done = 0;
       if (y5[1] <= r_cap || r_stage_min <= r_cap) {
@@ -644,7 +671,7 @@ int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, dou
   while (t->method != 1 && n < t->n_steps_cap) {
     double h = (t->dl_r_scale > 0.0) ? t->dl_r_scale * z[1] : t->dl;
     double r_stage_min;
-    rk4_generic(rhs, &bh, 8, h, z, 1, &r_stage_min);
+    rk4_generic(rhs, rctx, 8, h, z, 1, &r_stage_min);
     lam += h;
     ++n;
     if (ns && n % stride == 0) {
@@ -665,6 +692,14 @@ int orc_trace_one(double M, double a, const double y0[8], const orc_term* t, dou
   if (ns)
     for (uint32_t k = n / stride + 1; k < ns; ++k)
       for (int c = 0; c < 8; ++c) traj[(size_t)k * 8 + c] = NAN;
+  /* validity: the norm g(u,u) is a constant of the flow */
+  if (fate == ORC_FATE_ESCAPED || fate == ORC_FATE_CAPPED) {
+    double i0[4], i1[4];
+    orc_invariants(M, a, y0, i0);
+    orc_invariants(M, a, y, i1);
+    double lim = ORC_NORM_DRIFT_TOL * fmax(i0[0] * i0[0], fabs(i0[3]));
+    if (fabs(i1[3] - i0[3]) > lim) fate |= ORC_FATE_DRIFTED;
+  }
   *lambda = lam;
   *steps = n;
   return fate;

@@ -32,6 +32,14 @@ extern "C" {
 #define ORC_FATE_ESCAPED 2
 #define ORC_FATE_CAPPED 3
 #define ORC_FATE_NONFINITE 4
+/* validity flag or-ed into the fate of an ESCAPED or CAPPED ray: the norm
+ * g(u,u) at the end departs from its value at the start by more than
+ * ORC_NORM_DRIFT_TOL max(E^2, |g(u,u)|) (E and g(u,u) of the start state); the
+ * flow keeps g(u,u) constant (Sec. 2, eq. geo), so such an end state is not a
+ * solution to trust.  A CAPTURED ray ends at the capture radius, where the BL
+ * norm is dominated by u^t ~ 1/Delta, and is never flagged. */
+#define ORC_FATE_DRIFTED 0x80
+#define ORC_NORM_DRIFT_TOL 1e-3
 
 typedef struct {
   double eps_hor;      /* captured when r <= (1+eps_hor) r_+ */
@@ -52,6 +60,12 @@ typedef struct {
                              factor 0.9 err^(-1/5) taken down to the grid 2^(j/4);
                              n_steps_cap and the step count then count attempts */
   double rtol, atol;   /* tolerances of method 1 (atol > 0) */
+  double rhs_noise;    /* test-only (0 = off): every right-hand-side component is
+                          multiplied by 1 +- rhs_noise, the sign drawn from
+                          SplitMix64 (seeded with the bits of rhs_noise) on a
+                          per-ray counter of evaluations -- a
+                          rounding-sized perturbation that measures how much a
+                          ray's result depends on the rounding of its steps */
 } orc_term;
 
 /* -------- geometry (Sec. 2, eq. kerr) -------- */

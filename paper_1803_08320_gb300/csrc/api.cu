@@ -80,7 +80,7 @@ int device_sms(int* sms) {
 
 namespace {
 std::mutex g_launch_mu;
-malbec_launch_config g_launch = {0, 0, 0, 0, 0, 0};
+malbec_launch_config g_launch = {0, 0, 0, 0, 0, 0, 0};
 
 malbec_launch_config launch_config() {
   std::lock_guard<std::mutex> lk(g_launch_mu);
@@ -182,6 +182,7 @@ void fill_zone(TraceParams& p) {
   p.zone_batch = cfg.zone_batch ? (int)cfg.zone_batch : -1;  // -1: the launcher decides
   p.zone_wait = cfg.zone_wait ? (int)cfg.zone_wait : 64;
   p.exchange = cfg.exchange ? (cfg.exchange == 1 ? 1 : 0) : -1;  // -1: the launcher decides
+  p.zone_wait_ns = (uint64_t)(cfg.zone_wait_limit_us ? cfg.zone_wait_limit_us : 2000000u) * 1000ull;
 }
 
 int set_cuda_error(cudaError_t e) {
@@ -250,7 +251,7 @@ int malbec_set_mixed_zone(const malbec_mixed_zone* z) {
 }
 
 int malbec_set_launch_config(const malbec_launch_config* cfg) {
-  malbec_launch_config v = {0, 0, 0, 0, 0, 0};
+  malbec_launch_config v = {0, 0, 0, 0, 0, 0, 0};
   if (cfg) {
     if (cfg->threads_per_block && (cfg->threads_per_block % 32 != 0 || cfg->threads_per_block > 256))
       return MALBEC_EINVAL;
@@ -280,9 +281,11 @@ int malbec_get_mixed_zone(malbec_mixed_zone* z) {
 int malbec_out_layout(malbec_out_mode mode, malbec_precision prec, uint64_t n, uint32_t n_steps_cap,
                       uint32_t stride, malbec_layout* L) {
   if (!L || n == 0) return MALBEC_EINVAL;
-  if (mode != MALBEC_OUT_FINAL && mode != MALBEC_OUT_STRIDED) return MALBEC_EINVAL;
+  if (mode != MALBEC_OUT_FINAL && mode != MALBEC_OUT_STRIDED && mode != MALBEC_OUT_STRIDED_CARTESIAN)
+    return MALBEC_EINVAL;
   if (prec != MALBEC_FP64 && prec != MALBEC_FP32_MIXED) return MALBEC_EINVAL;
-  if (mode == MALBEC_OUT_STRIDED && stride == 0) return MALBEC_EINVAL;
+  const bool strided = mode != MALBEC_OUT_FINAL;
+  if (strided && stride == 0) return MALBEC_EINVAL;
   if (n > (1ull << 40)) return MALBEC_EINVAL;
   size_t off = 0;
   L->y = off;
@@ -299,14 +302,15 @@ int malbec_out_layout(malbec_out_mode mode, malbec_precision prec, uint64_t n, u
   off = align256(off + n);
   L->traj = 0;
   L->n_samples = 0;
-  if (mode == MALBEC_OUT_STRIDED) {
+  if (strided) {
     const uint64_t ns = (uint64_t)(n_steps_cap / stride) + 1;
     const size_t elem = prec == MALBEC_FP64 ? sizeof(double) : sizeof(float);
-    const long double bytes = (long double)n * ns * 8 * elem;
+    const size_t comps = mode == MALBEC_OUT_STRIDED_CARTESIAN ? 4 : 8;
+    const long double bytes = (long double)n * ns * comps * elem;
     if (bytes > 2.0e14L) return MALBEC_EINVAL;  // beyond any device memory
     L->traj = off;
     L->n_samples = ns;
-    off = align256(off + (size_t)(n * ns * 8 * elem));
+    off = align256(off + (size_t)(n * ns * comps * elem));
   }
   L->total = off;
   return MALBEC_OK;
@@ -355,12 +359,14 @@ int malbec_trace(malbec_metric m, const double* ics, uint64_t n, malbec_term t, 
   p.inv1_out = reinterpret_cast<double*>(o + L.inv1);
   p.steps_out = reinterpret_cast<uint32_t*>(o + L.steps);
   p.fate_out = reinterpret_cast<uint8_t*>(o + L.fate);
-  p.traj = mode == MALBEC_OUT_STRIDED ? static_cast<void*>(o + L.traj) : nullptr;
-  p.stride = mode == MALBEC_OUT_STRIDED ? stride : 1;
+  const bool strided = mode != MALBEC_OUT_FINAL;
+  p.traj = strided ? static_cast<void*>(o + L.traj) : nullptr;
+  p.stride = strided ? stride : 1;
   p.n_samples = L.n_samples;
+  p.traj_cartesian = mode == MALBEC_OUT_STRIDED_CARTESIAN ? 1 : 0;
   const bool kerr = !(m.a == 0.0 && m.a_per_ray == nullptr);
-  return run_trace(p, kerr, prec == MALBEC_FP32_MIXED, kSrcStates,
-                   mode == MALBEC_OUT_STRIDED ? kSinkStrided : kSinkFinal, (cudaStream_t)stream);
+  return run_trace(p, kerr, prec == MALBEC_FP32_MIXED, kSrcStates, strided ? kSinkStrided : kSinkFinal,
+                   (cudaStream_t)stream);
 }
 
 int malbec_camera_out_layout(const malbec_camera* cam, malbec_camera_layout* L) {
@@ -482,6 +488,25 @@ int malbec_ic_from_paper(malbec_metric m, const double* rows, uint64_t n, double
   if (!rows || !ics || n == 0 || rows == ics) return MALBEC_EINVAL;
   cudaError_t e = launch_ic_from_paper(m.M, m.a, m.a_per_ray, rows, n, ics, (cudaStream_t)stream);
   return e == cudaSuccess ? MALBEC_OK : set_cuda_error(e);
+}
+
+int malbec_wait_status(uint64_t* timeouts) {
+  static std::mutex mu;
+  static unsigned long long seen[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (dev < 0 || dev >= 64) return MALBEC_EINVAL;
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_cuda_error(e);
+  unsigned long long total = 0;
+  e = read_wait_timeouts(&total);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (timeouts) *timeouts = total;
+  std::lock_guard<std::mutex> lk(mu);
+  const bool grew = total > seen[dev];
+  seen[dev] = total;
+  return grew ? MALBEC_ETIMEDOUT : MALBEC_OK;
 }
 
 const char* malbec_build_info(void) {

@@ -202,7 +202,7 @@ struct malbec_plan {
   bool mixed = false;
   void* block = nullptr;
   BlockLayout bl;
-  malbec_launch_config cfg = {0, 0, 0, 0, 0, 0};
+  malbec_launch_config cfg = {0, 0, 0, 0, 0, 0, 0};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -222,6 +222,7 @@ int record_plan(malbec_plan* P, const malbec_launch_config& cfg) {
   if (cfg.zone_batch) p.zone_batch = (int)cfg.zone_batch;
   if (cfg.zone_wait) p.zone_wait = (int)cfg.zone_wait;
   if (cfg.exchange) p.exchange = cfg.exchange == 1 ? 1 : 0;
+  if (cfg.zone_wait_limit_us) p.zone_wait_ns = (uint64_t)cfg.zone_wait_limit_us * 1000ull;
   cudaStream_t s = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (e != cudaSuccess) return set_cuda_error(e);

@@ -67,6 +67,7 @@ struct TraceParams {
   void* traj;
   uint32_t stride;
   uint64_t n_samples;
+  int traj_cartesian;  // samples are (t, x, y, z) of eq. coord instead of the state
   // outputs (kSinkCamera)
   double* theta_out;
   double* phi_out;
@@ -74,6 +75,7 @@ struct TraceParams {
   double zone_horizon, zone_photon, zone_pole;
   int zone_batch, zone_wait;
   int exchange;       // FP32_MIXED: block ray exchange on (1) / off (0)
+  uint64_t zone_wait_ns;  // the zone warp's longest wait for its block (device clock)
   uint32_t form;      // MALBEC_FORM_*
   uint32_t method;    // MALBEC_METHOD_*
   double rtol, atol;  // MALBEC_METHOD_DOPRI5 tolerances
@@ -112,6 +114,8 @@ struct LaunchShape {
 cudaError_t launch_trace(const TraceParams& p, bool kerr, bool mixed, Source src, Sink sink,
                          const LaunchShape& shape, cudaStream_t stream);
 int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, int threads_per_block);
+// total of the device-wide counter of zone-warp waits that ran out (current device)
+cudaError_t read_wait_timeouts(unsigned long long* total);
 
 // ic.cu
 cudaError_t launch_ic_circular(double M, double a, const double* radii, uint64_t n, int prograde,

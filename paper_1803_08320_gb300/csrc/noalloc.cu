@@ -147,12 +147,14 @@ extern "C" int malbec_trace_noalloc(malbec_metric m, const double* ics, uint64_t
   p.inv1_out = reinterpret_cast<double*>(o + L.inv1);
   p.steps_out = reinterpret_cast<uint32_t*>(o + L.steps);
   p.fate_out = reinterpret_cast<uint8_t*>(o + L.fate);
-  p.traj = mode == MALBEC_OUT_STRIDED ? static_cast<void*>(o + L.traj) : nullptr;
-  p.stride = mode == MALBEC_OUT_STRIDED ? stride : 1;
+  const bool strided = mode != MALBEC_OUT_FINAL;
+  p.traj = strided ? static_cast<void*>(o + L.traj) : nullptr;
+  p.stride = strided ? stride : 1;
   p.n_samples = L.n_samples;
+  p.traj_cartesian = mode == MALBEC_OUT_STRIDED_CARTESIAN ? 1 : 0;
   const bool kerr = !(m.a == 0.0 && m.a_per_ray == nullptr);
   const bool mixed = prec == MALBEC_FP32_MIXED;
-  const Sink sink = mode == MALBEC_OUT_STRIDED ? kSinkStrided : kSinkFinal;
+  const Sink sink = strided ? kSinkStrided : kSinkFinal;
   LaunchShape shape;
   int refill_min = 1;
   rc = choose_shape(kerr, mixed, kSrcStates, sink, n, &shape, &refill_min);

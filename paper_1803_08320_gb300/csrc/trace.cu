@@ -70,9 +70,33 @@ __device__ __forceinline__ bool finite8f(const float y[8]) {
   return !bad;
 }
 
+// Trajectory sample k of ray id: the state (8 components), or with
+// p.traj_cartesian the paper's output record (t, x, y, z) of eq. coord,
+// x = sqrt(r^2 + a^2) sin th cos ph, y = sqrt(r^2 + a^2) sin th sin ph,
+// z = r cos th.  FP32_MIXED samples come from the hi words, in FP32.
 template <bool kMixed>
-__device__ __forceinline__ void store_sample(const TraceParams& p, uint64_t id, uint64_t k, const double y[8],
-                                             const float hi[8]) {
+__device__ __forceinline__ void store_sample(const TraceParams& p, double a, uint64_t id, uint64_t k,
+                                             const double y[8], const float hi[8]) {
+  if (p.traj_cartesian) {
+    const size_t off = ((size_t)id * p.n_samples + k) * 4;
+    if (kMixed) {
+      float st, ct, sp, cp;
+      sincosf(hi[2], &st, &ct);
+      sincosf(hi[3], &sp, &cp);
+      const float R = sqrtf(fmaf(hi[1], hi[1], (float)(a * a)));
+      *reinterpret_cast<float4*>(static_cast<float*>(p.traj) + off) =
+          make_float4(hi[0], R * st * cp, R * st * sp, hi[1] * ct);
+    } else {
+      double st, ct, sp, cp;
+      sincos(y[2], &st, &ct);
+      sincos(y[3], &sp, &cp);
+      const double R = sqrt(fma(y[1], y[1], a * a));
+      double2* t = reinterpret_cast<double2*>(static_cast<double*>(p.traj) + off);
+      t[0] = make_double2(y[0], R * st * cp);
+      t[1] = make_double2(R * st * sp, y[1] * ct);
+    }
+    return;
+  }
   const size_t off = ((size_t)id * p.n_samples + k) * 8;
   if (kMixed) {
     float4* t = reinterpret_cast<float4*>(static_cast<float*>(p.traj) + off);
@@ -87,18 +111,17 @@ __device__ __forceinline__ void store_sample(const TraceParams& p, uint64_t id, 
 
 template <bool kMixed>
 __device__ __forceinline__ void store_nan_samples(const TraceParams& p, uint64_t id, uint64_t k0) {
+  const int comps = p.traj_cartesian ? 4 : 8;
   for (uint64_t k = k0; k < p.n_samples; ++k) {
-    const size_t off = ((size_t)id * p.n_samples + k) * 8;
+    const size_t off = ((size_t)id * p.n_samples + k) * comps;
     if (kMixed) {
       const float fn = __int_as_float(0x7fc00000);
       float4* t = reinterpret_cast<float4*>(static_cast<float*>(p.traj) + off);
-      t[0] = make_float4(fn, fn, fn, fn);
-      t[1] = make_float4(fn, fn, fn, fn);
+      for (int c = 0; c < comps / 4; ++c) t[c] = make_float4(fn, fn, fn, fn);
     } else {
       const double qn = __longlong_as_double(0x7ff8000000000000ll);
       double2* t = reinterpret_cast<double2*>(static_cast<double*>(p.traj) + off);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) t[c] = make_double2(qn, qn);
+      for (int c = 0; c < comps / 2; ++c) t[c] = make_double2(qn, qn);
     }
   }
 }
@@ -256,6 +279,7 @@ struct RayBank {
   uint32_t job[kBankSlots], nst[kBankSlots], cap[kBankSlots];
   float r_zone[kBankSlots], pole[kBankSlots], lam_h[kBankSlots], lam_l[kBankSlots];
   uint32_t lam_fix[kBankSlots];
+  double n0[kBankSlots], drift_lim[kBankSlots];
 };
 
 struct BlockBanks {
@@ -332,10 +356,11 @@ __device__ __forceinline__ unsigned nsmid() {
   return n;
 }
 
-// Longest wait of a zone warp for the other warps of its block: after it the
-// zone warp closes its bank and leaves (the others then run their zone steps
-// in place).
-constexpr unsigned long long kZoneWarpWaitNs = 600ull * 1000000000ull;
+// Zone-warp waits that ran out (TraceParams::zone_wait_ns), device-wide: a
+// zone warp that has been without work for that long while other warps of
+// its block still run closes its bank and leaves (the others then take their
+// zone steps in place, with the same arithmetic) and counts itself here.
+__device__ unsigned long long g_wait_timeouts;
 
 static_assert(kHamKerrBL == MALBEC_FORM_HAMILTONIAN && kHamAdm == MALBEC_FORM_ADM, "form codes");
 
@@ -406,10 +431,18 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
   uint32_t nst = 0;
   uint64_t id = 0;
   double a = p.a, r_cap = 0.0;
+  // validity flag: the norm g(u,u) at the start and the largest departure
+  // from it that the end state may show (MALBEC_FATE_DRIFTED)
+  double n0 = 0.0, drift_lim = 0.0;
   float r_cap_f = 0.f, r_zone_f = 0.f, pole_lane = -1.f;
   BH<double> bh64 = make_bh<double>(M, p.a);
   BH<float> bh32 = make_bh<float>(M, p.a);
   int zone_waited = 0;
+  // fate of a ended ray whose end-of-ray work is deferred (0: none); the
+  // request loop finishes every ray at once (completion latency), the other
+  // sources once refill_min lanes wait (they are refilled together anyway)
+  int pending = 0;
+  const int flush_min = kSrc == kSrcServe ? 1 : p.refill_min;
   unsigned long long idle_since = 0ull, nap_since = 0ull;
   int claim_backoff = 0;
   bool active = false, drained = false, parked = false;
@@ -475,6 +508,8 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
     b.lam_h[s] = lam_h;
     b.lam_l[s] = lam_l;
     b.lam_fix[s] = lam_fix;
+    b.n0[s] = n0;
+    b.drift_lim[s] = drift_lim;
     active = false;
   };
   auto load_ray = [&](const RayBank& b, int s) {
@@ -504,6 +539,8 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
     lam_h = b.lam_h[s];
     lam_l = b.lam_l[s];
     lam_fix = b.lam_fix[s];
+    n0 = b.n0[s];
+    drift_lim = b.drift_lim[s];
     active = true;
   };
   auto zone_test = [&]() -> bool {
@@ -511,8 +548,9 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
   };
   // A warp with no ray left asks to leave (banks in use).  The zone warp
   // leaves once its bank is empty and every other warp of the block has left
-  // (it naps meanwhile, at most kZoneWarpWaitNs, then closes its bank); the
-  // others leave once the FP32 bank is empty.  Returns false to loop again.
+  // (it naps meanwhile, at most p.zone_wait_ns, then closes its bank and
+  // counts the expiry); the others leave once the FP32 bank is empty.
+  // Returns false to loop again.
   auto leave_block_banks = [&](auto& bk) -> bool {
     if (!warp_lock(&bk.lock, lane)) return false;
     int leave = 0;
@@ -522,7 +560,8 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
         if (nz == 0) {
           const unsigned long long now = global_ns();
           if (nap_since == 0ull) nap_since = now;
-          if (alive == 0 || now - nap_since > kZoneWarpWaitNs) {
+          if (alive == 0 || now - nap_since > p.zone_wait_ns) {
+            if (alive != 0) atomicAdd(&g_wait_timeouts, 1ull);
             shared_store(&bk.open, 0);
             leave = 1;
           }
@@ -538,8 +577,84 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
     return leave != 0;
   };
 
+  // End of a ray (its fate in `pending`): back to FP64 (x, u), the end
+  // invariants and the validity flag, the outputs, the job's completion.
+  auto finish_ray = [&]() {
+    int fate = pending;
+    if (kMixed) {
+      flush_lam();
+#pragma unroll
+      for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
+    }
+    if constexpr (kHam) {
+      // back to (x, u) for the outputs and the invariants
+      double u[4];
+      to_velocity<kForm>(M, a, y, u);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) y[4 + c] = u[c];
+    }
+    // the end invariants (FP64) and the validity flag
+    double inv1[4];
+    invariants64(M, a, y, inv1);
+    if ((fate == MALBEC_FATE_ESCAPED || fate == MALBEC_FATE_CAPPED) && fabs(inv1[3] - n0) > drift_lim)
+      fate |= MALBEC_FATE_DRIFTED;
+    if (kSink == kSinkJobs) {
+      const JobDesc J = load_job(&p.jobs[job]);
+      if (J.kind == MALBEC_BUNDLE_CAMERA) {
+        J.fate_out[id] = (uint8_t)fate;
+        J.steps_out[id] = nst;
+        J.theta_out[id] = y[2];
+        J.phi_out[id] = y[3];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) J.y_out[(size_t)c * J.n + id] = y[c];
+        J.lambda_out[id] = lam;
+        J.steps_out[id] = nst;
+        J.fate_out[id] = (uint8_t)fate;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) J.inv1_out[(size_t)c * J.n + id] = inv1[c];
+      }
+      // this ray's outputs are visible device-wide before it is counted
+      __threadfence();
+      const unsigned long long finished = atomicAdd(&p.job_ctr[job].done, 1ull) + 1ull;
+      if (kSrc == kSrcServe && finished == J.n) {
+        // last ray of the job: every output is visible, tell the host
+        __threadfence_system();
+        p.done_flags[job] = J.job_id;
+      }
+    } else if (kSink == kSinkCamera) {
+      p.fate_out[id] = (uint8_t)fate;
+      p.steps_out[id] = nst;
+      p.theta_out[id] = y[2];
+      p.phi_out[id] = y[3];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) p.y_out[(size_t)c * p.n + id] = y[c];
+      p.lambda_out[id] = lam;
+      p.steps_out[id] = nst;
+      p.fate_out[id] = (uint8_t)fate;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) p.inv1_out[(size_t)c * p.n + id] = inv1[c];
+      if (kSink == kSinkStrided) store_nan_samples<kMixed>(p, id, (uint64_t)nst / p.stride + 1);
+    }
+    pending = 0;
+  };
+
   while (true) {
-    unsigned act = __ballot_sync(kFull, active);
+    // ---- deferred sinks: the end-of-ray work of lanes whose rays ended (FP64
+    // invariants and flag, output writes) runs once `flush_min` of them wait
+    // or no ray of the warp is still running, so that this FP64 work runs on
+    // many lanes at once instead of one lane at a time with its warp waiting
+    // (an FP64 warp instruction costs the same with 1 active lane as with 32)
+    {
+      const unsigned pend = __ballot_sync(kFull, pending != 0);
+      if (pend != 0u) {
+        const unsigned run = __ballot_sync(kFull, active);
+        if ((__popc(pend) >= flush_min || run == 0u) && pending != 0) finish_ray();
+      }
+    }
+    // lanes that are busy: running a ray or holding one whose end is deferred
+    unsigned act = __ballot_sync(kFull, active || pending != 0);
     if constexpr (kBanks) {
       if (use_banks) {
         if (zone_warp) {
@@ -575,7 +690,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
               shared_store(&banks.n_fp32, nf);
             }
             warp_unlock(&banks.lock, lane);
-            act = __ballot_sync(kFull, active);
+            act = __ballot_sync(kFull, active || pending != 0);
           }
         } else if (act != kFull && warp_peek(&banks.n_fp32, lane) > 0 && warp_lock(&banks.lock, lane)) {
           // ---- other warps: rays the zone warp handed back go first
@@ -588,7 +703,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
           if (((free_lanes >> lane) & 1u) && (int)frank < take) load_ray(banks.fp32, nf - 1 - (int)frank);
           if (lane == 0) shared_store(&banks.n_fp32, nf - take);
           warp_unlock(&banks.lock, lane);
-          act = __ballot_sync(kFull, active);
+          act = __ballot_sync(kFull, active || pending != 0);
         }
       }
     }
@@ -603,7 +718,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
         base = __shfl_sync(kFull, base, 0);
         if (base + (unsigned long long)idle >= p.n) drained = true;
         const unsigned long long my = base + __popc(~act & lt_mask);
-        if (!active && my < p.n) {
+        if (!((act >> lane) & 1u) && my < p.n) {
           id = kSrc == kSrcCamera ? camera_claim_pixel(p.cam, my) : my;
           got = true;
         }
@@ -787,9 +902,11 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
         const JobDesc* Jp = from_jobs ? &p.jobs[job] : nullptr;
         const bool camera_ray = kSink == kSinkCamera ||
                                 (from_jobs && __ldcg(reinterpret_cast<const int*>(&Jp->kind)) == MALBEC_BUNDLE_CAMERA);
-        if (kMixed || !camera_ray) {
+        {
           double inv[4];
           invariants64(M, a, y, inv);
+          n0 = inv[3];
+          drift_lim = MALBEC_NORM_DRIFT_TOL * fmax(inv[0] * inv[0], fabs(inv[3]));
           if (!camera_ray) {
             double* inv0 = from_jobs ? reinterpret_cast<double*>(__ldcg(reinterpret_cast<const unsigned long long*>(&Jp->inv0_out)))
                                      : p.inv0_out;
@@ -809,7 +926,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
             split_pair(y, hi, lo);
           }
         }
-        if (kSink == kSinkStrided) store_sample<kMixed>(p, id, 0, y, hi);
+        if (kSink == kSinkStrided) store_sample<kMixed>(p, a, id, 0, y, hi);
         if constexpr (kHam) {
           // canonical form: integrate (x, p) with p = g u
           double pz[4];
@@ -984,7 +1101,8 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
       }
       ++nst;
       if (kSink == kSinkStrided && (nst % p.stride) == 0) {
-        if constexpr (kHam) {
+        if (kHam && !p.traj_cartesian) {
+          // canonical forms: the sample is (x, u), u = g^{-1} p
           double yz[8], yu[8];
           float hu[8];
 #pragma unroll
@@ -994,9 +1112,9 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
           to_velocity<kForm>(M, a, yz, yu + 4);
 #pragma unroll
           for (int c = 0; c < 8; ++c) hu[c] = (float)yu[c];
-          store_sample<kMixed>(p, id, nst / p.stride, yu, hu);
+          store_sample<kMixed>(p, a, id, nst / p.stride, yu, hu);
         } else {
-          store_sample<kMixed>(p, id, nst / p.stride, y, hi);
+          store_sample<kMixed>(p, a, id, nst / p.stride, y, hi);
         }
       }
       // ---- termination tests, in the documented order
@@ -1013,61 +1131,9 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
     }
 
     if (fate != 0) {
-      if (kMixed) {
-        flush_lam();
-#pragma unroll
-        for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
-      }
-      if constexpr (kHam) {
-        // back to (x, u) for the outputs and the invariants
-        double u[4];
-        to_velocity<kForm>(M, a, y, u);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) y[4 + c] = u[c];
-      }
-      if (kSink == kSinkJobs) {
-        const JobDesc J = load_job(&p.jobs[job]);
-        if (J.kind == MALBEC_BUNDLE_CAMERA) {
-          J.fate_out[id] = (uint8_t)fate;
-          J.steps_out[id] = nst;
-          J.theta_out[id] = y[2];
-          J.phi_out[id] = y[3];
-        } else {
-#pragma unroll
-          for (int c = 0; c < 8; ++c) J.y_out[(size_t)c * J.n + id] = y[c];
-          J.lambda_out[id] = lam;
-          J.steps_out[id] = nst;
-          J.fate_out[id] = (uint8_t)fate;
-          double inv[4];
-          invariants64(M, a, y, inv);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) J.inv1_out[(size_t)c * J.n + id] = inv[c];
-        }
-        // this ray's outputs are visible device-wide before it is counted
-        __threadfence();
-        const unsigned long long finished = atomicAdd(&p.job_ctr[job].done, 1ull) + 1ull;
-        if (kSrc == kSrcServe && finished == J.n) {
-          // last ray of the job: every output is visible, tell the host
-          __threadfence_system();
-          p.done_flags[job] = J.job_id;
-        }
-      } else if (kSink == kSinkCamera) {
-        p.fate_out[id] = (uint8_t)fate;
-        p.steps_out[id] = nst;
-        p.theta_out[id] = y[2];
-        p.phi_out[id] = y[3];
-      } else {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) p.y_out[(size_t)c * p.n + id] = y[c];
-        p.lambda_out[id] = lam;
-        p.steps_out[id] = nst;
-        p.fate_out[id] = (uint8_t)fate;
-        double inv[4];
-        invariants64(M, a, y, inv);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) p.inv1_out[(size_t)c * p.n + id] = inv[c];
-        if (kSink == kSinkStrided) store_nan_samples<kMixed>(p, id, (uint64_t)nst / p.stride + 1);
-      }
+      // the lane's ray is done; its end-of-ray work waits in `pending`
+      // (deferred sinks, at the top of the loop)
+      pending = fate;
       active = false;
     }
   }
@@ -1145,6 +1211,10 @@ const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, int f
 }
 
 }  // namespace
+
+cudaError_t read_wait_timeouts(unsigned long long* total) {
+  return cudaMemcpyFromSymbol(total, g_wait_timeouts, sizeof(unsigned long long));
+}
 
 int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, int threads_per_block) {
   const void* k = pick(kerr, mixed, src, sink, mixed, MALBEC_FORM_GEODESIC, MALBEC_METHOD_RK4);  // the larger of the two

@@ -20,8 +20,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmalbec.so")
 FP64, FP32_MIXED = 0, 1
 FORM_GEODESIC, FORM_HAMILTONIAN, FORM_ADM = 0, 1, 2
 METHOD_RK4, METHOD_DOPRI5 = 0, 1
-OUT_FINAL, OUT_STRIDED = 0, 1
+OUT_FINAL, OUT_STRIDED, OUT_STRIDED_CARTESIAN = 0, 1, 2
 FATE_CAPTURED, FATE_ESCAPED, FATE_CAPPED, FATE_NONFINITE = 1, 2, 3, 4
+FATE_DRIFTED, FATE_MASK, NORM_DRIFT_TOL = 0x80, 0x7F, 1e-3  # validity flag or-ed into a fate
 OK, EINVAL, ENOMEM, EBUSY, ETIMEDOUT, ECUDA, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
 
 _D = ctypes.c_double
@@ -67,7 +68,7 @@ class Bundle(ctypes.Structure):
 
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("threads_per_block", _U32), ("blocks_per_sm", _U32), ("refill_min", _U32),
-                ("zone_batch", _U32), ("zone_wait", _U32), ("exchange", _U32)]
+                ("zone_batch", _U32), ("zone_wait", _U32), ("exchange", _U32), ("zone_wait_limit_us", _U32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -151,6 +152,7 @@ def _declare(L):
     sig("malbec_set_launch_config", ctypes.c_int, ctypes.POINTER(LaunchConfig))
     sig("malbec_get_launch_config", ctypes.c_int, ctypes.POINTER(LaunchConfig))
     sig("malbec_set_mixed_zone", ctypes.c_int, ctypes.POINTER(MixedZone))
+    sig("malbec_wait_status", ctypes.c_int, ctypes.POINTER(_U64))
     sig("malbec_get_mixed_zone", ctypes.c_int, ctypes.POINTER(MixedZone))
 
 
@@ -255,10 +257,11 @@ def _views_final(buf, L: Layout, n: int, mode: int, precision):
         "fate": v(L.fate, n, torch.uint8, (n,)),
         "buffer": buf,
     }
-    if mode == OUT_STRIDED:
+    if mode != OUT_FINAL:
         ns = int(L.n_samples)
+        comps = 4 if mode == OUT_STRIDED_CARTESIAN else 8
         dt = torch.float64 if _prec(precision) == FP64 else torch.float32
-        out["traj"] = v(L.traj, n * ns * 8, dt, (n, ns, 8))
+        out["traj"] = v(L.traj, n * ns * comps, dt, (n, ns, comps))
     return out
 
 
@@ -304,7 +307,7 @@ def trace(M: float, a: float, ics, term, mode: int = OUT_FINAL, stride: int = 0,
     ics = _dev_f64(ics)
     n = ics.shape[1]
     t = term_from(term)
-    L = out_layout(mode, precision, n, t.n_steps_cap, stride if mode == OUT_STRIDED else 0)
+    L = out_layout(mode, precision, n, t.n_steps_cap, stride if mode != OUT_FINAL else 0)
     if out is None:
         out = torch.empty(L.total, dtype=torch.uint8, device=ics.device)
     else:
@@ -313,7 +316,7 @@ def trace(M: float, a: float, ics, term, mode: int = OUT_FINAL, stride: int = 0,
     if apr is not None:
         check_device_tensor(apr, "a_per_ray", torch.float64, numel=n, device_index=ics.device.index)
     m = Metric(float(M), float(a), _ptr(apr))
-    _check(lib().malbec_trace(m, _ptr(ics), n, t.c(), mode, stride if mode == OUT_STRIDED else 0,
+    _check(lib().malbec_trace(m, _ptr(ics), n, t.c(), mode, stride if mode != OUT_FINAL else 0,
                               _prec(precision), _ptr(out), _stream(stream)), "malbec_trace")
     res = _views_final(out, L, n, mode, precision)
     res["_keep"] = (ics, apr)
@@ -337,12 +340,12 @@ def trace_noalloc(M: float, a: float, ics, term, out, mode: int = OUT_FINAL, str
         raise ValueError(f"ics: expected shape (8, n) with n >= 1, got {tuple(ics.shape)}")
     t = term_from(term)
     n = ics.shape[1]
-    L = out_layout(mode, precision, n, t.n_steps_cap, stride if mode == OUT_STRIDED else 0)
+    L = out_layout(mode, precision, n, t.n_steps_cap, stride if mode != OUT_FINAL else 0)
     check_device_tensor(out, "out", torch.uint8, numel_min=int(L.total), device_index=dev)
     if a_per_ray is not None:
         check_device_tensor(a_per_ray, "a_per_ray", torch.float64, numel=n, device_index=dev)
     m = Metric(float(M), float(a), _ptr(a_per_ray))
-    _check(lib().malbec_trace_noalloc(m, _ptr(ics), n, t.c(), mode, stride if mode == OUT_STRIDED else 0,
+    _check(lib().malbec_trace_noalloc(m, _ptr(ics), n, t.c(), mode, stride if mode != OUT_FINAL else 0,
                                       _prec(precision), _ptr(out), _stream(stream)), "malbec_trace_noalloc")
     return _views_final(out, L, n, mode, precision)
 
@@ -619,15 +622,26 @@ def set_mixed_zone(horizon_factor=None, photon_margin=None, pole_sin=None, reset
 
 
 def set_launch_config(threads_per_block=0, blocks_per_sm=0, refill_min=0, zone_batch=0, zone_wait=0, exchange=0,
-                      reset=False) -> LaunchConfig:
+                      zone_wait_limit_us=0, reset=False) -> LaunchConfig:
     """Process-wide launch configuration of the trace kernels (0 = automatic)."""
     if reset:
         _check(lib().malbec_set_launch_config(None), "malbec_set_launch_config")
     else:
         c = LaunchConfig(int(threads_per_block), int(blocks_per_sm), int(refill_min), int(zone_batch),
-                         int(zone_wait), int(exchange))
+                         int(zone_wait), int(exchange), int(zone_wait_limit_us))
         _check(lib().malbec_set_launch_config(ctypes.byref(c)), "malbec_set_launch_config")
     return get_launch_config()
+
+
+def wait_status():
+    """(timed_out, total): malbec_wait_status -- whether a bounded device
+    wait ran out since the previous call (MALBEC_ETIMEDOUT), and the device's
+    running count of such expiries.  Synchronises the device."""
+    t = _U64()
+    rc = lib().malbec_wait_status(ctypes.byref(t))
+    if rc not in (OK, ETIMEDOUT):
+        _check(rc, "malbec_wait_status")
+    return rc == ETIMEDOUT, int(t.value)
 
 
 def get_launch_config() -> LaunchConfig:

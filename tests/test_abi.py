@@ -170,14 +170,28 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
         malbec.lib()
 
 
+def test_cartesian_layout(mb):
+    """MALBEC_OUT_STRIDED_CARTESIAN: the FINAL fields plus 4 components (t, x,
+    y, z) per sample instead of 8."""
+    n, cap, stride = 1000, 1000, 10
+    L8 = mb.out_layout(mb.OUT_STRIDED, "fp64", n, cap, stride)
+    L4 = mb.out_layout(mb.OUT_STRIDED_CARTESIAN, "fp64", n, cap, stride)
+    assert L4.traj == L8.traj and L4.n_samples == L8.n_samples == cap // stride + 1
+    assert L4.total - L4.traj == pytest.approx((L8.total - L8.traj) / 2, abs=256)
+    L4f = mb.out_layout(mb.OUT_STRIDED_CARTESIAN, "fp32_mixed", n, cap, stride)
+    assert L4f.total - L4f.traj >= n * L4f.n_samples * 16
+    with pytest.raises(mb.MalbecError):
+        mb.out_layout(mb.OUT_STRIDED_CARTESIAN, "fp64", n, cap, 0)
+
+
 def test_launch_config_setting(mb):
     c = mb.get_launch_config()
     assert c.as_dict() == {"threads_per_block": 0, "blocks_per_sm": 0, "refill_min": 0, "zone_batch": 0,
-                           "zone_wait": 0, "exchange": 0}
+                           "zone_wait": 0, "exchange": 0, "zone_wait_limit_us": 0}
     c2 = mb.set_launch_config(threads_per_block=64, blocks_per_sm=2, refill_min=4, zone_batch=8, zone_wait=32,
-                              exchange=2)
+                              exchange=2, zone_wait_limit_us=1500)
     assert c2.as_dict() == {"threads_per_block": 64, "blocks_per_sm": 2, "refill_min": 4, "zone_batch": 8,
-                            "zone_wait": 32, "exchange": 2}
+                            "zone_wait": 32, "exchange": 2, "zone_wait_limit_us": 1500}
     bad = mb.LaunchConfig(48, 0, 0, 0, 0)
     assert mb.lib().malbec_set_launch_config(ctypes.byref(bad)) == mb.EINVAL
     bad = mb.LaunchConfig(512, 0, 0, 0, 0)

@@ -120,10 +120,30 @@ def test_self_convergence_ratio_and_drift_summary():
 
     class FakeMb:
         FATE_NONFINITE = 4
+        FATE_MASK, FATE_DRIFTED = 0x7F, 0x80
 
-    r = {"fate": torch.tensor([3, 3, 4, 2]),
+    # a flagged CAPPED ray (0x83) counts as CAPPED: only the NONFINITE one is left out
+    r = {"fate": torch.tensor([3, 0x83, 4, 2]),
          "inv0": torch.ones((4, 4), dtype=torch.float64),
          "inv1": torch.ones((4, 4), dtype=torch.float64)}
     r["inv1"][2] += torch.tensor([1e-9, 3e-9, 1e3, 2e-9], dtype=torch.float64)
     d = bench.drift_summary(FakeMb, torch, r)
     assert d["nonfinite"] == 1 and abs(d["Q"]["median"] - 2e-9) < 1e-15 and d["E"]["median"] == 0.0
+
+
+def test_fate_counts_split_the_validity_flag():
+    """bench.fate_counts counts terminations by fate & FATE_MASK and the
+    flagged (FATE_DRIFTED) escaped and capped rays separately."""
+    sys.path.insert(0, ROOT)
+    import torch
+
+    import bench
+
+    class FakeMb:
+        FATE_MASK, FATE_DRIFTED = 0x7F, 0x80
+
+    f = torch.tensor([1, 2, 0x82, 0x82, 3, 0x83, 4, 2], dtype=torch.uint8)
+    c = bench.fate_counts(FakeMb, f)
+    assert c["captured"] == 1 and c["escaped"] == 4 and c["escaped_drifted"] == 2
+    assert c["capped"] == 2 and c["capped_drifted"] == 1 and c["nonfinite"] == 1
+    assert abs(c["drifted_fraction"] - 3 / 8) < 1e-12

@@ -2,8 +2,11 @@
 (MALBEC_METHOD_DOPRI5, FP64) on the GPU against the oracle's method 1 in
 each form (the geodesic equation, and the canonical equations through
 g^{mu nu} of eq. kerr or the 3+1 quantities of eq. ADM): the same tableau,
-error norm and controller, so the same sequence of attempts up to rounding.  States within 1e-9 per component on the rays
-whose oracle map is well conditioned; attempt counts and fates equal."""
+error norm and controller, so the same sequence of attempts up to rounding.
+States within 1e-9 per component, attempt counts and fates equal, on the rays
+whose oracle map is insensitive to rounding (bound orbits: measured with the
+oracle's rhs_noise option) or well conditioned (cameras and samples: kappa).
+"""
 import dataclasses
 
 import numpy as np
@@ -45,40 +48,61 @@ def dp_term(mb, tol=1e-10, **kw):
     return mb.Termination(**base)
 
 
+SENS_MAX = 1e-10
+
+
+def oracle_rounding_sensitivity(orc, M, a, ics, t_or, a_per_ray=None):
+    """Per ray, how far the oracle's own result moves when every component of
+    every right-hand-side evaluation is perturbed by +-1 unit in the last
+    place (the oracle's rhs_noise option, two sign patterns: delta = 2^-52
+    and 1.5 x 2^-52): the largest relative change of the final state, +inf
+    where the number of attempts, lambda or the fate changed.  Two correct
+    FP64 implementations of the adaptive map differ by rounding of about that
+    size on every evaluation, so a ray whose result moves by more than
+    SENS_MAX cannot be compared at 1e-9: its adaptive map sits at a step
+    decision the rounding can flip, or amplifies rounding (passages next to
+    the polar axis)."""
+    ref = orc.trace_many(M, a, ics, t_or, a_per_ray=a_per_ray)
+    sens = np.zeros(ics.shape[1])
+    for delta in (2.0**-52, 1.5 * 2.0**-52):
+        t1 = orc.make_term(t_or.eps_hor, t_or.r_esc, t_or.n_steps_cap, t_or.dl, t_or.dl_r_scale, t_or.form,
+                           t_or.method, t_or.rtol, t_or.atol, delta)
+        per = orc.trace_many(M, a, ics, t1, a_per_ray=a_per_ray)
+        with np.errstate(invalid="ignore"):
+            rel = (np.abs(per["y"] - ref["y"]) / np.maximum(np.abs(ref["y"]), 1.0)).max(axis=0)
+        rel = np.where(np.isfinite(rel), rel, np.inf)
+        moved = (per["steps"] != ref["steps"]) | (per["lambda"] != ref["lambda"]) | (per["fate"] != ref["fate"])
+        sens = np.maximum(sens, np.where(moved, np.inf, rel))
+    return ref, sens
+
+
 def test_bound_orbits_match_oracle(mb, orc, W, form):
     """512 generic bound orbits (per-particle spin), 3000 attempts at
     tolerance 1e-10.  The adaptive map is discontinuous where an attempt's
     error norm sits at the acceptance threshold or carries a step exponent
-    across an integer: there a rounding difference gives
-    another sequence of steps, seen as another lambda after the same number
-    of attempts.  On >= 95% of the orbits the sequence is the oracle's
-    (attempts and lambda equal); on those whose oracle map is also
-    well conditioned, fates equal and states within 1e-9 (99% of them;
-    all within 1e-6).  Every capped
-    orbit, the others included, keeps E, L_z, Q and the norm within
-    3000 x tol of their initial values."""
+    across an integer, and a step across a near-polar passage amplifies the
+    rounding of each stage; the oracle's own rounding sensitivity (above)
+    finds those rays.  On every other orbit (at least 95%; measured 97-98%)
+    the GPU takes the oracle's sequence of attempts (count and lambda equal,
+    bit for bit), ends with its fate, and every state component is within
+    1e-9.  Every capped orbit, the excluded ones included, keeps E, L_z, Q
+    and the norm within 3000 x tol of their initial values."""
     wl = W.bound()
     idx = wl.subsample(512)
     ys, spins, _ = orc.bound_samples(wl.M, wl.a_max, wl.seed, idx)
     t = dp_term(mb, form=form)
     got = gpu_trace(mb, wl.M, 0.0, ys, t, a_per_ray=spins)
-    ref, kappa = oracle_kappa(orc, wl.M, 0.0, ys, oracle_term(orc, t), a_per_ray=spins)
+    ref, sens = oracle_rounding_sensitivity(orc, wl.M, 0.0, ys, oracle_term(orc, t), a_per_ray=spins)
+    good = sens <= SENS_MAX
+    print("form", form, "rounding-sensitive orbits excluded:", int((~good).sum()), "of", len(good))
+    assert good.mean() >= 0.95, good.mean()
     # with a fixed first step and no r-proportional cap every step is
     # dl 2^(m/4): the same sequence of steps gives the same lambda, bit for bit
-    same = (got["steps"].astype(np.uint32) == ref["steps"]) & (got["lambda"] == ref["lambda"])
-    assert same.mean() >= 0.95, same.mean()
-    good = same & (kappa <= KAPPA_MAX)
-    assert good.mean() >= 0.95
+    assert np.array_equal(got["steps"][good].astype(np.uint32), ref["steps"][good])
+    assert np.array_equal(got["lambda"][good], ref["lambda"][good])
     assert np.array_equal(got["fate"][good], ref["fate"][good])
-    # the kappa test perturbs the initial state only; an adaptive step across
-    # a near-polar passage also amplifies the rounding of each step: 1e-16
-    # relative noise on every right-hand side moved one such orbit by 1e-8
-    # (measured with an independent re-implementation).  99% within 1e-9,
-    # all within 1e-6.
-    rel = (np.abs(got["y"][:, good] - ref["y"][:, good]) / np.maximum(np.abs(ref["y"][:, good]), 1.0)).max(axis=0)
-    assert np.mean(rel <= 1e-9) >= 0.99, np.sort(rel)[-10:]
-    assert rel.max() <= 1e-6, rel.max()
-    capped = got["fate"] == mb.FATE_CAPPED
+    assert_states_close(got["y"][:, good], ref["y"][:, good], what="Dormand-Prince bound orbits")
+    capped = (got["fate"] & mb.FATE_MASK) == mb.FATE_CAPPED
     assert capped.mean() > 0.95
     drift = np.abs(got["inv1"][:, capped] - got["inv0"][:, capped]) / np.maximum(np.abs(got["inv0"][:, capped]), 1.0)
     assert drift.max() <= 3000 * 1e-10, drift.max(axis=1)
@@ -157,10 +181,11 @@ def test_more_accurate_than_rk4_on_camera_rays(mb, W):
     rk = mb.trace(cw.M, cw.a, ics, cw.term)
     dp = mb.trace(cw.M, cw.a, ics, dp_term(mb, tol=1e-9, dl=0.0, dl_r_scale=0.5, n_steps_cap=20_000))
     torch.cuda.synchronize()
-    assert (dp["fate"] == rk["fate"]).float().mean().item() >= 0.99
+    m = mb.FATE_MASK
+    assert ((dp["fate"] & m) == (rk["fate"] & m)).float().mean().item() >= 0.99
 
     def drift(r, c):
-        ok = r["fate"] != mb.FATE_NONFINITE
+        ok = (r["fate"] & m) != mb.FATE_NONFINITE
         d = (r["inv1"][c] - r["inv0"][c]).abs()[ok]
         return d[torch.isfinite(d)].median().item()
 

@@ -224,15 +224,25 @@ def _pixel_ab(cw, pix):
     return al, be
 
 
+def _camera_near(orc, cw, pix, exclusion=0.098):
+    """Pixels whose (alpha, beta) lie within `exclusion` of the critical curve
+    (the oracle's polyline distance, vectorised)."""
+    al, be = _pixel_ab(cw, np.asarray(pix))
+    return orc.critical_curve_distance_many(cw.M, cw.a, cw.incl, al, be) < exclusion
+
+
 def _camera_compare(mb, orc, cw, got, pix, exclusion=0.098, form=None):
     """Per-pixel comparison with the oracle on the pixels `pix` (the form of
-    cw.term unless `form` is given)."""
+    cw.term unless `form` is given).  `agree` compares the whole fate byte,
+    validity flag included (both sides FP64, same rule); `far` drops pixels
+    near the critical curve and pixels CAPPED on either side."""
     ics = orc.camera_ics(cw.M, cw.a, cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny, pix)
     ref, kappa = oracle_kappa(orc, cw.M, cw.a, ics, oracle_term(orc, cw.term, form))
-    near = np.array([orc.critical_curve_distance(cw.M, cw.a, cw.incl, *_pixel_ab(cw, p)) < exclusion for p in pix])
+    near = _camera_near(orc, cw, pix, exclusion)
     fate_g = got["fate"][pix]
     agree = fate_g == ref["fate"]
-    far = ~near & (ref["fate"] != mb.FATE_CAPPED) & (fate_g != mb.FATE_CAPPED)
+    capped = ((ref["fate"] & mb.FATE_MASK) == mb.FATE_CAPPED) | ((fate_g & mb.FATE_MASK) == mb.FATE_CAPPED)
+    far = ~near & ~capped
     ref["kappa"] = kappa
     return ref, near, agree, far
 
@@ -316,15 +326,20 @@ def test_schwarzschild_camera_parity(mb, orc, W):
     al, be = _pixel_ab(cw, pix)
     b = np.hypot(al, be)
     crit = 3.0 * math.sqrt(3.0)
-    assert np.all(got["fate"][b < crit - 0.2] == mb.FATE_CAPTURED)
-    assert np.all(got["fate"][b > crit + 0.2] == mb.FATE_ESCAPED)
+    base = got["fate"] & mb.FATE_MASK
+    assert np.all(base[b < crit - 0.2] == mb.FATE_CAPTURED)
+    assert np.all(base[b > crit + 0.2] == mb.FATE_ESCAPED)
 
 
-def test_camera_full_size_sampled_parity(mb, orc, W):
-    """The full 1024 x 1024 render in the benchmark's launch configuration,
-    checked on 3000 seeded sample pixels: >= 99.99% fate agreement away from
-    the critical curve (2 pixel pitches = 0.098M), escaped-ray angles within
-    1e-9."""
+def test_camera_full_image_parity(mb, orc, W):
+    """The full 1024 x 1024 render in the benchmark's launch configuration
+    against the oracle on every one of its 1,048,576 pixels: fates (validity
+    flag included) agree on >= 99.99% of the pixels away from the critical
+    curve (2 pixel pitches = 0.098M, the reading of "away from the critical
+    curve") and on every such pixel whose oracle map is well conditioned;
+    escaped-ray angles within 1e-9 there; NONFINITE below 1e-3 of the
+    pixels.  The oracle traces the image twice (kappa), in about half a
+    minute on the host's cores."""
     import torch
 
     cw = W.camera()
@@ -332,16 +347,22 @@ def test_camera_full_size_sampled_parity(mb, orc, W):
     res = mb.trace_camera(cw.M, cw.a, cam, cw.term, "fp64")
     torch.cuda.synchronize()
     got = {k: np_(v) for k, v in res.items() if k != "buffer"}
-    # NONFINITE appears for a few rays that run into the polar axis
-    assert set(np.unique(got["fate"])) <= {1, 2, 3, 4} and (got["fate"] == 4).mean() < 1e-3
-    pix = np.random.default_rng(1803).choice(cw.n, 3000, replace=False)
+    base = got["fate"] & mb.FATE_MASK
+    assert set(np.unique(base)) <= {1, 2, 3, 4} and (base == 4).mean() < 1e-3
+    assert set(np.unique(got["fate"] & ~np.uint8(mb.FATE_MASK))) <= {0, mb.FATE_DRIFTED}
+    pix = np.arange(cw.n)
     ref, near, agree, far = _camera_compare(mb, orc, cw, got, pix)
-    assert agree[far].mean() >= 0.9999
     good = ref["kappa"] <= KAPPA_MAX
+    print("full image: far", far.sum(), "agree", agree[far].mean(), "ill-conditioned", (far & ~good).sum(),
+          "flagged", ((got["fate"] & mb.FATE_DRIFTED) != 0).mean())
+    assert agree[far].mean() >= 0.9999
+    assert agree[far & good].all(), np.argwhere(far & good & ~agree)[:10]
+    assert np.array_equal(got["steps"][far & good].astype(np.uint32), ref["steps"][far & good])
     assert (far & ~good).sum() <= 0.03 * far.sum(), (far & ~good).sum()
-    esc = far & good & agree & (ref["fate"] == mb.FATE_ESCAPED)
-    assert_states_close(got["theta"][pix][esc], ref["y"][2][esc], what="theta")
-    assert_states_close(got["phi"][pix][esc], ref["y"][3][esc], what="phi")
+    esc = far & good & (ref["fate"] == mb.FATE_ESCAPED)
+    assert esc.sum() > 500_000
+    assert_states_close(got["theta"][esc], ref["y"][2][esc], what="theta")
+    assert_states_close(got["phi"][esc], ref["y"][3][esc], what="phi")
 
 
 # --------------------------------------------------------------------------- edge cases
@@ -423,6 +444,60 @@ def test_strided_trajectories_match_oracle(mb, orc):
     got = gpu_trace(mb, 1.0, 0.0, ics, tn, mode=mb.OUT_STRIDED, stride=10)
     ref = orc.trace_many(1.0, 0.0, ics, oracle_term(orc, tn), stride=10, want_traj=True)
     assert np.array_equal(got["fate"], ref["fate"]) and np.array_equal(np.isnan(got["traj"]), np.isnan(ref["traj"]))
+
+
+def test_cartesian_samples_reproduce_the_paper_output_rows(mb):
+    """MALBEC_OUT_STRIDED_CARTESIAN writes the paper's output records (Sec. 5,
+    output.txt: t, x, y, z per step of tau, Cartesian by eq. coord).  From the
+    paper's own initial-condition rows (ic.txt, read in its text layout and
+    converted on the device, p_t column = E) with RK4 h = 0.1, the samples
+    equal the printed output rows to their four decimals (half a unit, plus
+    the effect of the four-decimal initial conditions: 6e-5)."""
+    import os
+
+    import torch
+
+    from conftest import GOLDEN, load_golden
+
+    rows = mb.read_paper_rows(os.path.join(GOLDEN, "ic_rows.txt"))
+    ics = mb.ic_from_paper(1.0, 0.0, rows)
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=2, dl=0.1)
+    got = mb.trace(1.0, 0.0, ics, t, mode=mb.OUT_STRIDED_CARTESIAN, stride=1)
+    torch.cuda.synchronize()
+    traj = np_(got["traj"])
+    assert traj.shape == (3, 3, 4)
+    for pid, tau, tt, x, y, z in load_golden("output_rows.txt"):
+        sample = traj[int(pid) - 1, int(round(float(tau) / 0.1))]
+        np.testing.assert_allclose(sample, [float(tt), float(x), float(y), float(z)], atol=6e-5)
+
+
+@pytest.mark.parametrize("precision,form", [("fp64", 0), ("fp64", 1), ("fp32_mixed", 0)])
+def test_cartesian_samples_match_oracle(mb, orc, precision, form):
+    """Cartesian samples (t, x, y, z) every 7 steps of 37 generic bound orbits
+    (per-ray spin up to 0.998) against the oracle's state samples mapped by
+    eq. coord (x = sqrt(r^2 + a^2) sin th cos ph, ...): within 1e-9 in FP64
+    (geodesic and canonical forms), within 1e-4 in FP32_MIXED (its samples
+    are FP32, from the state's hi words); NaN after the end on both sides."""
+    n = 37
+    ys, spins, _ = orc.bound_samples(1.0, 0.998, 77, np.arange(n))
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=1000, dl=0.05, form=form)
+    got = gpu_trace(mb, 1.0, 0.0, ys, t, mode=mb.OUT_STRIDED_CARTESIAN, stride=7, precision=precision,
+                    a_per_ray=spins)
+    ref = orc.trace_many(1.0, 0.0, ys, oracle_term(orc, t), a_per_ray=spins, stride=7, want_traj=True)
+    ns = 1000 // 7 + 1
+    assert got["traj"].shape == (n, ns, 4)
+    rt = ref["traj"]
+    want = np.full((n, ns, 4), np.nan)
+    for i in range(n):
+        for k in range(ns):
+            st = rt[i, k]
+            if np.isfinite(st).all():
+                want[i, k, 0] = st[0]
+                want[i, k, 1:] = orc.bl_to_cartesian(spins[i], st[1], st[2], st[3])
+    assert np.array_equal(np.isnan(got["traj"]), np.isnan(want))
+    fin = np.isfinite(want)
+    rtol = 1e-9 if precision == "fp64" else 1e-4
+    assert_states_close(got["traj"][fin], want[fin], rtol=rtol, what="Cartesian samples")
 
 
 def test_results_independent_of_batch_composition(mb, orc, W):
@@ -518,17 +593,97 @@ def test_mixed_camera_pixel_agreement(mb, orc, W):
     # exclusion mask on a strided subgrid of pixels (distance test is on the host)
     pix = np.arange(0, cw.n, 37)
     al, be = _pixel_ab(cw, pix)
-    far = np.array([orc.critical_curve_distance(cw.M, cw.a, cw.incl, x, y) >= 0.098 for x, y in zip(al, be)])
+    far = ~_camera_near(orc, cw, pix)
     Lz = -al * math.sin(cw.incl)
     Q = be * be + math.cos(cw.incl) ** 2 * (al * al - cw.a * cw.a)
     off_axis = sin_theta_turn(1.0, Lz, Q, cw.a, 0.0) >= 0.05
-    same = f64[pix] == f32[pix]
-    print("mixed vs fp64 fate agreement: all", (f64 == f32).mean(), "far", same[far].mean(),
+    # the termination (fate & FATE_MASK); the validity flag follows each
+    # path's own norm drift and is compared with the oracle separately
+    b64, b32 = f64 & mb.FATE_MASK, f32 & mb.FATE_MASK
+    same = b64[pix] == b32[pix]
+    print("mixed vs fp64 fate agreement: all", (b64 == b32).mean(), "far", same[far].mean(),
           "far & off-axis", same[far & off_axis].mean(), "off-axis fraction", off_axis.mean())
     # away from the critical curve and from the polar axis (sin theta_turn >= 0.05)
     # the fates agree; near the axis both paths are ill-conditioned
     assert same[far & off_axis].mean() >= 0.9999
-    assert (f64 == f32).mean() >= 0.99
+    assert (b64 == b32).mean() >= 0.99
+
+
+def _quantiles(x):
+    x = np.asarray(x)
+    return {"median": float(np.median(x)), "p99": float(np.quantile(x, 0.99)), "max": float(x.max())} if x.size else {}
+
+
+def test_mixed_camera_against_the_oracle(mb, orc, W):
+    """FP32_MIXED camera (Kerr a = 0.9, 80 deg, 128 x 128 of the +-25M field)
+    against the FP64 oracle directly.  Away from the critical curve and from
+    the polar axis (sin theta_turn >= 0.05): terminations (fate & FATE_MASK)
+    agree on >= 99.9% of the pixels; on rays escaped and unflagged on both
+    sides, the final theta and phi are within 1e-6 rad for 99% of them and
+    within 1e-4 rad for all (the stated FP32_MIXED error of escaped angles;
+    measured: median 2e-8 / 5e-8, p99 1.7e-7 / 4.4e-7, max 7.7e-6 / 4.8e-6).
+    The validity flag agrees with the oracle's on >= 99% of those pixels."""
+    import torch
+
+    cw = W.camera(nx=128, ny=128)
+    cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
+    res = mb.trace_camera(cw.M, cw.a, cam, cw.term, "fp32_mixed")
+    torch.cuda.synchronize()
+    got = {k: np_(v) for k, v in res.items() if k != "buffer"}
+    pix = np.arange(cw.n)
+    ics = orc.camera_ics(cw.M, cw.a, cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny, pix)
+    ref = orc.trace_many(cw.M, cw.a, ics, oracle_term(orc, cw.term))
+    al, be = _pixel_ab(cw, pix)
+    Lz = -al * math.sin(cw.incl)
+    Q = be * be + math.cos(cw.incl) ** 2 * (al * al - cw.a * cw.a)
+    sel = ~_camera_near(orc, cw, pix) & (sin_theta_turn(1.0, Lz, Q, cw.a, 0.0) >= 0.05)
+    m = mb.FATE_MASK
+    same = (got["fate"] & m) == (ref["fate"] & m)
+    esc = sel & (got["fate"] == mb.FATE_ESCAPED) & (ref["fate"] == mb.FATE_ESCAPED)
+    eth = np.abs(got["theta"][esc] - ref["y"][2][esc])
+    eph = np.abs(got["phi"][esc] - ref["y"][3][esc])
+    flag_same = (got["fate"] & mb.FATE_DRIFTED) == (ref["fate"] & mb.FATE_DRIFTED)
+    print("mixed camera vs oracle: selected", sel.sum(), "fate agreement", same[sel].mean(),
+          "flag agreement", flag_same[sel].mean(), "escaped", esc.sum(),
+          "theta", _quantiles(eth), "phi", _quantiles(eph))
+    assert sel.sum() > 10_000 and esc.sum() > 7_000
+    assert same[sel].mean() >= 0.999
+    assert flag_same[sel].mean() >= 0.99
+    for e in (eth, eph):
+        assert np.quantile(e, 0.99) <= 1e-6 and e.max() <= 1e-4
+
+
+def test_mixed_bound_orbits_against_the_oracle(mb, orc, W):
+    """FP32_MIXED on the generic bound-orbit subsample (1024 particles of the
+    2^20 workload, 10^4 steps of dtau = 0.02) against the FP64 oracle
+    directly: lambda (accumulated in FP64: fixed steps are counted and
+    added to the FP64 lambda 32 at a time, the oracle adds them one by one)
+    within 1e-12 relative of the oracle's (measured 1.7e-13); on the orbits
+    the oracle's map resolves (kappa <= 1e5, FP64 drift of the invariants
+    <= 1e-8), every state component within 1e-4 of the oracle (relative to
+    max(|y|, 1), as the FP64 parity bound; measured max 3.3e-5 in theta) with
+    a median below 1e-7 per component, and E, L_z, Q and the norm within 1e-6
+    of their initial values."""
+    wl = W.bound()
+    idx = wl.subsample(1024)
+    ref_y, ref_a, _ = orc.bound_samples(wl.M, wl.a_max, wl.seed, idx)
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=10_000, dl=0.02)
+    got = gpu_trace(mb, wl.M, 0.0, ref_y, t, precision="fp32_mixed", a_per_ray=ref_a)
+    ref, kappa = oracle_kappa(orc, wl.M, 0.0, ref_y, oracle_term(orc, t), a_per_ray=ref_a)
+    with np.errstate(invalid="ignore"):
+        d_ref = np.abs(ref["inv1"] - ref["inv0"]) / np.maximum(np.abs(ref["inv0"]), 1.0)
+        d_got = np.abs(got["inv1"] - got["inv0"]) / np.maximum(np.abs(got["inv0"]), 1.0)
+    ok = (kappa <= KAPPA_MAX) & (np.nan_to_num(d_ref, nan=np.inf).max(axis=0) <= 1e-8)
+    assert ok.mean() >= 0.97, ok.mean()
+    assert np.array_equal(got["fate"][ok], ref["fate"][ok])
+    lam_err = np.abs(got["lambda"] - ref["lambda"]) / ref["lambda"]
+    err = (np.abs(got["y"] - ref["y"]) / np.maximum(np.abs(ref["y"]), 1.0))[:, ok]
+    print("mixed bound vs oracle: resolved", ok.sum(), "lambda max rel", lam_err.max(),
+          "state rel err per component (max)", err.max(axis=1), "median", np.median(err, axis=1),
+          "drift max", d_got[:, ok].max(axis=1))
+    assert lam_err.max() <= 1e-12
+    assert err.max() <= 1e-4 and np.median(err, axis=1).max() <= 1e-7
+    assert d_got[:, ok].max() <= 1e-6
 
 
 @pytest.mark.parametrize("config", ["circular", "camera", "bound"])
