@@ -315,7 +315,7 @@ def steps_of(views) -> int:
 
 
 def run_bundles_case(mb, torch, stream, flush, count: int, precision: str, K: int, warmup: int,
-                     autotune_every: int = 8, per_bundle_arm: bool = True) -> dict:
+                     autotune_every: int = 8, per_bundle_arm: bool = True, refine_full_list: bool = True) -> dict:
     """Uneven bundles (the first `count` of the 4096-bundle list): one
     persistent launch replayed from a CUDA graph after autotuning, against
     one launch per bundle on the same stream.  Each timed pass is bracketed
@@ -342,7 +342,7 @@ def run_bundles_case(mb, torch, stream, flush, count: int, precision: str, K: in
     # flight, so it can prefer fewer resident warps than the full list), one
     # replay each after a warm-up replay; the faster one is timed below
     refine = {}
-    if count > len(sub):
+    if refine_full_list and count > len(sub):
         alt = dict(best, blocks_per_sm=best["blocks_per_sm"] + 1)
         for name, cfg in (("subset_choice", best), ("one_more_block_per_sm", alt)):
             mb.set_launch_config(**cfg)
@@ -890,6 +890,49 @@ def timed_renders(mb, cw, cam, precision, K, stream, flush, out=None, host_out=N
     return [s.elapsed_time(e) for s, e in evs], res
 
 
+def run_e2e_states(mb, torch, stream, flush, K: int, n: int = 1 << 20, n_steps: int = 200) -> dict:
+    """End to end with inputs: the generic bound-orbit workload (n particles,
+    per-particle spin, the configuration's dtau, n_steps steps), FP64.  Every
+    timed step copies the initial states and spins from pinned host memory to
+    the device, traces them through malbec_trace (the binding's trace), and
+    copies the whole output (final states, lambda, invariants, steps, fates)
+    back to pinned host memory; CUDA events on the stream bracket all three."""
+    from paper_1803_08320_gb300 import workloads as W
+
+    wl = W.bound(n=n, n_steps=n_steps)
+    ics_d, spins_d, _ = mb.ic_bound(wl.M, wl.a_max, wl.seed, n, stream=stream)
+    stream.synchronize()
+    ics_h = torch.empty(ics_d.shape, dtype=torch.float64, pin_memory=True)
+    spins_h = torch.empty(spins_d.shape, dtype=torch.float64, pin_memory=True)
+    ics_h.copy_(ics_d)
+    spins_h.copy_(spins_d)
+    L = mb.out_layout(mb.OUT_FINAL, "fp64", n, n_steps, 0)
+    out_d = torch.empty(L.total, dtype=torch.uint8, device="cuda")
+    out_h = torch.empty(L.total, dtype=torch.uint8, pin_memory=True)
+    times, steps = [], 0
+    for k in range(K + 1):  # the first pass warms up
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            ics_d.copy_(ics_h, non_blocking=True)
+            spins_d.copy_(spins_h, non_blocking=True)
+            r = mb.trace(wl.M, 0.0, ics_d, wl.term, precision="fp64", a_per_ray=spins_d, stream=stream, out=out_d)
+            out_h.copy_(out_d, non_blocking=True)
+            e1.record(stream)
+        stream.synchronize()
+        if k:
+            times.append(e0.elapsed_time(e1))
+            steps = int(r["steps"].to(torch.int64).sum().item())
+    sec = statistics.mean(times) / 1e3
+    h2d = int(ics_h.numel() * 8 + spins_h.numel() * 8)
+    return {"value": steps / sec, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(L.total),
+            "ms_per_step": 1e3 * sec, "rk4_steps_per_step": steps,
+            "workload": f"bound_orbits_{n}_a0-0.998_dtau{wl.term.dl}_{n_steps}steps_fp64",
+            "note": "initial states and spins copied host->device, malbec_trace, the full output copied "
+                    "device->host, every step inside the CUDA events (pinned host memory)"}
+
+
 def run_workload(args) -> None:
     """--workload bundles | serving: one JSON line of its own (1 GPU)."""
     import torch
@@ -1038,6 +1081,8 @@ def main():
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="req/s for --workload serving")
     ap.add_argument("--requests", type=int, default=64, help="requests per rate for --workload serving")
     ap.add_argument("--no-extras", action="store_true", help="camera line without the bundles/serving samples")
+    ap.add_argument("--no-full-configs", action="store_true",
+                    help="skip the full-size generic bound-orbit and uneven-bundle runs of the default line")
     ap.add_argument("--no-per-bundle-arm", action="store_true",
                     help="--workload bundles: time the persistent graph launch only (the full 4096-bundle list "
                          "takes about ten minutes with one launch per bundle)")
@@ -1250,6 +1295,8 @@ def main():
         barrier()
         t_e2e = max_over_ranks(sum(times_e2e) / 1e3)
         value_e2e = world * steps_per_render * args.steps / t_e2e
+        # end to end with input copies (states H2D, results D2H)
+        e2e_states = run_e2e_states(mb, torch, stream, flush, max(1, min(args.steps, 5)))
 
     cl = clocks.summary()
     flops = FLOPS_PER_STEP["kerr"] * steps_per_render
@@ -1279,6 +1326,7 @@ def main():
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(L.total),
                 "note": "malbec_trace_camera + copy of the image (fate, steps, theta, phi) to pinned host memory; "
                         "the rays are built on the device from the camera description passed by value"},
+        "e2e_states": e2e_states,
         "canonical_form": canonical,
         "adm_form": adm_form,
         "dopri5": dopri5,
@@ -1299,6 +1347,17 @@ def main():
         line["serving_sample"] = run_serving_case(mb, torch, rate=200.0, n_req=32, precision=args.precision)
         line["serving_below_saturation"] = run_serving_low_load(mb, torch, line["serving_sample"], n_req=32,
                                                                 precision=args.precision)
+        if not args.no_full_configs:
+            # the generic bound-orbit and uneven-bundle configurations at
+            # their full sizes: 2^20 orbits x 10^5 steps (FP64 and
+            # FP32_MIXED, 1024-particle oracle subsample), and all 4096
+            # bundles in one persistent graph launch (autotuned on every 32nd
+            # bundle; the kernel is warm from the sample above)
+            line["config3_bound_full"] = run_bound_case(mb, torch, stream, flush, n=1 << 20, n_steps=100_000,
+                                                        precisions=("fp64", "fp32_mixed"), with_oracle=True)
+            line["config4_bundles_full"] = run_bundles_case(mb, torch, stream, flush, 4096, args.precision, K=1,
+                                                            warmup=0, autotune_every=32, per_bundle_arm=False,
+                                                            refine_full_list=False)
         line["gpu_launches_note"] = ("gpu_launches counts the timed FP64 renders; the samples report their own "
                                      "launch counts")
     if rank == 0:

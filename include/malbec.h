@@ -113,9 +113,9 @@ typedef struct {
  *                            p = g u, H = g^{ab} p_a p_b / 2 (Sec. 2, eq. Ham):
  *                            the paper's own form; p_t and p_ph (-E and L_z)
  *                            stay exactly constant.  FP64 and FP32_MIXED
- *                            (same FP64 zones); malbec_trace, malbec_trace_noalloc
- *                            and malbec_trace_camera only (MALBEC_EINVAL for
- *                            bundles and server jobs).
+ *                            (same FP64 zones); every entry point (bundles:
+ *                            one persistent launch per (form, method) class;
+ *                            servers: one class per server).
  *   MALBEC_FORM_ADM          (2) the same canonical equations with H written
  *                            through the lapse alpha, shift beta^ph and
  *                            spatial metric gamma_ij of the 3+1 line element
@@ -152,8 +152,8 @@ typedef struct {
  *                         stage points, as for RK4), escape on accepted
  *                         steps.  Any form (in the canonical forms p_t and
  *                         p_ph stay exactly constant, as with RK4).  Requires
- *                         atol > 0, rtol >= 0 and MALBEC_FP64; malbec_trace,
- *                         malbec_trace_noalloc and malbec_trace_camera only.
+ *                         atol > 0, rtol >= 0 and MALBEC_FP64; every entry
+ *                         point (bundles and servers as for the forms).
  * rtol, atol: the tolerances of MALBEC_METHOD_DOPRI5 (ignored by RK4). */
 #define MALBEC_FORM_GEODESIC 0
 #define MALBEC_FORM_HAMILTONIAN 1
@@ -415,10 +415,12 @@ typedef struct {
  * layout of an n x 1 camera (fate, steps, theta, phi of n pixels). */
 size_t malbec_bundle_out_bytes(const malbec_bundle* b, malbec_precision prec);
 
-/* Trace `count` bundles (host array) in one launch on `stream`.  Every
- * bundle is validated as malbec_trace / malbec_trace_camera would
- * (MALBEC_EINVAL before anything is enqueued).  Scratch (job table, counters)
- * comes from the stream-ordered allocator. */
+/* Trace `count` bundles (host array) in one launch on `stream` -- one
+ * persistent launch per class of (term.form, term.method) present, one after
+ * the other, each kernel specialised for its class (a table of one class, the
+ * usual case, is one launch).  Every bundle is validated as malbec_trace /
+ * malbec_trace_camera would (MALBEC_EINVAL before anything is enqueued).
+ * Scratch (job table, counters) comes from the stream-ordered allocator. */
 int malbec_trace_bundles(const malbec_bundle* bundles, uint32_t count, malbec_precision prec,
                          malbec_stream stream);
 
@@ -468,6 +470,8 @@ typedef struct {
   uint32_t max_pending;   /* queued jobs beyond that, >= 1 */
   malbec_precision precision;
   double idle_timeout_s;  /* kernel exit after this long without work, > 0 */
+  uint32_t form;          /* MALBEC_FORM_* of every job of this server (0: geodesic) */
+  uint32_t method;        /* MALBEC_METHOD_* of every job (DOPRI5: FP64 servers only) */
 } malbec_server_config;
 
 typedef struct {
@@ -480,7 +484,10 @@ typedef struct {
 int malbec_server_create(const malbec_server_config* cfg, malbec_server** server);
 int malbec_server_destroy(malbec_server* server);
 /* Non-blocking.  `job->out` is ignored.  STATES jobs read `ics` while they
- * run: keep it valid until the job is done. */
+ * run: keep it valid until the job is done.  job->term.form and
+ * job->term.method must be the server's (MALBEC_EINVAL otherwise): one server
+ * runs one class of equations and integrator, its resident kernel
+ * specialised for it; each job keeps its own tolerances. */
 int malbec_submit(malbec_server* server, const malbec_bundle* job, uint64_t* job_id);
 /* Non-blocking: *done = 1 once every ray of the job has finished. */
 int malbec_poll(malbec_server* server, uint64_t job_id, int* done);

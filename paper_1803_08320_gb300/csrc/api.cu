@@ -103,13 +103,18 @@ int choose_shape_cfg(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, c
   int tpb = 128;
   if (warps_needed < (uint64_t)sms * 4) tpb = 32;
   if (cfg.threads_per_block) tpb = (int)cfg.threads_per_block;
-  int per_sm = trace_max_blocks_per_sm(kerr, mixed, src, sink, tpb);
+  // the exchange as launch_trace will decide it: off for whole-image cameras
+  // unless asked for
+  const bool banks = mixed && (cfg.exchange ? cfg.exchange == 1 : src != kSrcCamera);
+  int per_sm = trace_max_blocks_per_sm(kerr, mixed, src, sink, banks, tpb);
   if (per_sm <= 0) per_sm = 1;
   // Resident warps per SM.  FP64: one warp per SM sub-partition already
   // saturates the FP64 unit (it costs the same per warp instruction whatever
   // the number of active lanes), and more warps only slow the longest rays,
-  // which set the end of the launch.  FP32_MIXED: two per sub-partition.
-  const int target_warps = mixed ? 8 : 4;
+  // which set the end of the launch.  FP32_MIXED: two per sub-partition,
+  // three for whole-image cameras (their kernels are held to 168 registers
+  // for it; latency-bound with two: 1024^2 render 9.4-9.7 ms against 11.0).
+  const int target_warps = mixed ? (src == kSrcCamera ? 12 : 8) : 4;
   int want = target_warps / (tpb / 32);
   if (want < 1) want = 1;
   if (cfg.blocks_per_sm) want = (int)cfg.blocks_per_sm;

@@ -37,12 +37,12 @@ CameraFields camera_fields(uint64_t n) {
 
 int validate(const malbec_bundle& b, malbec_precision prec) {
   if (b.n == 0 || !b.out || ((uintptr_t)b.out & 255u) != 0) return MALBEC_EINVAL;
-  // job tables: geodesic form, classical RK4
-  if (b.term.form != MALBEC_FORM_GEODESIC || b.term.method != MALBEC_METHOD_RK4) return MALBEC_EINVAL;
   const malbec_metric m = {b.M, b.a, nullptr};
   int rc = check_metric(m);
   if (rc) return rc;
-  rc = check_term(b.term, m);
+  rc = check_term(b.term, m);  // form and method included
+  if (rc) return rc;
+  rc = check_method_precision(b.term, prec);
   if (rc) return rc;
   if (b.kind == MALBEC_BUNDLE_CAMERA) {
     rc = check_camera_desc(m, &b.camera, &b.term);
@@ -79,6 +79,10 @@ void fill_job_desc(const malbec_bundle& b, malbec_precision prec, void* out, uin
   J->dl = b.term.dl;
   J->dl_r_scale = b.term.dl_r_scale;
   J->seed = b.seed;
+  J->form = b.term.form;
+  J->method = b.term.method;
+  J->rtol = b.term.rtol;
+  J->atol = b.term.atol;
   J->ics = b.ics;
   char* o = static_cast<char*>(out);
   if (b.kind == MALBEC_BUNDLE_CAMERA) {
@@ -104,8 +108,18 @@ void fill_job_desc(const malbec_bundle& b, malbec_precision prec, void* out, uin
 
 namespace {
 
+// The class of a job: its (form, method); one persistent launch runs the jobs
+// of one class (the kernel is specialised for its equations and integrator).
+uint32_t job_class(const JobDesc& J) { return J.form * 2u + J.method; }
+
+// A class's run of the order array: jobs order[first .. first + count - 1].
+struct ClassRun {
+  uint32_t form, method, first, count;
+  uint64_t rays;
+};
+
 int build_jobs(const malbec_bundle* bundles, uint32_t count, malbec_precision prec, std::vector<JobDesc>& jobs,
-               std::vector<uint32_t>& order, uint64_t* total_rays) {
+               std::vector<uint32_t>& order, std::vector<ClassRun>& runs, uint64_t* total_rays) {
   if (!bundles || count == 0) return MALBEC_EINVAL;
   jobs.assign(count, JobDesc());
   uint64_t total = 0;
@@ -114,51 +128,32 @@ int build_jobs(const malbec_bundle* bundles, uint32_t count, malbec_precision pr
     const malbec_bundle& b = bundles[i];
     int rc = validate(b, prec);
     if (rc) return rc;
-    JobDesc& J = jobs[i];
-    memset(&J, 0, sizeof(J));
-    J.kind = b.kind;
-    J.cap = b.term.n_steps_cap;
-    J.n = b.n;
-    J.M = b.M;
-    J.a = b.a;
-    J.eps_hor = b.term.eps_hor;
-    J.r_esc = b.term.r_esc;
-    J.dl = b.term.dl;
-    J.dl_r_scale = b.term.dl_r_scale;
-    J.seed = b.seed;
-    J.ics = b.ics;
-    char* o = static_cast<char*>(b.out);
-    if (b.kind == MALBEC_BUNDLE_CAMERA) {
-      J.cam = make_camera_const(b.M, b.a, b.camera);
-      const CameraFields f = camera_fields(b.n);
-      J.fate_out = reinterpret_cast<uint8_t*>(o + f.fate);
-      J.steps_out = reinterpret_cast<uint32_t*>(o + f.steps);
-      J.theta_out = reinterpret_cast<double*>(o + f.theta);
-      J.phi_out = reinterpret_cast<double*>(o + f.phi);
-      cost[i] = (double)b.n * std::min<double>(b.term.n_steps_cap, 300.0);
-    } else {
-      malbec_layout L;
-      rc = malbec_out_layout(MALBEC_OUT_FINAL, prec, b.n, b.term.n_steps_cap, 0, &L);
-      if (rc) return rc;
-      J.y_out = reinterpret_cast<double*>(o + L.y);
-      J.lambda_out = reinterpret_cast<double*>(o + L.lambda);
-      J.inv0_out = reinterpret_cast<double*>(o + L.inv0);
-      J.inv1_out = reinterpret_cast<double*>(o + L.inv1);
-      J.steps_out = reinterpret_cast<uint32_t*>(o + L.steps);
-      J.fate_out = reinterpret_cast<uint8_t*>(o + L.fate);
-      cost[i] = (double)b.n * (double)b.term.n_steps_cap;
-    }
+    fill_job_desc(b, prec, b.out, 0, &jobs[i], &cost[i]);
     total += b.n;
   }
+  // jobs grouped by class (form, method), costliest first within a class
   order.resize(count);
   std::iota(order.begin(), order.end(), 0u);
-  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return cost[x] > cost[y]; });
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+    const uint32_t cx = job_class(jobs[x]), cy = job_class(jobs[y]);
+    return cx != cy ? cx < cy : cost[x] > cost[y];
+  });
+  runs.clear();
+  for (uint32_t k = 0; k < count; ++k) {
+    const JobDesc& J = jobs[order[k]];
+    if (runs.empty() || job_class(jobs[order[runs.back().first]]) != job_class(J))
+      runs.push_back(ClassRun{J.form, J.method, k, 0u, 0ull});
+    runs.back().count++;
+    runs.back().rays += J.n;
+  }
   *total_rays = total;
   return MALBEC_OK;
 }
 
-// Scratch block: [jobs][order][counters][cursor], each 256-aligned; the
-// counters and the cursor (the tail from `ctr` on) are zeroed before a launch.
+// Scratch block: [jobs][order][counters][cursors], each 256-aligned; the
+// counters and the cursors (one per class run; the tail from `ctr` on) are
+// zeroed before a launch.
+constexpr uint32_t kMaxRuns = 8;  // classes: 3 forms x 2 methods
 struct BlockLayout {
   size_t jobs, ctr, order, cursor, total;
 };
@@ -172,22 +167,52 @@ BlockLayout block_layout(uint32_t count) {
   b.ctr = off;
   off = align256(off + count * sizeof(JobCounter));
   b.cursor = off;
-  off = align256(off + sizeof(unsigned int));
+  off = align256(off + kMaxRuns * sizeof(unsigned int));
   b.total = off;
   return b;
 }
 
-void fill_params(TraceParams& p, char* block, const BlockLayout& bl, uint32_t count, uint64_t total_rays) {
+// Parameters of the launch of class run `k`: its slice of the order array,
+// its own cursor, its equations and integrator.
+void fill_params(TraceParams& p, char* block, const BlockLayout& bl, const ClassRun& run, uint32_t k) {
   memset(&p, 0, sizeof(p));
   p.M = 1.0;
-  p.n = total_rays;
+  p.n = run.rays;
   p.stride = 1;
+  p.form = run.form;
+  p.method = run.method;
   p.jobs = reinterpret_cast<const JobDesc*>(block + bl.jobs);
   p.job_ctr = reinterpret_cast<JobCounter*>(block + bl.ctr);
-  p.job_order = reinterpret_cast<const uint32_t*>(block + bl.order);
-  p.n_jobs = count;
-  p.job_cursor = reinterpret_cast<unsigned int*>(block + bl.cursor);
+  p.job_order = reinterpret_cast<const uint32_t*>(block + bl.order) + run.first;
+  p.n_jobs = run.count;
+  p.job_cursor = reinterpret_cast<unsigned int*>(block + bl.cursor) + k;
   fill_zone(p);
+}
+
+// Enqueue the launches of every class run on `s` (after the counters and
+// cursors have been zeroed): one persistent launch per class, in class order.
+int launch_runs(char* block, const BlockLayout& bl, const std::vector<ClassRun>& runs, bool mixed,
+                const malbec_launch_config* cfg, cudaStream_t s, cudaError_t* err) {
+  *err = cudaSuccess;
+  for (uint32_t k = 0; k < (uint32_t)runs.size(); ++k) {
+    TraceParams p;
+    fill_params(p, block, bl, runs[k], k);
+    LaunchShape shape;
+    int refill_min = 1;
+    int rc = cfg ? choose_shape_cfg(true, mixed, kSrcJobs, kSinkJobs, runs[k].rays, *cfg, &shape, &refill_min)
+                 : choose_shape(true, mixed, kSrcJobs, kSinkJobs, runs[k].rays, &shape, &refill_min);
+    if (rc) return rc;
+    p.refill_min = refill_min;
+    if (cfg) {
+      if (cfg->zone_batch) p.zone_batch = (int)cfg->zone_batch;
+      if (cfg->zone_wait) p.zone_wait = (int)cfg->zone_wait;
+      if (cfg->exchange) p.exchange = cfg->exchange == 1 ? 1 : 0;
+      if (cfg->zone_wait_limit_us) p.zone_wait_ns = (uint64_t)cfg->zone_wait_limit_us * 1000ull;
+    }
+    *err = launch_trace(p, true, mixed, kSrcJobs, kSinkJobs, shape, s);
+    if (*err != cudaSuccess) return MALBEC_OK;
+  }
+  return MALBEC_OK;
 }
 
 }  // namespace
@@ -202,6 +227,7 @@ struct malbec_plan {
   bool mixed = false;
   void* block = nullptr;
   BlockLayout bl;
+  std::vector<ClassRun> runs;
   malbec_launch_config cfg = {0, 0, 0, 0, 0, 0, 0};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -212,33 +238,24 @@ namespace {
 // Record [zero the counters and the cursor] + [the persistent kernel] with
 // launch configuration `cfg` as the plan's graph.
 int record_plan(malbec_plan* P, const malbec_launch_config& cfg) {
-  TraceParams p;
-  fill_params(p, static_cast<char*>(P->block), P->bl, P->count, P->total_rays);
-  LaunchShape shape;
-  int refill_min = 1;
-  int rc = choose_shape_cfg(true, P->mixed, kSrcJobs, kSinkJobs, P->total_rays, cfg, &shape, &refill_min);
-  if (rc) return rc;
-  p.refill_min = refill_min;
-  if (cfg.zone_batch) p.zone_batch = (int)cfg.zone_batch;
-  if (cfg.zone_wait) p.zone_wait = (int)cfg.zone_wait;
-  if (cfg.exchange) p.exchange = cfg.exchange == 1 ? 1 : 0;
-  if (cfg.zone_wait_limit_us) p.zone_wait_ns = (uint64_t)cfg.zone_wait_limit_us * 1000ull;
   cudaStream_t s = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (e != cudaSuccess) return set_cuda_error(e);
   cudaGraph_t g = nullptr;
+  int rc = MALBEC_OK;
   e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     char* blk = static_cast<char*>(P->block);
     cudaError_t e1 = cudaMemsetAsync(blk + P->bl.ctr, 0, P->bl.total - P->bl.ctr, s);
-    cudaError_t e2 = e1 == cudaSuccess ? launch_trace(p, true, P->mixed, kSrcJobs, kSinkJobs, shape, s) : e1;
+    cudaError_t e2 = e1;
+    if (e1 == cudaSuccess) rc = launch_runs(blk, P->bl, P->runs, P->mixed, &cfg, s, &e2);
     e = cudaStreamEndCapture(s, &g);
     if (e2 != cudaSuccess) e = e2;
   }
   cudaStreamDestroy(s);
-  if (e != cudaSuccess) {
+  if (rc != MALBEC_OK || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
-    return set_cuda_error(e);
+    return rc != MALBEC_OK ? rc : set_cuda_error(e);
   }
   cudaGraphExec_t x = nullptr;
   e = cudaGraphInstantiate(&x, g, 0);
@@ -267,8 +284,9 @@ size_t malbec_bundle_out_bytes(const malbec_bundle* b, malbec_precision prec) {
 int malbec_trace_bundles(const malbec_bundle* bundles, uint32_t count, malbec_precision prec, malbec_stream stream) {
   std::vector<JobDesc> jobs;
   std::vector<uint32_t> order;
+  std::vector<ClassRun> runs;
   uint64_t total = 0;
-  int rc = build_jobs(bundles, count, prec, jobs, order, &total);
+  int rc = build_jobs(bundles, count, prec, jobs, order, runs, &total);
   if (rc) return rc;
   const bool mixed = prec == MALBEC_FP32_MIXED;
   const BlockLayout bl = block_layout(count);
@@ -281,17 +299,7 @@ int malbec_trace_bundles(const malbec_bundle* bundles, uint32_t count, malbec_pr
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(blk + bl.order, order.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(blk + bl.ctr, 0, bl.total - bl.ctr, s);
-  if (e == cudaSuccess) {
-    TraceParams p;
-    fill_params(p, blk, bl, count, total);
-    LaunchShape shape;
-    int refill_min = 1;
-    rc = choose_shape(true, mixed, kSrcJobs, kSinkJobs, total, &shape, &refill_min);
-    if (rc == MALBEC_OK) {
-      p.refill_min = refill_min;
-      e = launch_trace(p, true, mixed, kSrcJobs, kSinkJobs, shape, s);
-    }
-  }
+  if (e == cudaSuccess) rc = launch_runs(blk, bl, runs, mixed, nullptr, s, &e);
   cudaError_t e2 = cudaFreeAsync(block, s);
   if (rc) return rc;
   if (e != cudaSuccess) return set_cuda_error(e);
@@ -304,14 +312,16 @@ int malbec_plan_create(const malbec_bundle* bundles, uint32_t count, malbec_prec
   *plan = nullptr;
   std::vector<JobDesc> jobs;
   std::vector<uint32_t> order;
+  std::vector<ClassRun> runs;
   uint64_t total = 0;
-  int rc = build_jobs(bundles, count, prec, jobs, order, &total);
+  int rc = build_jobs(bundles, count, prec, jobs, order, runs, &total);
   if (rc) return rc;
   malbec_plan* P = new malbec_plan();
   cudaGetDevice(&P->device);
   P->count = count;
   P->total_rays = total;
   P->mixed = prec == MALBEC_FP32_MIXED;
+  P->runs = runs;
   P->bl = block_layout(count);
   cudaError_t e = cudaMalloc(&P->block, P->bl.total);
   if (e != cudaSuccess) {

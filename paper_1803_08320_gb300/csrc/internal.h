@@ -28,6 +28,8 @@ struct JobDesc {
   uint64_t job_id;  // serving: the id whose slot this is (0 = empty)
   double M, a, eps_hor, r_esc, dl, dl_r_scale;
   uint64_t seed;
+  uint32_t form, method;  // MALBEC_FORM_*, MALBEC_METHOD_* (every job of a launch has the same)
+  double rtol, atol;      // MALBEC_METHOD_DOPRI5 tolerances of this job
   CameraConst cam;
   const double* ics;
   // outputs: FINAL layout (states, bound) or camera layout (camera)
@@ -113,7 +115,9 @@ struct LaunchShape {
 // trace.cu
 cudaError_t launch_trace(const TraceParams& p, bool kerr, bool mixed, Source src, Sink sink,
                          const LaunchShape& shape, cudaStream_t stream);
-int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, int threads_per_block);
+// resident blocks per SM of the geodesic RK4 kernel of (kerr, mixed, src,
+// sink), with (banks) or without the FP32_MIXED block ray exchange
+int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, bool banks, int threads_per_block);
 // total of the device-wide counter of zone-warp waits that ran out (current device)
 cudaError_t read_wait_timeouts(unsigned long long* total);
 

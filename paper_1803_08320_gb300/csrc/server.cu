@@ -113,6 +113,8 @@ int launch_kernel(malbec_server* S) {
   p.park = S->d_park;
   p.max_active = S->cfg.max_active;
   p.idle_ns = (uint64_t)(S->cfg.idle_timeout_s * 1e9);
+  p.form = S->cfg.form;
+  p.method = S->cfg.method;
   fill_zone(p);
   const bool mixed = S->cfg.precision == MALBEC_FP32_MIXED;
   LaunchShape shape;
@@ -198,6 +200,10 @@ int malbec_server_create(const malbec_server_config* cfg, malbec_server** server
       !(cfg->idle_timeout_s > 0.0) || !isfinite(cfg->idle_timeout_s) ||
       (cfg->precision != MALBEC_FP64 && cfg->precision != MALBEC_FP32_MIXED))
     return MALBEC_EINVAL;
+  // the class of jobs this server runs: any form; Dormand-Prince in FP64 only
+  if (cfg->form > MALBEC_FORM_ADM || cfg->method > MALBEC_METHOD_DOPRI5 ||
+      (cfg->method == MALBEC_METHOD_DOPRI5 && cfg->precision != MALBEC_FP64))
+    return MALBEC_EINVAL;
   malbec_server* S = new malbec_server();
   S->cfg = *cfg;
   memset(&S->stats, 0, sizeof(S->stats));
@@ -271,6 +277,8 @@ int malbec_server_destroy(malbec_server* S) {
 
 int malbec_submit(malbec_server* S, const malbec_bundle* job, uint64_t* job_id) {
   if (!S || !job || !job_id) return MALBEC_EINVAL;
+  // a job of another class than the server's (form, method) is refused
+  if (job->term.form != S->cfg.form || job->term.method != S->cfg.method) return MALBEC_EINVAL;
   int rc = validate_job(*job, S->cfg.precision);
   if (rc) return rc;
   const size_t bytes = malbec_bundle_out_bytes(job, S->cfg.precision);

@@ -389,19 +389,23 @@ __device__ __forceinline__ void to_velocity(double M, double a, const double z[8
 }
 
 // Launch bounds: at most kMaxTPB threads per block, one block per SM
-// guaranteed.  The kernel runs one to eight warps per SM (see choose_shape),
-// so the register budget is not the occupancy limit; without the
-// minimum-blocks argument the compiler gives every instantiation fewer
-// registers (the FP32_MIXED camera kernel 146 instead of 190, and 1.9x slower:
-// 20.5 against 10.8 ms per 1024^2 render; some request-loop instantiations
-// were capped at 128 and spilled).  The one exception is the FP32_MIXED
-// job-table kernel with the block ray exchange, whose autotuned shape is three
-// 128-thread blocks per SM: it is held to 168 registers (3 x 128 x 168 <=
-// 65536; with 176 registers it ran on two blocks per SM, and the 4096 uneven
-// bundles took 32.7 s against 27.4 s).
+// guaranteed.  The kernel runs one to twelve warps per SM (see choose_shape),
+// and the register budget is left to the compiler; without the
+// minimum-blocks argument it gives every instantiation fewer registers (the
+// FP32_MIXED camera kernel 146 instead of 190, and 1.9x slower: 20.5 against
+// 10.8 ms per 1024^2 render; some request-loop instantiations were capped at
+// 128 and spilled).  Two exceptions are held to 168 registers, so that three
+// 128-thread blocks fit an SM (3 x 128 x 168 <= 65536): the FP32_MIXED
+// job-table kernel with the block ray exchange, whose autotuned shape is
+// three blocks per SM (with 176 registers it ran on two, and the 4096 uneven
+// bundles took 32.7 s against 27.4 s), and the FP32_MIXED whole-image camera
+// kernels, which are latency-bound with two warps per SM sub-partition (8 B
+// of spills at 168; 1024^2 render 9.4-9.7 ms on three blocks per SM against
+// 11.0 ms on two with 194 registers; at 128 registers, four blocks per SM:
+// 13.8 ms).
 template <bool kMixed, int kSrc, bool kBanks>
 constexpr int trace_reg_cap() {
-  return (kMixed && kBanks && kSrc == kSrcJobs) ? 168 : 255;
+  return (kMixed && kBanks && kSrc == kSrcJobs) || (kMixed && !kBanks && kSrc == kSrcCamera) ? 168 : 255;
 }
 
 template <bool kKerr, bool kMixed, int kSrc, int kSink, bool kBanks, int kForm, int kMethod>
@@ -419,6 +423,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
   // Step rule and termination of the lane's ray: uniform, except for rays of
   // a job table, which carry their job's values.
   double M = p.M, dl = p.dl, dl_scale = p.dl_r_scale, r_esc = p.r_esc, eps_hor = p.eps_hor;
+  double rtol = p.rtol, atol = p.atol;
   uint32_t cap = p.cap;
   // FP32-path constants: fixed step as a float pair, 1/6 as a float pair
   float h_fix, h6_fix_h, h6_fix_l, scale_f, r_esc_f;
@@ -438,11 +443,6 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
   BH<double> bh64 = make_bh<double>(M, p.a);
   BH<float> bh32 = make_bh<float>(M, p.a);
   int zone_waited = 0;
-  // fate of a ended ray whose end-of-ray work is deferred (0: none); the
-  // request loop finishes every ray at once (completion latency), the other
-  // sources once refill_min lanes wait (they are refilled together anyway)
-  int pending = 0;
-  const int flush_min = kSrc == kSrcServe ? 1 : p.refill_min;
   unsigned long long idle_since = 0ull, nap_since = 0ull;
   int claim_backoff = 0;
   bool active = false, drained = false, parked = false;
@@ -577,84 +577,8 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
     return leave != 0;
   };
 
-  // End of a ray (its fate in `pending`): back to FP64 (x, u), the end
-  // invariants and the validity flag, the outputs, the job's completion.
-  auto finish_ray = [&]() {
-    int fate = pending;
-    if (kMixed) {
-      flush_lam();
-#pragma unroll
-      for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
-    }
-    if constexpr (kHam) {
-      // back to (x, u) for the outputs and the invariants
-      double u[4];
-      to_velocity<kForm>(M, a, y, u);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) y[4 + c] = u[c];
-    }
-    // the end invariants (FP64) and the validity flag
-    double inv1[4];
-    invariants64(M, a, y, inv1);
-    if ((fate == MALBEC_FATE_ESCAPED || fate == MALBEC_FATE_CAPPED) && fabs(inv1[3] - n0) > drift_lim)
-      fate |= MALBEC_FATE_DRIFTED;
-    if (kSink == kSinkJobs) {
-      const JobDesc J = load_job(&p.jobs[job]);
-      if (J.kind == MALBEC_BUNDLE_CAMERA) {
-        J.fate_out[id] = (uint8_t)fate;
-        J.steps_out[id] = nst;
-        J.theta_out[id] = y[2];
-        J.phi_out[id] = y[3];
-      } else {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) J.y_out[(size_t)c * J.n + id] = y[c];
-        J.lambda_out[id] = lam;
-        J.steps_out[id] = nst;
-        J.fate_out[id] = (uint8_t)fate;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) J.inv1_out[(size_t)c * J.n + id] = inv1[c];
-      }
-      // this ray's outputs are visible device-wide before it is counted
-      __threadfence();
-      const unsigned long long finished = atomicAdd(&p.job_ctr[job].done, 1ull) + 1ull;
-      if (kSrc == kSrcServe && finished == J.n) {
-        // last ray of the job: every output is visible, tell the host
-        __threadfence_system();
-        p.done_flags[job] = J.job_id;
-      }
-    } else if (kSink == kSinkCamera) {
-      p.fate_out[id] = (uint8_t)fate;
-      p.steps_out[id] = nst;
-      p.theta_out[id] = y[2];
-      p.phi_out[id] = y[3];
-    } else {
-#pragma unroll
-      for (int c = 0; c < 8; ++c) p.y_out[(size_t)c * p.n + id] = y[c];
-      p.lambda_out[id] = lam;
-      p.steps_out[id] = nst;
-      p.fate_out[id] = (uint8_t)fate;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) p.inv1_out[(size_t)c * p.n + id] = inv1[c];
-      if (kSink == kSinkStrided) store_nan_samples<kMixed>(p, id, (uint64_t)nst / p.stride + 1);
-    }
-    pending = 0;
-  };
-
   while (true) {
-    // ---- deferred sinks: the end-of-ray work of lanes whose rays ended (FP64
-    // invariants and flag, output writes) runs once `flush_min` of them wait
-    // or no ray of the warp is still running, so that this FP64 work runs on
-    // many lanes at once instead of one lane at a time with its warp waiting
-    // (an FP64 warp instruction costs the same with 1 active lane as with 32)
-    {
-      const unsigned pend = __ballot_sync(kFull, pending != 0);
-      if (pend != 0u) {
-        const unsigned run = __ballot_sync(kFull, active);
-        if ((__popc(pend) >= flush_min || run == 0u) && pending != 0) finish_ray();
-      }
-    }
-    // lanes that are busy: running a ray or holding one whose end is deferred
-    unsigned act = __ballot_sync(kFull, active || pending != 0);
+    unsigned act = __ballot_sync(kFull, active);
     if constexpr (kBanks) {
       if (use_banks) {
         if (zone_warp) {
@@ -690,7 +614,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
               shared_store(&banks.n_fp32, nf);
             }
             warp_unlock(&banks.lock, lane);
-            act = __ballot_sync(kFull, active || pending != 0);
+            act = __ballot_sync(kFull, active);
           }
         } else if (act != kFull && warp_peek(&banks.n_fp32, lane) > 0 && warp_lock(&banks.lock, lane)) {
           // ---- other warps: rays the zone warp handed back go first
@@ -703,7 +627,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
           if (((free_lanes >> lane) & 1u) && (int)frank < take) load_ray(banks.fp32, nf - 1 - (int)frank);
           if (lane == 0) shared_store(&banks.n_fp32, nf - take);
           warp_unlock(&banks.lock, lane);
-          act = __ballot_sync(kFull, active || pending != 0);
+          act = __ballot_sync(kFull, active);
         }
       }
     }
@@ -718,7 +642,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
         base = __shfl_sync(kFull, base, 0);
         if (base + (unsigned long long)idle >= p.n) drained = true;
         const unsigned long long my = base + __popc(~act & lt_mask);
-        if (!((act >> lane) & 1u) && my < p.n) {
+        if (!active && my < p.n) {
           id = kSrc == kSrcCamera ? camera_claim_pixel(p.cam, my) : my;
           got = true;
         }
@@ -872,6 +796,8 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
           r_esc = J.r_esc;
           eps_hor = J.eps_hor;
           cap = J.cap;
+          rtol = J.rtol;
+          atol = J.atol;
           step_consts(dl, dl_scale, r_esc, h_fix, h6_fix_h, h6_fix_l, scale_f, r_esc_f);
           if (J.kind == MALBEC_BUNDLE_CAMERA) {
             camera_state(J.cam, a, id, y);
@@ -1028,7 +954,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
         escaped = false;
         bool accept = captured || !finite;
         if (!accept) {
-          const double err = dopri5_norm(y, y5, e, p.rtol, p.atol);
+          const double err = dopri5_norm(y, y5, e, rtol, atol);
           accept = err <= 1.0;
           h_next = h * dopri5_factor(err, accept, after_reject);
           after_reject = !accept;
@@ -1131,9 +1057,62 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
     }
 
     if (fate != 0) {
-      // the lane's ray is done; its end-of-ray work waits in `pending`
-      // (deferred sinks, at the top of the loop)
-      pending = fate;
+      if (kMixed) {
+        flush_lam();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
+      }
+      if constexpr (kHam) {
+        // back to (x, u) for the outputs and the invariants
+        double u[4];
+        to_velocity<kForm>(M, a, y, u);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) y[4 + c] = u[c];
+      }
+      // the end invariants (FP64) and the validity flag
+      double inv1[4];
+      invariants64(M, a, y, inv1);
+      if ((fate == MALBEC_FATE_ESCAPED || fate == MALBEC_FATE_CAPPED) && fabs(inv1[3] - n0) > drift_lim)
+        fate |= MALBEC_FATE_DRIFTED;
+      if (kSink == kSinkJobs) {
+        const JobDesc J = load_job(&p.jobs[job]);
+        if (J.kind == MALBEC_BUNDLE_CAMERA) {
+          J.fate_out[id] = (uint8_t)fate;
+          J.steps_out[id] = nst;
+          J.theta_out[id] = y[2];
+          J.phi_out[id] = y[3];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) J.y_out[(size_t)c * J.n + id] = y[c];
+          J.lambda_out[id] = lam;
+          J.steps_out[id] = nst;
+          J.fate_out[id] = (uint8_t)fate;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) J.inv1_out[(size_t)c * J.n + id] = inv1[c];
+        }
+        // this ray's outputs are visible device-wide before it is counted
+        __threadfence();
+        const unsigned long long finished = atomicAdd(&p.job_ctr[job].done, 1ull) + 1ull;
+        if (kSrc == kSrcServe && finished == J.n) {
+          // last ray of the job: every output is visible, tell the host
+          __threadfence_system();
+          p.done_flags[job] = J.job_id;
+        }
+      } else if (kSink == kSinkCamera) {
+        p.fate_out[id] = (uint8_t)fate;
+        p.steps_out[id] = nst;
+        p.theta_out[id] = y[2];
+        p.phi_out[id] = y[3];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) p.y_out[(size_t)c * p.n + id] = y[c];
+        p.lambda_out[id] = lam;
+        p.steps_out[id] = nst;
+        p.fate_out[id] = (uint8_t)fate;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p.inv1_out[(size_t)c * p.n + id] = inv1[c];
+        if (kSink == kSinkStrided) store_nan_samples<kMixed>(p, id, (uint64_t)nst / p.stride + 1);
+      }
       active = false;
     }
   }
@@ -1150,7 +1129,7 @@ const void* kernel_ptr() {
 // none of its code).
 const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, int form, int method) {
   // Dormand-Prince 5(4): FP64, every form (the Kerr right-hand sides, a = 0
-  // included), state arrays and cameras
+  // included), every source
   if (method == MALBEC_METHOD_DOPRI5) {
     if (mixed) return nullptr;
 #define MALBEC_PICK_DP(F)                                                                  \
@@ -1161,6 +1140,10 @@ const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, int f
       return kernel_ptr<true, false, kSrcStates, kSinkStrided, false, F, MALBEC_METHOD_DOPRI5>(); \
     if (src == kSrcCamera && sink == kSinkCamera)                                          \
       return kernel_ptr<true, false, kSrcCamera, kSinkCamera, false, F, MALBEC_METHOD_DOPRI5>();  \
+    if (src == kSrcJobs && sink == kSinkJobs)                                              \
+      return kernel_ptr<true, false, kSrcJobs, kSinkJobs, false, F, MALBEC_METHOD_DOPRI5>();      \
+    if (src == kSrcServe && sink == kSinkJobs)                                             \
+      return kernel_ptr<true, false, kSrcServe, kSinkJobs, false, F, MALBEC_METHOD_DOPRI5>();     \
   }
     MALBEC_PICK_DP(MALBEC_FORM_GEODESIC)
     MALBEC_PICK_DP(MALBEC_FORM_HAMILTONIAN)
@@ -1169,7 +1152,7 @@ const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, int f
     return nullptr;
   }
   // canonical forms (Sec. 2, eq. Ham, with g of eq. kerr or of eq. ADM):
-  // state arrays and cameras
+  // every source
   if (form != MALBEC_FORM_GEODESIC) {
 #define MALBEC_PICK_HAM(F, S, T)                                                                   \
   if (form == F && src == S && sink == T) {                                                        \
@@ -1182,6 +1165,10 @@ const void* pick(bool kerr, bool mixed, Source src, Sink sink, bool banks, int f
     MALBEC_PICK_HAM(MALBEC_FORM_ADM, kSrcStates, kSinkFinal)
     MALBEC_PICK_HAM(MALBEC_FORM_ADM, kSrcStates, kSinkStrided)
     MALBEC_PICK_HAM(MALBEC_FORM_ADM, kSrcCamera, kSinkCamera)
+    MALBEC_PICK_HAM(MALBEC_FORM_HAMILTONIAN, kSrcJobs, kSinkJobs)
+    MALBEC_PICK_HAM(MALBEC_FORM_ADM, kSrcJobs, kSinkJobs)
+    MALBEC_PICK_HAM(MALBEC_FORM_HAMILTONIAN, kSrcServe, kSinkJobs)
+    MALBEC_PICK_HAM(MALBEC_FORM_ADM, kSrcServe, kSinkJobs)
 #undef MALBEC_PICK_HAM
     return nullptr;
   }
@@ -1216,8 +1203,8 @@ cudaError_t read_wait_timeouts(unsigned long long* total) {
   return cudaMemcpyFromSymbol(total, g_wait_timeouts, sizeof(unsigned long long));
 }
 
-int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, int threads_per_block) {
-  const void* k = pick(kerr, mixed, src, sink, mixed, MALBEC_FORM_GEODESIC, MALBEC_METHOD_RK4);  // the larger of the two
+int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, bool banks, int threads_per_block) {
+  const void* k = pick(kerr, mixed, src, sink, mixed && banks, MALBEC_FORM_GEODESIC, MALBEC_METHOD_RK4);
   if (!k) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads_per_block, 0) != cudaSuccess) return 0;

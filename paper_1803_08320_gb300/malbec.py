@@ -76,7 +76,7 @@ class LaunchConfig(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget", _SZ), ("max_active", _U32), ("max_pending", _U32), ("precision", ctypes.c_int),
-                ("idle_timeout_s", _D)]
+                ("idle_timeout_s", _D), ("form", _U32), ("method", _U32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -440,10 +440,13 @@ class Server:
     """Continuous-batching request loop (malbec_server_*)."""
 
     def __init__(self, hbm_budget: int = 150 * 10**9, max_active: int = 1024, max_pending: int = 100_000,
-                 precision="fp32_mixed", idle_timeout_s: float = 0.002):
+                 precision="fp32_mixed", idle_timeout_s: float = 0.002, form: int = FORM_GEODESIC,
+                 method: int = METHOD_RK4):
+        """form, method: the class of every job of this server (a job's
+        term.form and term.method must match)."""
         self.precision = precision
         cfg = ServerConfig(int(hbm_budget), int(max_active), int(max_pending), _prec(precision),
-                           float(idle_timeout_s))
+                           float(idle_timeout_s), int(form), int(method))
         self._h = _VP()
         _check(lib().malbec_server_create(ctypes.byref(cfg), ctypes.byref(self._h)), "malbec_server_create")
         self._specs = {}

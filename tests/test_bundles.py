@@ -44,9 +44,17 @@ def test_bundle_validation_on_host(mb):
     unaligned = mb.make_bundle(mb.BUNDLE_BOUND, 10, 1.0, 0.5, t)
     unaligned.out = ctypes.c_void_p(300)
     lib = mb.lib()
-    for b in (bad_kind, bad_spin, no_ics, too_many, unaligned):
+    bad_form = mb.make_bundle(mb.BUNDLE_BOUND, 10, 1.0, 0.5, _term(eps_hor=0.01, r_esc=1100.0, n_steps_cap=100,
+                                                                    dl=0.02, form=3), seed=3)
+    bad_form.out = fake
+    for b in (bad_kind, bad_spin, no_ics, too_many, unaligned, bad_form):
         arr = mb._bundle_array([good, b])
         assert lib.malbec_trace_bundles(arr, 2, mb.FP64, None) == mb.EINVAL
+    # Dormand-Prince runs in FP64 only
+    dp = mb.make_bundle(mb.BUNDLE_BOUND, 10, 1.0, 0.5, _term(eps_hor=0.01, r_esc=1100.0, n_steps_cap=100, dl=0.02,
+                                                             method=1, rtol=1e-9, atol=1e-9), seed=3)
+    dp.out = fake
+    assert lib.malbec_trace_bundles(mb._bundle_array([dp]), 1, mb.FP32_MIXED, None) == mb.EINVAL
     assert lib.malbec_trace_bundles(mb._bundle_array([good]), 0, mb.FP64, None) == mb.EINVAL
     assert lib.malbec_bundle_out_bytes(ctypes.byref(good), mb.FP64) == mb.out_layout(mb.OUT_FINAL, "fp64", 10, 100,
                                                                                     0).total
@@ -176,3 +184,93 @@ def test_bound_bundle_matches_oracle(mb, orc):
     ref = orc.trace_many(1.0, a, ys, oracle_term(orc, t))
     np.testing.assert_allclose(v["inv0"].cpu().numpy(), ref["inv0"], rtol=1e-11, atol=1e-12)
     assert_states_close(v["y"].cpu().numpy(), ref["y"], rtol=RTOL)
+
+
+CLASSES = [(0, 0), (1, 0), (2, 0), (0, 1), (1, 1), (2, 1)]  # (form, method): RK4 and Dormand-Prince, each form
+
+
+def _with_class(mb, t, form, method):
+    """The bundle's term in class (form, method); Dormand-Prince at tolerance
+    1e-9 (its first step is the RK4 step: dl, or dl_r_scale r0)."""
+    return mb.term_from(t, form=form, method=method, rtol=1e-9 if method else 0.0, atol=1e-9 if method else 0.0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_bundles_of_every_form_and_method_equal_single_launches(mb, precision):
+    """A job table mixing the equations (geodesic form, canonical forms
+    through eq. kerr and eq. ADM) and the integrators (RK4, Dormand-Prince
+    5(4), FP64 only): one persistent launch per class, and every bundle's
+    results equal those of tracing it alone with the same term -- bitwise in
+    FP64; in FP32_MIXED (RK4 only) fates and steps on >= 99.5% of rays and
+    states within 1e-6 on >= 99% of those."""
+    import torch
+
+    classes = CLASSES if precision == "fp64" else [c for c in CLASSES if c[1] == 0]
+    bundles, singles = _mixed_bundles(mb, torch, seed=5, count=18)
+    for i, b in enumerate(bundles):
+        form, method = classes[i % len(classes)]
+        t = _with_class(mb, singles[i][2], form, method)
+        b.term = t.c()
+        singles[i] = (singles[i][0], singles[i][1], t, singles[i][3], singles[i][4])
+    views = mb.attach_outputs(bundles, precision)
+    mb.trace_bundles(bundles, precision)
+    torch.cuda.synchronize()
+    for b, spec, v in zip(bundles, singles, views):
+        ref = _single(mb, torch, spec, int(b.n), precision)
+        torch.cuda.synchronize()
+        keys = ("fate", "steps", "theta", "phi") if spec[0] == "camera" else ("y", "inv0", "inv1", "steps", "fate",
+                                                                             "lambda")
+        cls = (spec[2].form, spec[2].method)
+        if precision == "fp64":
+            for k in keys:
+                x, y = v[k].cpu().numpy(), ref[k].cpu().numpy()
+                assert np.array_equal(np.isnan(x), np.isnan(y)), (spec[0], cls, k)
+                assert np.array_equal(np.nan_to_num(x), np.nan_to_num(y)), (spec[0], cls, k)
+        else:
+            f_ok = (v["fate"] == ref["fate"]) & (v["steps"] == ref["steps"])
+            assert f_ok.float().mean().item() >= 0.995, (spec[0], cls)
+            for k in keys:
+                if k in ("fate", "steps"):
+                    continue
+                x, y = v[k].cpu().numpy(), ref[k].cpu().numpy()
+                sel = f_ok.cpu().numpy()
+                x, y = (x[..., sel], y[..., sel])
+                fin = np.isfinite(x) & np.isfinite(y) & (np.abs(y) < 1e3)
+                close = np.abs(x[fin] - y[fin]) <= 1e-6 * np.maximum(np.abs(y[fin]), 1.0)
+                assert close.size == 0 or close.mean() >= 0.99, (spec[0], cls, k, close.mean())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form,method", [(1, 0), (2, 0), (0, 1), (2, 1)])
+def test_bound_bundle_of_another_class_matches_oracle(mb, orc, form, method):
+    """A BOUND bundle in the canonical forms (eq. Ham through eq. kerr, and
+    through eq. ADM) or with Dormand-Prince (tolerance 1e-9), in a table with
+    a geodesic RK4 bundle: its states within 1e-9 of the oracle's same form
+    and method (Dormand-Prince: with the oracle's attempts and lambda, on the
+    orbits its rounding-sensitivity test keeps)."""
+    import torch
+
+    from test_gpu_dopri5 import SENS_MAX, oracle_rounding_sensitivity
+
+    a, seed, n = 0.73, 987654321, 64
+    t = _with_class(mb, _term(eps_hor=0.01, r_esc=1100.0, n_steps_cap=400, dl=0.02), form, method)
+    b = mb.make_bundle(mb.BUNDLE_BOUND, n, 1.0, a, t, seed=seed)
+    other = mb.make_bundle(mb.BUNDLE_BOUND, 32, 1.0, 0.3, _term(eps_hor=0.01, r_esc=1100.0, n_steps_cap=300, dl=0.02),
+                           seed=5)
+    views = mb.attach_outputs([b, other], "fp64")
+    mb.trace_bundles([b, other], "fp64")
+    torch.cuda.synchronize()
+    v = views[0]
+    ys, _, _ = orc.bound_samples(1.0, a, seed, np.arange(n), spin_fixed=True)
+    if method == 0:
+        ref = orc.trace_many(1.0, a, ys, oracle_term(orc, t))
+        good = np.ones(n, dtype=bool)
+    else:
+        ref, sens = oracle_rounding_sensitivity(orc, 1.0, a, ys, oracle_term(orc, t))
+        good = sens <= SENS_MAX
+        assert good.mean() >= 0.9
+        assert np.array_equal(v["steps"].cpu().numpy()[good].astype(np.uint32), ref["steps"][good])
+        assert np.array_equal(v["lambda"].cpu().numpy()[good], ref["lambda"][good])
+    assert np.array_equal(v["fate"].cpu().numpy()[good], ref["fate"][good])
+    assert_states_close(v["y"].cpu().numpy()[:, good], ref["y"][:, good], rtol=RTOL)

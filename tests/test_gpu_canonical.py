@@ -135,14 +135,6 @@ def test_canonical_agrees_with_geodesic_form(mb, W, form):
     assert np.median(rel.max(axis=0)) < 1e-7
 
 
-def test_canonical_rejects_job_tables(mb, form):
-    t = mb.Termination(eps_hor=0.01, r_esc=60.0, n_steps_cap=10, dl=0.05, form=form)
-    b = mb.make_bundle(mb.BUNDLE_BOUND, 4, 1.0, 0.5, t, seed=1)
-    with pytest.raises(mb.MalbecError):
-        mb.attach_outputs([b], "fp64")
-        mb.trace_bundles([b], "fp64")
-
-
 def test_mixed_canonical_conserves_E_and_Lz(mb, W, form):
     """FP32_MIXED in the canonical form keeps p_t and p_phi fixed as float
     pairs: E and L_z change only through the end conversions (< 1e-12), while

@@ -200,10 +200,13 @@ def test_unsupported_combinations_are_rejected(mb):
     ics[4] = 1.2
     with pytest.raises(mb.MalbecError):
         gpu_trace(mb, 1.0, 0.5, ics, dp_term(mb), precision="fp32_mixed")
+    # job tables and servers run Dormand-Prince in FP64 only
     b = mb.make_bundle(mb.BUNDLE_BOUND, 4, 1.0, 0.5, dp_term(mb), seed=1)
     with pytest.raises(mb.MalbecError):
-        mb.attach_outputs([b], "fp64")
-        mb.trace_bundles([b], "fp64")
+        mb.attach_outputs([b], "fp32_mixed")
+        mb.trace_bundles([b], "fp32_mixed")
+    with pytest.raises(mb.MalbecError):
+        mb.Server(hbm_budget=10**9, precision="fp32_mixed", method=mb.METHOD_DOPRI5)
 
 
 def test_noalloc_entry_point_gives_the_same_bits(mb, W):

@@ -24,28 +24,40 @@ def mb():
 
 
 def test_zone_warp_wait_runs_out_and_results_are_unchanged(mb):
+    import numpy as np
     import torch
 
-    from paper_1803_08320_gb300 import workloads as W
-
-    wl = W.bound()
-    # 128-thread blocks (the zone warp and three others), many rays per lane,
-    # so that zone warps run out of rays while their block-mates still run
-    ics, spins, _ = mb.ic_bound(wl.M, wl.a_max, wl.seed, 40_000)
-    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=1500, dl=0.02)
+    # 40,000 rays, one in 64 a long circular orbit outside every FP64 zone
+    # (r in [8, 12] M, equatorial: FP32 steps only), the others started
+    # inside the capture radius (they end after one step).  With 128-thread
+    # blocks (the zone warp and three others) and the exchange on, the zone
+    # warp of a block whose long orbits sit in other warps runs out of rays
+    # long before its block does.
+    a, n = 0.5, 40_000
+    rng = np.random.default_rng(17)
+    long_idx = np.arange(0, n, 64)
+    radii = rng.uniform(8.0, 12.0, len(long_idx))
+    circ = mb.ic_circular(1.0, a, radii)
+    ics = torch.zeros((8, n), dtype=torch.float64, device="cuda")
+    ics[1] = 1.5                    # inside (1 + eps) r_+ = 1.885 M
+    ics[2] = 1.0
+    ics[4] = 1.0
+    ics[:, torch.as_tensor(long_idx).cuda()] = circ
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=20_000, dl=0.02)
     mb.set_launch_config(threads_per_block=128, exchange=1)
-    ref = mb.trace(wl.M, 0.0, ics, t, precision="fp32_mixed", a_per_ray=spins)
+    ref = mb.trace(1.0, a, ics, t, precision="fp32_mixed")
     torch.cuda.synchronize()
     mb.wait_status()  # forget earlier expiries
     mb.set_launch_config(threads_per_block=128, exchange=1, zone_wait_limit_us=1)
-    got = mb.trace(wl.M, 0.0, ics, t, precision="fp32_mixed", a_per_ray=spins)
+    got = mb.trace(1.0, a, ics, t, precision="fp32_mixed")
     timed_out, total = mb.wait_status()
     mb.set_launch_config(reset=True)
     assert timed_out and total > 0
     for k in ("y", "inv1", "lambda"):
-        a, b = got[k], ref[k]
-        assert torch.equal(torch.isnan(a), torch.isnan(b)), k
-        assert torch.equal(torch.nan_to_num(a), torch.nan_to_num(b)), k
+        x, y = got[k], ref[k]
+        assert torch.equal(torch.isnan(x), torch.isnan(y)), k
+        assert torch.equal(torch.nan_to_num(x), torch.nan_to_num(y)), k
     assert torch.equal(got["fate"], ref["fate"]) and torch.equal(got["steps"], ref["steps"])
+    assert int((got["steps"] == t.n_steps_cap).sum().item()) == len(long_idx)
     # nothing ran out since: the status is back to OK
     assert mb.wait_status() == (False, total)

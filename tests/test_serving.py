@@ -26,7 +26,9 @@ def test_server_config_validation(mb):
                 mb.ServerConfig(10**9, 5000, 16, mb.FP64, 0.01),  # too many
                 mb.ServerConfig(10**9, 16, 0, mb.FP64, 0.01),
                 mb.ServerConfig(10**9, 16, 16, 7, 0.01),
-                mb.ServerConfig(10**9, 16, 16, mb.FP64, 0.0)):
+                mb.ServerConfig(10**9, 16, 16, mb.FP64, 0.0),
+                mb.ServerConfig(10**9, 16, 16, mb.FP64, 0.01, 3, 0),          # no such form
+                mb.ServerConfig(10**9, 16, 16, mb.FP32_MIXED, 0.01, 0, 1)):   # Dormand-Prince: FP64 only
         assert lib.malbec_server_create(ctypes.byref(cfg), ctypes.byref(h)) == mb.EINVAL
     assert lib.malbec_server_destroy(None) == mb.EINVAL
     assert lib.malbec_submit(None, None, None) == mb.EINVAL
@@ -47,10 +49,11 @@ def _jobs(mb, seed=1, count=12):
     return out
 
 
-def _serve(mb, jobs, precision, budget=2 * 10**9, timeout=60.0):
+def _serve(mb, jobs, precision, budget=2 * 10**9, timeout=60.0, form=0, method=0):
     import torch
 
-    srv = mb.Server(hbm_budget=budget, max_active=64, precision=precision, idle_timeout_s=0.002)
+    srv = mb.Server(hbm_budget=budget, max_active=64, precision=precision, idle_timeout_s=0.002, form=form,
+                    method=method)
     ids = [srv.submit(b) for b in jobs]
     done, t0 = set(), time.time()
     while len(done) < len(ids):
@@ -130,3 +133,65 @@ def test_admission_by_budget_and_pending_limit(mb):
     assert served == ids[:4]  # FIFO admission with a one-job budget
     assert srv.stats()["bytes_in_use"] == 0
     srv.close()
+
+
+def _in_class(mb, jobs, form, method):
+    """The same jobs in another class (form, method); Dormand-Prince at
+    tolerance 1e-9."""
+    for b in jobs:
+        t = mb.Termination(b.term.eps_hor, b.term.r_esc, b.term.n_steps_cap, b.term.dl, b.term.dl_r_scale, form,
+                           method, 1e-9 if method else 0.0, 1e-9 if method else 0.0)
+        b.term = t.c()
+    return jobs
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,form,method", [("fp32_mixed", 1, 0), ("fp32_mixed", 2, 0), ("fp64", 2, 0),
+                                                   ("fp64", 0, 1), ("fp64", 1, 1)])
+def test_server_of_another_class_alone_and_in_the_mix(mb, precision, form, method):
+    """A server runs one class of jobs (form, method): the canonical forms
+    (eq. Ham through eq. kerr and eq. ADM) and Dormand-Prince (FP64) are
+    served with the same guarantees -- each result bitwise the same alone and
+    in the mix, FP64 results equal to tracing the job alone with the bundle
+    launch -- and a job of another class is refused."""
+    import torch
+
+    jobs = _in_class(mb, _jobs(mb, seed=4, count=6), form, method)
+    mixed, stats = _serve(mb, jobs, precision, form=form, method=method)
+    assert stats["completed"] == len(jobs)
+    for j, b in enumerate(jobs):
+        alone, _ = _serve(mb, [b], precision, form=form, method=method)
+        keys = ("fate", "steps", "theta", "phi") if b.kind == mb.BUNDLE_CAMERA else ("fate", "steps", "y", "inv1")
+        for k in keys:
+            assert _same(mixed[j][k], alone[0][k]), (j, k)
+        if precision == "fp64":
+            (ref,) = mb.attach_outputs([b], "fp64")
+            mb.trace_bundles([b], "fp64")
+            torch.cuda.synchronize()
+            for k in keys:
+                assert _same(mixed[j][k], ref[k]), (j, k)
+    srv = mb.Server(hbm_budget=10**9, precision=precision, form=form, method=method)
+    other = _jobs(mb, seed=9, count=1)[0]  # geodesic RK4
+    if (form, method) != (0, 0):
+        with pytest.raises(mb.MalbecError):
+            srv.submit(other)
+    srv.close()
+
+
+@pytest.mark.gpu
+def test_canonical_server_job_matches_oracle(mb, orc):
+    """A BOUND job on an FP64 server of the canonical form through eq. ADM:
+    states within 1e-9 of the oracle's form 2."""
+    import torch
+
+    from test_gpu_parity import RTOL, assert_states_close, oracle_term
+
+    a, seed, n = 0.6, 4242, 48
+    t = mb.Termination(eps_hor=0.01, r_esc=1100.0, n_steps_cap=500, dl=0.02, form=2)
+    b = mb.make_bundle(mb.BUNDLE_BOUND, n, 1.0, a, t, seed=seed)
+    (out,), _ = _serve(mb, [b], "fp64", form=2)
+    torch.cuda.synchronize()
+    ys, _, _ = orc.bound_samples(1.0, a, seed, np.arange(n), spin_fixed=True)
+    ref = orc.trace_many(1.0, a, ys, oracle_term(orc, t))
+    assert np.array_equal(out["fate"].cpu().numpy(), ref["fate"])
+    assert_states_close(out["y"].cpu().numpy(), ref["y"], rtol=RTOL)
