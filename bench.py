@@ -1316,6 +1316,7 @@ def main():
                      "frac": achieved / peak64, "traffic": load_traffic("camera_fp64"),
                      "fp64_pipe_utilization": {
                          "pct_of_peak": load_traffic("camera_fp64", "fp64_pipe_pct_of_peak"),
+                         "fp64_instructions_per_rk4_step": load_traffic("camera_fp64", "fp64_instructions_per_step"),
                          "source": "ncu sm__inst_executed_pipe_fp64 of this kernel (512x512 case, committed "
                                    "summary of the current source); the FP64-peak criterion read as pipe "
                                    "utilisation, beside the algorithmic-flop fraction above"},
@@ -1334,6 +1335,8 @@ def main():
                        "speedup_vs_fp64": value32 / value, "fate_agreement_vs_fp64": agree, "fates": fates32,
                        "escaped_error_vs_fp64": err_stats(torch, dth, dph),
                        "roofline": {"bound": "alu", "peak": peak32, "unit": "GFLOP/s (FP32)",
+                                    "traffic": load_traffic("camera_mixed"),
+                                    "issue_active_pct": load_traffic("camera_mixed", "issue_active_pct"),
                                     "achieved_fp32_equiv": FLOPS_PER_STEP["kerr"] * steps32 /
                                     (statistics.mean(times32) / 1e3) / 1e9,
                                     "frac": FLOPS_PER_STEP["kerr"] * steps32 / (statistics.mean(times32) / 1e3)

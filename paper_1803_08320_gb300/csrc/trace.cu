@@ -48,12 +48,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-// (hi, lo) += d + d_err, renormalised so that hi = fl(hi + lo).
+// (hi, lo) += d + d_err, renormalised so that hi = fl(hi + lo): TwoSum of
+// hi + d (no order of magnitudes assumed), then the error terms folded in and
+// the pair renormalised with Fast2Sum, exact here because |e| (a rounding
+// error of s plus the small lo and d_err) never exceeds |s| -- the same
+// result as a second TwoSum in half the operations.
 __device__ __forceinline__ void comp_add(float& hi, float& lo, float d, float d_err) {
   float s, e;
   two_sum(hi, d, s, e);
   e += lo + d_err;
-  two_sum(s, e, hi, lo);
+  hi = s + e;
+  lo = e - (hi - s);
 }
 
 // Non-finite test on the exponent bits (integer pipe, no FP64 compare).
@@ -1023,7 +1028,9 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
           rmin = rk4_step_mixed<kKerr>(bh32, hf, h6h, h6l, hi, lo);
         captured = (hi[1] <= r_cap_f) | (rmin <= r_cap_f);
         escaped = hi[1] >= r_esc_f;
-        finite = finite8f(hi) & finite8f(lo);
+        // a non-finite lo word comes with a non-finite hi word (lo is the
+        // rounding error of hi's own sum), so the hi words decide
+        finite = finite8f(hi);
       }
       ++nst;
       if (kSink == kSinkStrided && (nst % p.stride) == 0) {
