@@ -59,43 +59,73 @@ __device__ __forceinline__ float recip<float>(float x) {
   return fmaf(y, fmaf(-x, y, 1.0f), y);
 }
 
-// sin and cos at an RK4 stage angle th = th0 + d, given s0 = sin th0 and
-// c0 = cos th0 of the step's start.  FP64 with |d| <= 1/4: the angle-addition
-// formulas with sin d and cos d - 1 from their Taylor series,
+// sin and cos at a stage angle th = th0 + c x (c x = d, the stage's offset
+// from the step's start angle th0), given s0 = sin th0 and c0 = cos th0.
+// FP64 with |d| < 1/4: the angle-addition formulas with sin d and cos d - 1
+// from their Taylor series,
 //   sin d = d - d^3/3! + ... - d^11/11!,  cos d - 1 = -d^2/2! + ... + d^12/12!
-// (the first omitted terms are below 1e-17 relative for |d| <= 1/4), so one
-// sincos serves the four stages of a step.  Otherwise, and in FP32: sincos of
-// th itself.
+// (the first omitted terms are below 1e-17 relative for |d| <= 1/4), and for
+// |d| < 2^-5 the shorter
+//   sin d = d - d^3/3! + d^5/5! - d^7/7!,  cos d - 1 = -d^2/2! + ... + d^8/8!
+// (first omitted terms below 1e-19 absolute there), so one sincos serves the
+// four stages of a step; th itself is formed only for the sincos taken when
+// |d| >= 1/4.  Otherwise, and in FP32: sincos of th = fma(c, x, th0).  The
+// tier is a per-lane choice on the bits of d, so a ray's result never depends
+// on the other rays of its warp.
 template <typename T>
-__device__ __forceinline__ void stage_trig(T s0, T c0, T d, T th, T* s, T* c) {
-  Trig<T>::sc(th, s, c);
+__device__ __forceinline__ void stage_trig(T s0, T c0, T c, T x, T th0, T* s, T* cs) {
+  Trig<T>::sc(fma(c, x, th0), s, cs);
 }
-// The range test |d| < 1/4 reads the exponent bits on the integer pipe (an
-// FP64 compare would take an issue of the FP64 unit, which costs as much as
-// an FMA there); sin th = s0 + c0 sin d + s0 (cos d - 1) and likewise cos th
-// are two FMAs each.
+// The range tests read the exponent bits on the integer pipe (an FP64 compare
+// would take an issue of the FP64 unit, which costs as much as an FMA there);
+// sin th = s0 + c0 sin d + s0 (cos d - 1) and likewise cos th are two FMAs
+// each.
 template <>
-__device__ __forceinline__ void stage_trig<double>(double s0, double c0, double d, double th, double* s,
-                                                   double* c) {
-  if ((__double2hiint(d) & 0x7fffffff) < 0x3fd00000) {  // |d| < 0.25 (NaN: no)
+__device__ __forceinline__ void stage_trig<double>(double s0, double c0, double c, double x, double th0, double* s,
+                                                   double* cs) {
+  const double d = c * x;
+  const int ex = __double2hiint(d) & 0x7fffffff;
+  double sd, cm1;
+  if (ex < 0x3fa00000) {  // |d| < 2^-5
+    const double z = d * d;
+    double ps = fma(z, -1.0 / 5040.0, 1.0 / 120.0);
+    ps = fma(z, ps, -1.0 / 6.0);
+    sd = fma(d * z, ps, d);
+    double pc = fma(z, 1.0 / 40320.0, -1.0 / 720.0);
+    pc = fma(z, pc, 1.0 / 24.0);
+    pc = fma(z, pc, -0.5);
+    cm1 = z * pc;
+  } else if (ex < 0x3fd00000) {  // |d| < 1/4 (NaN: no)
     const double z = d * d;
     double ps = fma(z, -1.0 / 39916800.0, 1.0 / 362880.0);
     ps = fma(z, ps, -1.0 / 5040.0);
     ps = fma(z, ps, 1.0 / 120.0);
     ps = fma(z, ps, -1.0 / 6.0);
-    const double sd = fma(d * z, ps, d);  // sin d
+    sd = fma(d * z, ps, d);
     double pc = fma(z, 1.0 / 479001600.0, -1.0 / 3628800.0);
     pc = fma(z, pc, 1.0 / 40320.0);
     pc = fma(z, pc, -1.0 / 720.0);
     pc = fma(z, pc, 1.0 / 24.0);
     pc = fma(z, pc, -0.5);
-    const double cm1 = z * pc;  // cos d - 1
-    *s = fma(s0, cm1, fma(c0, sd, s0));
-    *c = fma(c0, cm1, fma(-s0, sd, c0));
+    cm1 = z * pc;
   } else {
-    sincos(th, s, c);
+    sincos(fma(c, x, th0), s, cs);
+    return;
   }
+  *s = fma(s0, cm1, fma(c0, sd, s0));
+  *cs = fma(c0, cm1, fma(-s0, sd, c0));
 }
+
+// 2x for a finite, normal x: the exponent field raised by one, on the integer
+// pipe (exact; an FP64 add or multiply would take an issue of the FP64 unit).
+// Used for 2r and 4r of stage radii, which are finite and normal on every ray
+// still traced: r = 0 (which this maps to the smallest normal number) lies
+// inside the capture radius, and a non-finite r makes the whole state
+// non-finite, so either ray ends at this step.  FP32: x + x.
+__device__ __forceinline__ double twice(double x) {
+  return __hiloint2double(__double2hiint(x) + 0x00100000, __double2loint(x));
+}
+__device__ __forceinline__ float twice(float x) { return x + x; }
 
 // Ordering key of a radius for the termination tests, on the integer pipe:
 // the signed 64-bit view of its bits, with every NaN mapped above all
@@ -187,7 +217,7 @@ __device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T s, T c, T ut,
   const T iDs2 = rho2 * inv;  // 1 / (Delta sin^2)
   const T iDelta = iDs2 * s2;
   const T q = tMr * irho2;
-  const T r_2 = r + r;
+  const T r_2 = twice(r);
   const T dq_r = fma(-r_2, q, bh.twoM) * irho2;
   const T a2sc2 = bh.two_a2 * sc;  // 2 a^2 sin cos
   const T dq_th = a2sc2 * (q * irho2);
@@ -209,7 +239,7 @@ __device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T s, T c, T ut,
   const T drr_th = -a2sc2 * iDelta;                                       // d_th g_rr
   const T Wr2 = fma(ur, fma(ur, drr_r, (uth + uth) * drr_th), -Kr);      // 2 W_r
   const T Kth = fma(dq_th, v2, fma(sc2 * uph, B - aqv, drr_th * (ur * ur)));
-  const T Wth2 = fma(uth, fma(-a2sc2, uth, (r_2 + r_2) * ur), -Kth);     // 2 W_th
+  const T Wth2 = fma(uth, fma(-a2sc2, uth, twice(r_2) * ur), -Kth);     // 2 W_th
   const T hirho2 = T(0.5) * irho2;
   acc[1] = -Wr2 * (Delta * hirho2);
   acc[2] = -Wth2 * hirho2;
@@ -285,8 +315,10 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
     if (s < 3) {
       const T c = s < 2 ? hh : h;
       r = fma(c, u[1], y[1]);
-      th = fma(c, u[2], y[2]);
-      if constexpr (!kRolled) stage_trig<T>(s0, c0, c * u[2], th, &sn, &cs);
+      if constexpr (kRolled)
+        th = fma(c, u[2], y[2]);
+      else
+        stage_trig<T>(s0, c0, c, u[2], y[2], &sn, &cs);
 #pragma unroll
       for (int j = 0; j < 4; ++j) u[j] = fma(c, acc[j], y[4 + j]);
       if constexpr (kKeys) {
@@ -423,7 +455,7 @@ __device__ __forceinline__ void adm_kerr_sc(const BH<T>& bh, T r, T s, T c, Adm<
   m.igam[1] = irho2;
   m.igam[2] = rho2 * iSigma * is2;
   const T a2sc2 = T(2) * a2 * sc;
-  const T lrho_r = T(2) * r * irho2, lrho_t = -a2sc2 * irho2;
+  const T lrho_r = twice(r) * irho2, lrho_t = -a2sc2 * irho2;
   const T dDr = T(2) * (r - bh.M);
   const T lD_r = dDr * iDelta;
   const T lS_r = fma(T(4) * r, r2a2, -(a2 * s2) * dDr) * iSigma;
@@ -539,8 +571,10 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
     if (s < 3) {
       const T c = s < 2 ? hh : h;
       r = fma(c, f[1], z[1]);
-      th = fma(c, f[2], z[2]);
-      if constexpr (!kRolled) stage_trig<T>(s0, c0, c * f[2], th, &sn, &cs);
+      if constexpr (kRolled)
+        th = fma(c, f[2], z[2]);
+      else
+        stage_trig<T>(s0, c0, c, f[2], z[2], &sn, &cs);
       pr = fma(c, f[4], z[5]);
       pth = fma(c, f[5], z[6]);
       if constexpr (kKeys) {
@@ -654,9 +688,8 @@ __device__ __forceinline__ double dopri5_attempt(const BH<double>& bh, double h,
   // k = f(y + h d): stage velocity (the first half of k) and acceleration
   auto stage = [&](double k[8], bool first) {
     const double r = fma(h, d[1], y[1]);
-    const double th = fma(h, d[2], y[2]);
     double sn, cs;
-    stage_trig<double>(s0, c0, h * d[2], th, &sn, &cs);
+    stage_trig<double>(s0, c0, h, d[2], y[2], &sn, &cs);
     if constexpr (kForm == 0) {
       // k = (u, -Gamma u u) at the stage point
 #pragma unroll

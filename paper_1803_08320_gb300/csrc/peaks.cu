@@ -131,7 +131,8 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
 
 // stage_trig against sincos at exactly representable angles th0 + d
 // (th0 = k / 256 with |th0| < 4, d = m / 2^40 with |d| <= 1/4, so the sum has
-// at most 42 significant bits), and recip against the IEEE division on
+// at most 42 significant bits; one eighth of the draws fall in the short
+// tier |d| < 2^-5), and recip against the IEEE division on
 // x = mantissa x 2^e, e in [-60, 60].  err: max |sin error|, max |cos error|,
 // max recip error in units of the last place of 1/x, max relative error of
 // the hardware estimate alone; non-negative doubles ordered as integers.
@@ -143,7 +144,7 @@ __global__ void helpers_check_kernel(unsigned long long* err, uint64_t n) {
     const double th = th0 + d;
     double s0, c0, s, c, sr, cr;
     sincos(th0, &s0, &c0);
-    stage_trig<double>(s0, c0, d, th, &s, &c);
+    stage_trig<double>(s0, c0, 1.0, d, th0, &s, &c);
     sincos(th, &sr, &cr);
     const double es = fabs(s - sr), ec = fabs(c - cr);
     const unsigned long long h3 = mix64(~i);

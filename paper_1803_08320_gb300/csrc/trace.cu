@@ -306,6 +306,40 @@ struct BanksFor<true> {
   using type = BlockBanks;
 };
 
+// ---------------------------------------------------------------------------
+// FP64 whole-image cameras: ray starts and ends staged per warp.
+//
+// The FP64 work at a ray's start (the pixel's initial state, its invariants,
+// the canonical momenta) and at its end (the invariants behind the validity
+// flag) costs one FP64 warp instruction per operation whether one lane needs
+// it or 32, and an FP64 warp refills its lanes a few at a time.  So the warp
+// prepares the starts of up to 32 queued pixels at once, one per lane, and
+// hands them out as lanes fall idle; and it parks ended rays here and
+// finishes up to 32 of them at once.  Each ray's arithmetic is unchanged;
+// only when, and in which lane, it runs.  (FP32_MIXED camera warps refill all
+// 32 lanes at once, so their starts are batched already.)
+struct WarpStage {
+  double y0[8][32];          // start states (canonical forms: (x, p))
+  double n0[32], dlim0[32];  // norm at the start, drift limit of the flag
+  unsigned long long id0[32];
+  double y1[7][32];          // end states y[1..7]
+  double n1[32], dlim1[32];
+  unsigned long long id1[32];
+  uint32_t nst1[32], fate1[32];
+};
+struct NoStage {
+  int unused;
+};
+template <bool kOn>
+struct StageFor {
+  using type = NoStage;
+};
+template <>
+struct StageFor<true> {
+  using type = WarpStage[kMaxTPB / 32];
+};
+static_assert(sizeof(WarpStage) * (kMaxTPB / 32) <= 48 * 1024, "static shared memory of the camera stage");
+
 // Lane 0 only: take the block's lock, at most 64 tries.
 __device__ __forceinline__ bool bank_try_lock(int* lock) {
   for (int k = 0; k < 64; ++k) {
@@ -582,7 +616,114 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
     return leave != 0;
   };
 
+  // Quantities fixed at a ray's start: the norm at the start and the drift
+  // limit of the validity flag, and (FP32_MIXED) the FP64-zone radius and
+  // polar threshold, which differ between null rays and particles.
+  auto start_consts = [&](const double ys[8], const double inv[4], double rp, double& n0_s, double& dlim_s,
+                          float& rz_s, float& pole_s) {
+    n0_s = inv[3];
+    dlim_s = MALBEC_NORM_DRIFT_TOL * fmax(inv[0] * inv[0], fabs(inv[3]));
+    if constexpr (kMixed) {
+      const double cth = cos(ys[2]);
+      const double gtt = 2.0 * M * ys[1] / fma(a * a, cth * cth, ys[1] * ys[1]) - 1.0;
+      const bool is_null = fabs(inv[3]) <= 1e-6 * fabs(gtt) * ys[4] * ys[4];
+      double rz = p.zone_horizon * rp;
+      if (is_null) rz = fmax(rz, dev_r_photon_retro(M, a) + p.zone_photon * M);
+      rz_s = (float)rz;
+      pole_s = is_null ? -1.f : pole_f;
+    }
+  };
+
+  // FP64 whole-image cameras: the warp's stage (see WarpStage).  The black
+  // hole, the capture radius and the step rule are the same for every pixel.
+  constexpr bool kStage = kSrc == kSrcCamera && kSink == kSinkCamera && !kMixed;
+  __shared__ typename StageFor<kStage>::type stage;
+  const int warp_in_block = (int)(threadIdx.x >> 5);
+  double rp_cam = 0.0;
+  int st_left = 0, st_pos = 0, e_n = 0;  // warp-uniform: staged starts left, next one; staged ends
+  bool q_done = false, pend = false;      // queue exhausted; this lane's ray ended, not yet staged
+  uint32_t end_fate = 0;
+  if constexpr (kStage) {
+    rp_cam = dev_r_plus(M, a);
+    r_cap = (1.0 + eps_hor) * rp_cam;
+  }
+  // Lane l prepares the start of pixel pix in slot l.
+  auto stage_start = [&](WarpStage& ws, unsigned long long pix) {
+    double ys[8], inv[4];
+    camera_state(p.cam, a, pix, ys);
+    invariants64(M, a, ys, inv);
+    double n0_s, dlim_s;
+    float rz_s = 0.f, pole_s = -1.f;  // FP32_MIXED only
+    start_consts(ys, inv, rp_cam, n0_s, dlim_s, rz_s, pole_s);
+    if constexpr (kHam) {
+      double pz[4];
+      to_momenta<kForm>(M, a, ys, pz);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ys[4 + c] = pz[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) ws.y0[c][lane] = ys[c];
+    ws.n0[lane] = n0_s;
+    ws.dlim0[lane] = dlim_s;
+    ws.id0[lane] = pix;
+  };
+  // This lane's ended ray into end slot s (its state has not changed since
+  // it ended: an idle lane is not stepped).
+  auto stage_end = [&](WarpStage& ws, int s) {
+#pragma unroll
+    for (int c = 1; c < 8; ++c) ws.y1[c - 1][s] = y[c];
+    ws.n1[s] = n0;
+    ws.dlim1[s] = drift_lim;
+    ws.id1[s] = id;
+    ws.nst1[s] = nst;
+    ws.fate1[s] = end_fate;
+  };
+  // The whole warp finishes the n staged ends: end invariants, validity flag,
+  // the pixel's outputs.
+  auto finish_ends = [&](WarpStage& ws, int n) {
+    __syncwarp();
+    if (lane < n) {
+      double ye[8];
+      ye[0] = 0.0;  // t enters neither the invariants nor the outputs
+#pragma unroll
+      for (int c = 1; c < 8; ++c) ye[c] = ws.y1[c - 1][lane];
+      if constexpr (kHam) {
+        double u[4];
+        to_velocity<kForm>(M, a, ye, u);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ye[4 + c] = u[c];
+      }
+      double inv1[4];
+      invariants64(M, a, ye, inv1);
+      uint32_t f = ws.fate1[lane];
+      if ((f == MALBEC_FATE_ESCAPED || f == MALBEC_FATE_CAPPED) && fabs(inv1[3] - ws.n1[lane]) > ws.dlim1[lane])
+        f |= MALBEC_FATE_DRIFTED;
+      const unsigned long long i = ws.id1[lane];
+      p.fate_out[i] = (uint8_t)f;
+      p.steps_out[i] = ws.nst1[lane];
+      p.theta_out[i] = ye[2];
+      p.phi_out[i] = ye[3];
+    }
+    __syncwarp();
+  };
+
   while (true) {
+    if constexpr (kStage) {
+      // rays that ended in the last warp step go to the stage
+      const unsigned pm = __ballot_sync(kFull, pend);
+      if (pm != 0u) {
+        WarpStage& ws = stage[warp_in_block];
+        if (e_n + __popc(pm) > 32) {
+          finish_ends(ws, e_n);
+          e_n = 0;
+        }
+        if (pend) {
+          stage_end(ws, e_n + __popc(pm & lt_mask));
+          pend = false;
+        }
+        e_n += __popc(pm);
+      }
+    }
     unsigned act = __ballot_sync(kFull, active);
     if constexpr (kBanks) {
       if (use_banks) {
@@ -640,7 +781,53 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
     if (kSrc == kSrcServe && claim_backoff > 0) --claim_backoff;
     if (!drained && idle > 0 && (idle >= p.refill_min || act == 0) && (act == 0 || claim_backoff == 0)) {
       bool got = false;
-      if (kSrc == kSrcStates || kSrc == kSrcCamera) {
+      if constexpr (kStage) {
+        // ---- idle lanes take staged starts; an empty stage is refilled with
+        // the next 32 pixels of the queue (near the end of the queue, with
+        // as many as there are idle lanes, so that no warp holds back rays
+        // that other warps could take)
+        WarpStage& ws = stage[warp_in_block];
+        unsigned need = ~act;
+        while (need != 0u) {
+          if (st_left == 0) {
+            if (q_done) break;
+            __syncwarp();  // every slot has been read before it is rewritten
+            unsigned long long base = 0;
+            int want = 32;
+            if (lane == 0) {
+              const unsigned long long reserve = 2ull * gridDim.x * blockDim.x;
+              const unsigned long long h = *reinterpret_cast<volatile unsigned long long*>(p.head);
+              if (h >= p.n || p.n - h <= reserve) want = __popc(need);
+              base = atomicAdd(p.head, (unsigned long long)want);
+            }
+            base = __shfl_sync(kFull, base, 0);
+            want = __shfl_sync(kFull, want, 0);
+            if (base + (unsigned long long)want >= p.n) q_done = true;
+            const int k = base < p.n ? (int)min((unsigned long long)want, p.n - base) : 0;
+            if (lane < k) stage_start(ws, camera_claim_pixel(p.cam, base + (unsigned long long)lane));
+            __syncwarp();
+            st_left = k;
+            st_pos = 0;
+            if (k == 0) break;
+          }
+          const int take = min(__popc(need), st_left);
+          const unsigned rank = __popc(need & lt_mask);
+          const bool mine = ((need >> lane) & 1u) && (int)rank < take;
+          if (mine) {
+            const int s = st_pos + (int)rank;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) y[c] = ws.y0[c][s];
+            n0 = ws.n0[s];
+            drift_lim = ws.dlim0[s];
+            id = ws.id0[s];
+            got = true;
+          }
+          need &= ~__ballot_sync(kFull, mine);
+          st_pos += take;
+          st_left -= take;
+        }
+        drained = q_done && st_left == 0;
+      } else if (kSrc == kSrcStates || kSrc == kSrcCamera) {
         // ---- hand the next `idle` rays of the queue to the idle lanes
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(p.head, (unsigned long long)idle);
@@ -817,54 +1004,52 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
 #pragma unroll
           for (int c = 0; c < 8; ++c) y[c] = p.ics[(size_t)c * p.n + id];
           if (p.a_per_ray) a = p.a_per_ray[id];
-        } else {
+        } else if constexpr (!kStage) {
           camera_state(p.cam, a, id, y);
         }
-        bh64 = make_bh<double>(M, a);
-        if (kMixed) bh32 = make_bh<float>(M, a);
-        const double rp = dev_r_plus(M, a);
-        r_cap = (1.0 + eps_hor) * rp;
         lam = 0.0;
         lam_h = lam_l = 0.f;
         lam_fix = 0;
         nst = 0;
         zone_waited = 0;
-        const bool from_jobs = kSrc == kSrcJobs || kSrc == kSrcServe;
-        const JobDesc* Jp = from_jobs ? &p.jobs[job] : nullptr;
-        const bool camera_ray = kSink == kSinkCamera ||
-                                (from_jobs && __ldcg(reinterpret_cast<const int*>(&Jp->kind)) == MALBEC_BUNDLE_CAMERA);
-        {
-          double inv[4];
-          invariants64(M, a, y, inv);
-          n0 = inv[3];
-          drift_lim = MALBEC_NORM_DRIFT_TOL * fmax(inv[0] * inv[0], fabs(inv[3]));
-          if (!camera_ray) {
-            double* inv0 = from_jobs ? reinterpret_cast<double*>(__ldcg(reinterpret_cast<const unsigned long long*>(&Jp->inv0_out)))
-                                     : p.inv0_out;
-            const uint64_t nn = from_jobs ? __ldcg(reinterpret_cast<const unsigned long long*>(&Jp->n)) : p.n;
+        if constexpr (!kStage) {
+          // (staged camera rays: state (x, u) or (x, p), n0 and drift_lim
+          // came from the stage; black hole and capture radius are fixed)
+          bh64 = make_bh<double>(M, a);
+          if (kMixed) bh32 = make_bh<float>(M, a);
+          const double rp = dev_r_plus(M, a);
+          r_cap = (1.0 + eps_hor) * rp;
+          const bool from_jobs = kSrc == kSrcJobs || kSrc == kSrcServe;
+          const JobDesc* Jp = from_jobs ? &p.jobs[job] : nullptr;
+          const bool camera_ray =
+              kSink == kSinkCamera ||
+              (from_jobs && __ldcg(reinterpret_cast<const int*>(&Jp->kind)) == MALBEC_BUNDLE_CAMERA);
+          {
+            double inv[4];
+            invariants64(M, a, y, inv);
+            start_consts(y, inv, rp, n0, drift_lim, r_zone_f, pole_lane);
+            if (!camera_ray) {
+              double* inv0 = from_jobs ? reinterpret_cast<double*>(
+                                             __ldcg(reinterpret_cast<const unsigned long long*>(&Jp->inv0_out)))
+                                       : p.inv0_out;
+              const uint64_t nn = from_jobs ? __ldcg(reinterpret_cast<const unsigned long long*>(&Jp->n)) : p.n;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) inv0[(size_t)c * nn + id] = inv[c];
+              for (int c = 0; c < 4; ++c) inv0[(size_t)c * nn + id] = inv[c];
+            }
+            if (kMixed) {
+              r_cap_f = (float)r_cap;
+              split_pair(y, hi, lo);
+            }
           }
-          if (kMixed) {
-            const double cth = cos(y[2]);
-            const double gtt = 2.0 * M * y[1] / fma(a * a, cth * cth, y[1] * y[1]) - 1.0;
-            const bool is_null = fabs(inv[3]) <= 1e-6 * fabs(gtt) * y[4] * y[4];
-            double rz = p.zone_horizon * rp;
-            if (is_null) rz = fmax(rz, dev_r_photon_retro(M, a) + p.zone_photon * M);
-            r_zone_f = (float)rz;
-            r_cap_f = (float)r_cap;
-            pole_lane = is_null ? -1.f : pole_f;
-            split_pair(y, hi, lo);
-          }
-        }
-        if (kSink == kSinkStrided) store_sample<kMixed>(p, a, id, 0, y, hi);
-        if constexpr (kHam) {
-          // canonical form: integrate (x, p) with p = g u
-          double pz[4];
-          to_momenta<kForm>(M, a, y, pz);
+          if (kSink == kSinkStrided) store_sample<kMixed>(p, a, id, 0, y, hi);
+          if constexpr (kHam) {
+            // canonical form: integrate (x, p) with p = g u
+            double pz[4];
+            to_momenta<kForm>(M, a, y, pz);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) y[4 + c] = pz[c];
-          if constexpr (kMixed) split_pair(y, hi, lo);
+            for (int c = 0; c < 4; ++c) y[4 + c] = pz[c];
+            if constexpr (kMixed) split_pair(y, hi, lo);
+          }
         }
         if constexpr (kDopri) {
           // first trial step; k1 = f(y) for the first attempt
@@ -893,6 +1078,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
         if (!use_banks || leave_block_banks(banks)) break;
         continue;
       } else {
+        if constexpr (kStage) finish_ends(stage[warp_in_block], e_n);
         break;
       }
     }
@@ -1064,61 +1250,67 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
     }
 
     if (fate != 0) {
-      if (kMixed) {
-        flush_lam();
+      if constexpr (kStage) {
+        // staged at the top of the next warp step, finished with others
+        pend = true;
+        end_fate = (uint32_t)fate;
+      } else {
+        if (kMixed) {
+          flush_lam();
 #pragma unroll
-        for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
-      }
-      if constexpr (kHam) {
-        // back to (x, u) for the outputs and the invariants
-        double u[4];
-        to_velocity<kForm>(M, a, y, u);
+          for (int c = 0; c < 8; ++c) y[c] = (double)hi[c] + (double)lo[c];
+        }
+        if constexpr (kHam) {
+          // back to (x, u) for the outputs and the invariants
+          double u[4];
+          to_velocity<kForm>(M, a, y, u);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) y[4 + c] = u[c];
-      }
-      // the end invariants (FP64) and the validity flag
-      double inv1[4];
-      invariants64(M, a, y, inv1);
-      if ((fate == MALBEC_FATE_ESCAPED || fate == MALBEC_FATE_CAPPED) && fabs(inv1[3] - n0) > drift_lim)
-        fate |= MALBEC_FATE_DRIFTED;
-      if (kSink == kSinkJobs) {
-        const JobDesc J = load_job(&p.jobs[job]);
-        if (J.kind == MALBEC_BUNDLE_CAMERA) {
-          J.fate_out[id] = (uint8_t)fate;
-          J.steps_out[id] = nst;
-          J.theta_out[id] = y[2];
-          J.phi_out[id] = y[3];
+          for (int c = 0; c < 4; ++c) y[4 + c] = u[c];
+        }
+        // the end invariants (FP64) and the validity flag
+        double inv1[4];
+        invariants64(M, a, y, inv1);
+        if ((fate == MALBEC_FATE_ESCAPED || fate == MALBEC_FATE_CAPPED) && fabs(inv1[3] - n0) > drift_lim)
+          fate |= MALBEC_FATE_DRIFTED;
+        if (kSink == kSinkJobs) {
+          const JobDesc J = load_job(&p.jobs[job]);
+          if (J.kind == MALBEC_BUNDLE_CAMERA) {
+            J.fate_out[id] = (uint8_t)fate;
+            J.steps_out[id] = nst;
+            J.theta_out[id] = y[2];
+            J.phi_out[id] = y[3];
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) J.y_out[(size_t)c * J.n + id] = y[c];
+            J.lambda_out[id] = lam;
+            J.steps_out[id] = nst;
+            J.fate_out[id] = (uint8_t)fate;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) J.inv1_out[(size_t)c * J.n + id] = inv1[c];
+          }
+          // this ray's outputs are visible device-wide before it is counted
+          __threadfence();
+          const unsigned long long finished = atomicAdd(&p.job_ctr[job].done, 1ull) + 1ull;
+          if (kSrc == kSrcServe && finished == J.n) {
+            // last ray of the job: every output is visible, tell the host
+            __threadfence_system();
+            p.done_flags[job] = J.job_id;
+          }
+        } else if (kSink == kSinkCamera) {
+          p.fate_out[id] = (uint8_t)fate;
+          p.steps_out[id] = nst;
+          p.theta_out[id] = y[2];
+          p.phi_out[id] = y[3];
         } else {
 #pragma unroll
-          for (int c = 0; c < 8; ++c) J.y_out[(size_t)c * J.n + id] = y[c];
-          J.lambda_out[id] = lam;
-          J.steps_out[id] = nst;
-          J.fate_out[id] = (uint8_t)fate;
+          for (int c = 0; c < 8; ++c) p.y_out[(size_t)c * p.n + id] = y[c];
+          p.lambda_out[id] = lam;
+          p.steps_out[id] = nst;
+          p.fate_out[id] = (uint8_t)fate;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) J.inv1_out[(size_t)c * J.n + id] = inv1[c];
+          for (int c = 0; c < 4; ++c) p.inv1_out[(size_t)c * p.n + id] = inv1[c];
+          if (kSink == kSinkStrided) store_nan_samples<kMixed>(p, id, (uint64_t)nst / p.stride + 1);
         }
-        // this ray's outputs are visible device-wide before it is counted
-        __threadfence();
-        const unsigned long long finished = atomicAdd(&p.job_ctr[job].done, 1ull) + 1ull;
-        if (kSrc == kSrcServe && finished == J.n) {
-          // last ray of the job: every output is visible, tell the host
-          __threadfence_system();
-          p.done_flags[job] = J.job_id;
-        }
-      } else if (kSink == kSinkCamera) {
-        p.fate_out[id] = (uint8_t)fate;
-        p.steps_out[id] = nst;
-        p.theta_out[id] = y[2];
-        p.phi_out[id] = y[3];
-      } else {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) p.y_out[(size_t)c * p.n + id] = y[c];
-        p.lambda_out[id] = lam;
-        p.steps_out[id] = nst;
-        p.fate_out[id] = (uint8_t)fate;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) p.inv1_out[(size_t)c * p.n + id] = inv1[c];
-        if (kSink == kSinkStrided) store_nan_samples<kMixed>(p, id, (uint64_t)nst / p.stride + 1);
       }
       active = false;
     }

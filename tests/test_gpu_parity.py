@@ -273,11 +273,13 @@ def test_camera_small_image_parity(mb, orc, W):
 
 
 @pytest.mark.parametrize("nx,ny,precision", [(37, 23, "fp64"), (48, 5, "fp64"), (1, 9, "fp64"), (2, 3, "fp64"),
-                                              (37, 23, "fp32_mixed"), (48, 5, "fp32_mixed")])
+                                              (256, 257, "fp64"), (37, 23, "fp32_mixed"), (48, 5, "fp32_mixed")])
 def test_camera_claim_order_is_a_schedule_only(mb, W, nx, ny, precision):
     """The camera kernel starts the centre columns first; its per-pixel
     output equals the trace of the same pixels' initial states in index order
-    (odd and even widths, one and two columns): bitwise in FP64; in
+    (odd and even widths, one and two columns; 256 x 257 is large enough
+    that FP64 warps stage their starts 32 pixels at a time before the end of
+    the queue, and their ends up to 32 at a time): bitwise in FP64; in
     FP32_MIXED (two kernel instantiations may round an FP32 operation
     differently) fates and steps on >= 99% of pixels, angles within 1e-6."""
     import torch
