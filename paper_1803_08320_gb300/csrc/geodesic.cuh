@@ -43,20 +43,106 @@ struct Trig<float> {
 // division's sequence (the 1024^2 FP32_MIXED camera: the same image, 5%
 // faster).  Arguments here are positive and normal (products of rho^2,
 // Delta, sin^2, far from the subnormal range).
+// `one` is 1 (FP64: in a per-thread register, see vmul).
 template <typename T>
-__device__ __forceinline__ T recip(T x);
+__device__ __forceinline__ T recip(T x, T one);
 template <>
-__device__ __forceinline__ double recip<double>(double x) {
+__device__ __forceinline__ double recip<double>(double x, double one) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  const double e = fma(-x, y, 1.0);
+  const double e = fma(-x, y, one);
   return fma(y, fma(e, e, e), y);
 }
 template <>
-__device__ __forceinline__ float recip<float>(float x) {
+__device__ __forceinline__ float recip<float>(float x, float) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return fmaf(y, fmaf(-x, y, 1.0f), y);
+}
+template <typename T>
+__device__ __forceinline__ T recip(T x) {
+  return recip<T>(x, T(1));
+}
+
+// ---------------------------------------------------------------------------
+// FP64 operand forms.  On this part the FP64 unit takes an FMA whose operands
+// are all per-thread registers (or two constant-bank operands) at its full
+// rate, one warp instruction per ~64 cycles, but a DMUL, a DADD, or an FMA
+// with an operand in a uniform register or mixed with one constant-bank
+// operand takes ~18% longer (measured on GB300 with independent chains: 39.0
+// against 33.0 ns per warp instruction; dependent chains run at the full rate
+// too).  So the FP64 right-hand sides write a product as fma(x, y, -0) and a
+// sum as fma(x, 1, y) -- exactly the IEEE product and sum, signed zeros, NaN
+// and infinities included -- with -0, 1, the black-hole constants and the
+// series coefficients held in per-thread registers: vreg(v, vz) is v with vz
+// OR-ed into its bits, vz = threadIdx.x & (a launch parameter that is always
+// 0), which the compiler can neither fold nor prove warp-uniform.  FP32: the
+// plain operations.
+__device__ __forceinline__ double vreg(double x, unsigned long long vz) {
+  return __longlong_as_double(__double_as_longlong(x) | (long long)vz);
+}
+
+template <typename T>
+struct BH {
+  T M, a, a2, twoM, two_a2;
+  T nz, one, two, half;  // -0, 1, 2, 1/2
+  T k[10];               // k[n - 3] = 1/n!, n = 3..12 (the stage-angle series; k[0] = 1/6 also for h/6)
+};
+
+// vz = 0: the constants are whatever the compiler makes of them (any kernel
+// may use that); per-thread registers when vz is the per-thread zero above.
+template <typename T>
+__device__ __forceinline__ BH<T> make_bh(double M, double a, unsigned long long vz = 0ull) {
+  BH<T> b;
+  double v[9] = {M, a, a * a, 2.0 * M, 2.0 * a * a, -0.0, 1.0, 2.0, 0.5};
+  double f = 1.0;
+  double k[10];
+#pragma unroll
+  for (int n = 1; n <= 12; ++n) {
+    f *= (double)n;
+    if (n >= 3) k[n - 3] = 1.0 / f;
+  }
+  if (sizeof(T) == 8) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = vreg(v[i], vz);
+#pragma unroll
+    for (int i = 0; i < 10; ++i) k[i] = vreg(k[i], vz);
+  }
+  b.M = T(v[0]);
+  b.a = T(v[1]);
+  b.a2 = T(v[2]);
+  b.twoM = T(v[3]);
+  b.two_a2 = T(v[4]);
+  b.nz = T(v[5]);
+  b.one = T(v[6]);
+  b.two = T(v[7]);
+  b.half = T(v[8]);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) b.k[i] = T(k[i]);
+  return b;
+}
+
+// x y, x + y, x - y in the full-rate operand form (FP64) or plainly (FP32).
+template <typename T>
+__device__ __forceinline__ T vmul(const BH<T>& b, T x, T y) {
+  if constexpr (sizeof(T) == 8)
+    return fma(x, y, b.nz);
+  else
+    return x * y;
+}
+template <typename T>
+__device__ __forceinline__ T vadd(const BH<T>& b, T x, T y) {
+  if constexpr (sizeof(T) == 8)
+    return fma(x, b.one, y);
+  else
+    return x + y;
+}
+template <typename T>
+__device__ __forceinline__ T vsub(const BH<T>& b, T x, T y) {
+  if constexpr (sizeof(T) == 8)
+    return fma(x, b.one, -y);
+  else
+    return x - y;
 }
 
 // sin and cos at a stage angle th = th0 + c x (c x = d, the stage's offset
@@ -73,41 +159,42 @@ __device__ __forceinline__ float recip<float>(float x) {
 // tier is a per-lane choice on the bits of d, so a ray's result never depends
 // on the other rays of its warp.
 template <typename T>
-__device__ __forceinline__ void stage_trig(T s0, T c0, T c, T x, T th0, T* s, T* cs) {
+__device__ __forceinline__ void stage_trig(const BH<T>&, T s0, T c0, T c, T x, T th0, T* s, T* cs) {
   Trig<T>::sc(fma(c, x, th0), s, cs);
 }
 // The range tests read the exponent bits on the integer pipe (an FP64 compare
 // would take an issue of the FP64 unit, which costs as much as an FMA there);
 // sin th = s0 + c0 sin d + s0 (cos d - 1) and likewise cos th are two FMAs
-// each.
+// each.  Products and coefficients in the full-rate operand forms (vmul).
 template <>
-__device__ __forceinline__ void stage_trig<double>(double s0, double c0, double c, double x, double th0, double* s,
-                                                   double* cs) {
-  const double d = c * x;
+__device__ __forceinline__ void stage_trig<double>(const BH<double>& b, double s0, double c0, double c, double x,
+                                                   double th0, double* s, double* cs) {
+  const double* k = b.k;  // k[n - 3] = 1/n!
+  const double d = vmul(b, c, x);
   const int ex = __double2hiint(d) & 0x7fffffff;
   double sd, cm1;
   if (ex < 0x3fa00000) {  // |d| < 2^-5
-    const double z = d * d;
-    double ps = fma(z, -1.0 / 5040.0, 1.0 / 120.0);
-    ps = fma(z, ps, -1.0 / 6.0);
-    sd = fma(d * z, ps, d);
-    double pc = fma(z, 1.0 / 40320.0, -1.0 / 720.0);
-    pc = fma(z, pc, 1.0 / 24.0);
-    pc = fma(z, pc, -0.5);
-    cm1 = z * pc;
+    const double z = vmul(b, d, d);
+    double ps = fma(z, -k[4], k[2]);
+    ps = fma(z, ps, -k[0]);
+    sd = fma(vmul(b, d, z), ps, d);
+    double pc = fma(z, k[5], -k[3]);
+    pc = fma(z, pc, k[1]);
+    pc = fma(z, pc, -b.half);
+    cm1 = vmul(b, z, pc);
   } else if (ex < 0x3fd00000) {  // |d| < 1/4 (NaN: no)
-    const double z = d * d;
-    double ps = fma(z, -1.0 / 39916800.0, 1.0 / 362880.0);
-    ps = fma(z, ps, -1.0 / 5040.0);
-    ps = fma(z, ps, 1.0 / 120.0);
-    ps = fma(z, ps, -1.0 / 6.0);
-    sd = fma(d * z, ps, d);
-    double pc = fma(z, 1.0 / 479001600.0, -1.0 / 3628800.0);
-    pc = fma(z, pc, 1.0 / 40320.0);
-    pc = fma(z, pc, -1.0 / 720.0);
-    pc = fma(z, pc, 1.0 / 24.0);
-    pc = fma(z, pc, -0.5);
-    cm1 = z * pc;
+    const double z = vmul(b, d, d);
+    double ps = fma(z, -k[8], k[6]);
+    ps = fma(z, ps, -k[4]);
+    ps = fma(z, ps, k[2]);
+    ps = fma(z, ps, -k[0]);
+    sd = fma(vmul(b, d, z), ps, d);
+    double pc = fma(z, k[9], -k[7]);
+    pc = fma(z, pc, k[5]);
+    pc = fma(z, pc, -k[3]);
+    pc = fma(z, pc, k[1]);
+    pc = fma(z, pc, -b.half);
+    cm1 = vmul(b, z, pc);
   } else {
     sincos(fma(c, x, th0), s, cs);
     return;
@@ -141,22 +228,6 @@ __device__ __forceinline__ long long radius_key(double r) {
 __device__ __forceinline__ bool key_le(long long k, double ref) { return k <= __double_as_longlong(ref); }
 __device__ __forceinline__ bool key_ge(long long k, double ref) { return k >= __double_as_longlong(ref); }
 
-template <typename T>
-struct BH {
-  T M, a, a2, twoM, two_a2;
-};
-
-template <typename T>
-__device__ __forceinline__ BH<T> make_bh(double M, double a) {
-  BH<T> b;
-  b.M = T(M);
-  b.a = T(a);
-  b.a2 = T(a * a);
-  b.twoM = T(2.0 * M);
-  b.two_a2 = T(2.0 * a * a);
-  return b;
-}
-
 // ---------------------------------------------------------------------------
 // Schwarzschild: Gamma^t_tr = M/(r f), Gamma^r_tt = M f / r^3,
 // Gamma^r_rr = -M/(r f), Gamma^r_thth = -f, Gamma^r_phph = -f sin^2,
@@ -165,18 +236,20 @@ __device__ __forceinline__ BH<T> make_bh(double M, double a) {
 template <typename T, bool kFastRcp = true>
 __device__ __forceinline__ void accel_schw(const BH<T>& bh, T r, T s, T c, T ut, T ur, T uth, T uph,
                                            T acc[4]) {
-  const T f = r - bh.twoM;
-  const T rf = r * f;
-  const T inv = kFastRcp ? recip<T>(rf * s) : T(1) / (rf * s);  // 1 / (r f sin)
-  const T ir = f * s * inv;       // 1/r
-  const T i_f = r * s * inv;      // 1/f
-  const T cot = c * rf * inv;     // cos/sin
-  const T Mirf = bh.M * ir * i_f; // M/(r f)
-  const T ang = fma(s * s * uph, uph, uth * uth);
-  acc[0] = T(-2) * Mirf * ut * ur;
-  acc[1] = fma(f, ang, fma(Mirf * ur, ur, -(bh.M * f * ir * ir * ir) * ut * ut));
-  acc[2] = fma(s * c * uph, uph, T(-2) * ir * ur * uth);
-  acc[3] = T(-2) * uph * fma(ir, ur, cot * uth);
+  auto mul = [&](T x, T y) { return vmul<T>(bh, x, y); };
+  const T f = vsub<T>(bh, r, bh.twoM);
+  const T rf = mul(r, f);
+  const T den = mul(rf, s);
+  const T inv = kFastRcp ? recip<T>(den, bh.one) : T(1) / den;  // 1 / (r f sin)
+  const T ir = mul(mul(f, s), inv);       // 1/r
+  const T i_f = mul(mul(r, s), inv);      // 1/f
+  const T cot = mul(mul(c, rf), inv);     // cos/sin
+  const T Mirf = mul(mul(bh.M, ir), i_f); // M/(r f)
+  const T ang = fma(mul(mul(s, s), uph), uph, mul(uth, uth));
+  acc[0] = mul(mul(mul(-bh.two, Mirf), ut), ur);
+  acc[1] = fma(f, ang, fma(mul(Mirf, ur), ur, mul(mul(-mul(mul(mul(mul(bh.M, f), ir), ir), ir), ut), ut)));
+  acc[2] = fma(mul(mul(s, c), uph), uph, mul(mul(mul(-bh.two, ir), ur), uth));
+  acc[3] = mul(mul(-bh.two, uph), fma(ir, ur, mul(cot, uth)));
 }
 
 // ---------------------------------------------------------------------------
@@ -202,47 +275,53 @@ __device__ __forceinline__ void accel_schw(const BH<T>& bh, T r, T s, T c, T ut,
 //   acc^r = -Delta W_r / rho^2,                  acc^th = -W_th / rho^2.
 // The same bilinear form as the twenty second-kind symbols of BL Kerr, in 71
 // FP64 operations plus one reciprocal.
+// Products and sums in the full-rate FP64 operand forms (vmul, vadd, vsub:
+// the same IEEE results).
 template <typename T, bool kFastRcp = true>
 __device__ __forceinline__ void accel_kerr(const BH<T>& bh, T r, T s, T c, T ut, T ur, T uth, T uph,
                                            T acc[4]) {
+  auto mul = [&](T x, T y) { return vmul<T>(bh, x, y); };
+  auto add = [&](T x, T y) { return vadd<T>(bh, x, y); };
+  auto sub = [&](T x, T y) { return vsub<T>(bh, x, y); };
   const T a = bh.a, a2 = bh.a2;
-  const T s2 = s * s, sc = s * c;
+  const T s2 = mul(s, s), sc = mul(s, c);
   const T r2a2 = fma(r, r, a2);
   const T rho2 = fma(-a2, s2, r2a2);
-  const T tMr = bh.twoM * r;
-  const T Delta = r2a2 - tMr;
-  const T Ds2 = Delta * s2;
-  const T inv = kFastRcp ? recip<T>(rho2 * Ds2) : T(1) / (rho2 * Ds2);
-  const T irho2 = Ds2 * inv;
-  const T iDs2 = rho2 * inv;  // 1 / (Delta sin^2)
-  const T iDelta = iDs2 * s2;
-  const T q = tMr * irho2;
+  const T tMr = mul(bh.twoM, r);
+  const T Delta = sub(r2a2, tMr);
+  const T Ds2 = mul(Delta, s2);
+  const T den = mul(rho2, Ds2);
+  const T inv = kFastRcp ? recip<T>(den, bh.one) : T(1) / den;
+  const T irho2 = mul(Ds2, inv);
+  const T iDs2 = mul(rho2, inv);  // 1 / (Delta sin^2)
+  const T iDelta = mul(iDs2, s2);
+  const T q = mul(tMr, irho2);
   const T r_2 = twice(r);
-  const T dq_r = fma(-r_2, q, bh.twoM) * irho2;
-  const T a2sc2 = bh.two_a2 * sc;  // 2 a^2 sin cos
-  const T dq_th = a2sc2 * (q * irho2);
-  const T Dq = fma(ur, dq_r, uth * dq_th);
-  const T as2 = a * s2;
+  const T dq_r = mul(fma(-r_2, q, bh.twoM), irho2);
+  const T a2sc2 = mul(bh.two_a2, sc);  // 2 a^2 sin cos
+  const T dq_th = mul(a2sc2, mul(q, irho2));
+  const T Dq = fma(ur, dq_r, mul(uth, dq_th));
+  const T as2 = mul(a, s2);
   const T v = fma(-as2, uph, ut);
-  const T aq = a * q;
-  const T aqv = aq * v;
+  const T aq = mul(a, q);
+  const T aqv = mul(aq, v);
   const T B = fma(r2a2, uph, -aqv);
-  const T sc2 = sc + sc;
-  const T sc2uth = sc2 * uth;
-  const T X = fma(sc2uth, B, (r_2 * s2) * (ur * uph));
-  const T Wt = fma(Dq, v, -(aq * sc2uth) * uph);
-  acc[0] = fma(r2a2, Wt, aq * X) * iDelta;
-  acc[3] = fma(q, X, fma(as2, Wt, -X)) * iDs2;
-  const T v2 = v * v;
-  const T Kr = fma(dq_r, v2, r_2 * fma(s2 * uph, uph, uth * uth));
-  const T drr_r = fma(-(r_2 - bh.twoM) * rho2, iDelta, r_2) * iDelta;  // d_r g_rr
-  const T drr_th = -a2sc2 * iDelta;                                       // d_th g_rr
-  const T Wr2 = fma(ur, fma(ur, drr_r, (uth + uth) * drr_th), -Kr);      // 2 W_r
-  const T Kth = fma(dq_th, v2, fma(sc2 * uph, B - aqv, drr_th * (ur * ur)));
-  const T Wth2 = fma(uth, fma(-a2sc2, uth, twice(r_2) * ur), -Kth);     // 2 W_th
-  const T hirho2 = T(0.5) * irho2;
-  acc[1] = -Wr2 * (Delta * hirho2);
-  acc[2] = -Wth2 * hirho2;
+  const T sc2 = add(sc, sc);
+  const T sc2uth = mul(sc2, uth);
+  const T X = fma(sc2uth, B, mul(mul(r_2, s2), mul(ur, uph)));
+  const T Wt = fma(Dq, v, mul(-mul(aq, sc2uth), uph));
+  acc[0] = mul(fma(r2a2, Wt, mul(aq, X)), iDelta);
+  acc[3] = mul(fma(q, X, fma(as2, Wt, -X)), iDs2);
+  const T v2 = mul(v, v);
+  const T Kr = fma(dq_r, v2, mul(r_2, fma(mul(s2, uph), uph, mul(uth, uth))));
+  const T drr_r = mul(fma(mul(-sub(r_2, bh.twoM), rho2), iDelta, r_2), iDelta);  // d_r g_rr
+  const T drr_th = mul(-a2sc2, iDelta);                                             // d_th g_rr
+  const T Wr2 = fma(ur, fma(ur, drr_r, mul(add(uth, uth), drr_th)), -Kr);           // 2 W_r
+  const T Kth = fma(dq_th, v2, fma(mul(sc2, uph), sub(B, aqv), mul(drr_th, mul(ur, ur))));
+  const T Wth2 = fma(uth, fma(-a2sc2, uth, mul(twice(r_2), ur)), -Kth);            // 2 W_th
+  const T hirho2 = mul(bh.half, irho2);
+  acc[1] = mul(-Wr2, mul(Delta, hirho2));
+  acc[2] = mul(-Wth2, hirho2);
 }
 
 // The acceleration at (r, theta) given s = sin theta, c = cos theta
@@ -280,7 +359,7 @@ __device__ __forceinline__ void accel(const BH<T>& bh, T r, T th, T ut, T ur, T 
 template <bool kKerr, typename T, bool kRolled = false>
 __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
   constexpr bool kKeys = sizeof(T) == 8 && !kRolled;
-  const T hh = T(0.5) * h;
+  const T hh = vmul<T>(bh, bh.half, h);
   T r = y[1], th = y[2];
   T u[4] = {y[4], y[5], y[6], y[7]};
   T sx[4], su[4];
@@ -305,7 +384,7 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
         su[j] = acc[j];
       }
     } else {
-      const T w = s == 3 ? T(1) : T(2);
+      const T w = s == 3 ? bh.one : bh.two;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         sx[j] = fma(w, u[j], sx[j]);
@@ -318,7 +397,7 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
       if constexpr (kRolled)
         th = fma(c, u[2], y[2]);
       else
-        stage_trig<T>(s0, c0, c, u[2], y[2], &sn, &cs);
+        stage_trig<T>(bh, s0, c0, c, u[2], y[2], &sn, &cs);
 #pragma unroll
       for (int j = 0; j < 4; ++j) u[j] = fma(c, acc[j], y[4 + j]);
       if constexpr (kKeys) {
@@ -336,7 +415,7 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) stage(s);
   }
-  const T h6 = h * T(1.0 / 6.0);
+  const T h6 = vmul<T>(bh, h, bh.k[0]);  // h/6
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     y[j] = fma(h6, sx[j], y[j]);
@@ -543,7 +622,7 @@ __device__ __forceinline__ void adm_raise(const Adm<double>& m, const double p[4
 template <typename T, bool kRolled = false, int kForm = kHamKerrBL>
 __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
   constexpr bool kKeys = sizeof(T) == 8 && !kRolled;
-  const T hh = T(0.5) * h;
+  const T hh = vmul<T>(bh, bh.half, h);
   T r = z[1], th = z[2], pr = z[5], pth = z[6];
   T sx[6];
   T rmin = T(0);
@@ -564,7 +643,7 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) sx[j] = f[j];
     } else {
-      const T w = s == 3 ? T(1) : T(2);
+      const T w = s == 3 ? bh.one : bh.two;
 #pragma unroll
       for (int j = 0; j < 6; ++j) sx[j] = fma(w, f[j], sx[j]);
     }
@@ -574,7 +653,7 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
       if constexpr (kRolled)
         th = fma(c, f[2], z[2]);
       else
-        stage_trig<T>(s0, c0, c, f[2], z[2], &sn, &cs);
+        stage_trig<T>(bh, s0, c0, c, f[2], z[2], &sn, &cs);
       pr = fma(c, f[4], z[5]);
       pth = fma(c, f[5], z[6]);
       if constexpr (kKeys) {
@@ -592,7 +671,7 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) stage(s);
   }
-  const T h6 = h * T(1.0 / 6.0);
+  const T h6 = vmul<T>(bh, h, bh.k[0]);  // h/6
 #pragma unroll
   for (int j = 0; j < 4; ++j) z[j] = fma(h6, sx[j], z[j]);
   z[5] = fma(h6, sx[4], z[5]);
@@ -689,7 +768,7 @@ __device__ __forceinline__ double dopri5_attempt(const BH<double>& bh, double h,
   auto stage = [&](double k[8], bool first) {
     const double r = fma(h, d[1], y[1]);
     double sn, cs;
-    stage_trig<double>(s0, c0, h, d[2], y[2], &sn, &cs);
+    stage_trig<double>(bh, s0, c0, h, d[2], y[2], &sn, &cs);
     if constexpr (kForm == 0) {
       // k = (u, -Gamma u u) at the stage point
 #pragma unroll

@@ -105,6 +105,10 @@ struct TraceParams {
   unsigned long long* park;
   // launch shape
   int refill_min;  // refill when at least this many lanes of a warp are idle
+  // always 0 (every TraceParams is zeroed): ANDed with threadIdx.x it gives
+  // FP64 kernels a zero the compiler cannot fold or prove warp-uniform, which
+  // keeps their constant operands in per-thread registers (make_bh)
+  unsigned long long lane_zero;
 };
 
 struct LaunchShape {

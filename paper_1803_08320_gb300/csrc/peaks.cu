@@ -64,10 +64,10 @@ int measure(int iters, double* gflops) {
 // bound orbit of Kerr a = 0.9 M (r0 = 10 M + a lane offset, dtau = 0.5) for
 // nsteps steps; one warp per SM sub-partition, as in the trace kernels.
 template <int kForm>
-__global__ void __launch_bounds__(128, 1) step_loop_kernel(double* out, int nsteps) {
+__global__ void __launch_bounds__(128, 1) step_loop_kernel(double* out, int nsteps, unsigned long long lane_zero) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const double M = 1.0, a = 0.9, h = 0.5;
-  const BH<double> bh = make_bh<double>(M, a);
+  const BH<double> bh = make_bh<double>(M, a, (unsigned long long)threadIdx.x & lane_zero);  // as the trace kernels
   const double r0 = 10.0 + 1e-3 * (tid % 97);
   double y[8] = {0.0, r0, 1.2, 0.0, 1.0 / sqrt(1.0 - 3.0 / r0), 0.0, 0.01, 0.0};
   y[7] = sqrt(1.0 / (r0 * r0 * r0)) * y[4];
@@ -102,11 +102,11 @@ int step_loop(double* steps_per_s) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  step_loop_kernel<kForm><<<blocks, threads>>>(buf, 50);
+  step_loop_kernel<kForm><<<blocks, threads>>>(buf, 50, 0ull);
   float best = 1e30f;
   for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
     cudaEventRecord(e0);
-    step_loop_kernel<kForm><<<blocks, threads>>>(buf, nsteps);
+    step_loop_kernel<kForm><<<blocks, threads>>>(buf, nsteps, 0ull);
     cudaEventRecord(e1);
     e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -144,7 +144,7 @@ __global__ void helpers_check_kernel(unsigned long long* err, uint64_t n) {
     const double th = th0 + d;
     double s0, c0, s, c, sr, cr;
     sincos(th0, &s0, &c0);
-    stage_trig<double>(s0, c0, 1.0, d, th0, &s, &c);
+    stage_trig<double>(make_bh<double>(1.0, 0.0), s0, c0, 1.0, d, th0, &s, &c);
     sincos(th, &sr, &cr);
     const double es = fabs(s - sr), ec = fabs(c - cr);
     const unsigned long long h3 = mix64(~i);

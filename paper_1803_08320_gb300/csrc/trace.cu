@@ -75,6 +75,32 @@ __device__ __forceinline__ bool finite8f(const float y[8]) {
   return !bad;
 }
 
+// g(u,u) of an FP32 state in FP32 arithmetic, Kerr in BL coordinates: the
+// geodesic form from (x, u) as g_ab u^a u^b, the canonical forms from (x, p)
+// as g^ab p_a p_b (the inverse (t, phi) block has det -Delta sin^2).
+template <bool kCanon>
+__device__ __forceinline__ float state_norm_f(float M, float a, const float y[8]) {
+  float s, c;
+  sincosf(y[2], &s, &c);
+  const float r = y[1], a2 = a * a, s2 = s * s;
+  const float rho2 = fmaf(a2, c * c, r * r);
+  const float Delta = fmaf(r, r - 2.0f * M, a2);
+  const float q = 2.0f * M * r / rho2;
+  const float gtt = q - 1.0f;
+  const float gtp = -a * s2 * q;
+  const float gpp = s2 * fmaf(a2 * s2, q, fmaf(r, r, a2));
+  if constexpr (kCanon) {
+    const float det = -Delta * s2;
+    const float ut = fmaf(gpp, y[4], -gtp * y[7]) / det;
+    const float up = fmaf(gtt, y[7], -gtp * y[4]) / det;
+    return fmaf(y[4], ut, fmaf(Delta / rho2 * y[5], y[5], fmaf(y[6] / rho2, y[6], y[7] * up)));
+  } else {
+    const float pt = fmaf(gtt, y[4], gtp * y[7]);
+    const float pp = fmaf(gtp, y[4], gpp * y[7]);
+    return fmaf(pt, y[4], fmaf(rho2 / Delta * y[5], y[5], fmaf(rho2 * y[6], y[6], pp * y[7])));
+  }
+}
+
 // Trajectory sample k of ray id: the state (8 components), or with
 // p.traj_cartesian the paper's output record (t, x, y, z) of eq. coord,
 // x = sqrt(r^2 + a^2) sin th cos ph, y = sqrt(r^2 + a^2) sin th sin ph,
@@ -479,7 +505,10 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
   // from it that the end state may show (MALBEC_FATE_DRIFTED)
   double n0 = 0.0, drift_lim = 0.0;
   float r_cap_f = 0.f, r_zone_f = 0.f, pole_lane = -1.f;
-  BH<double> bh64 = make_bh<double>(M, p.a);
+  // FP64 kernels: constant operands in per-thread registers (make_bh); the
+  // FP32_MIXED kernels keep their register budget for the FP32 state
+  const unsigned long long vz = kMixed ? 0ull : ((unsigned long long)threadIdx.x & p.lane_zero);
+  BH<double> bh64 = make_bh<double>(M, p.a, vz);
   BH<float> bh32 = make_bh<float>(M, p.a);
   int zone_waited = 0;
   unsigned long long idle_since = 0ull, nap_since = 0ull;
@@ -1015,7 +1044,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
         if constexpr (!kStage) {
           // (staged camera rays: state (x, u) or (x, p), n0 and drift_lim
           // came from the stage; black hole and capture radius are fixed)
-          bh64 = make_bh<double>(M, a);
+          bh64 = make_bh<double>(M, a, vz);
           if (kMixed) bh32 = make_bh<float>(M, a);
           const double rp = dev_r_plus(M, a);
           r_cap = (1.0 + eps_hor) * rp;
@@ -1161,13 +1190,13 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
           lam += h;
         }
       } else if (!kMixed) {
-        const double h = dl_scale > 0.0 ? dl_scale * y[1] : dl;
+        const double h = dl_scale > 0.0 ? vmul(bh64, vreg(dl_scale, vz), y[1]) : dl;
         double rmin;
         if constexpr (kHam)
           rmin = rk4_step_ham<double, false, kForm>(bh64, h, y);
         else
           rmin = rk4_step<kKerr, double>(bh64, h, y);
-        lam += h;
+        lam = vadd(bh64, lam, h);
         // the radius tests on the integer pipe (radius_key)
         const long long k1 = radius_key(y[1]);
         captured = key_le(k1, r_cap) | key_le(radius_key(rmin), r_cap);
@@ -1254,6 +1283,18 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
         // staged at the top of the next warp step, finished with others
         pend = true;
         end_fate = (uint32_t)fate;
+      } else if constexpr (kMixed && kSink == kSinkCamera) {
+        // FP32_MIXED camera pixel: the validity flag from the norm of the
+        // FP32 state in FP32 arithmetic (no FP64 work for one lane at a time:
+        // its error, ~1e-6 of the largest term, is far inside the flag's
+        // 1e-3 tolerance)
+        const float nrm = state_norm_f<kHam>((float)M, (float)a, hi);
+        if ((fate == MALBEC_FATE_ESCAPED || fate == MALBEC_FATE_CAPPED) && fabs((double)nrm - n0) > drift_lim)
+          fate |= MALBEC_FATE_DRIFTED;
+        p.fate_out[id] = (uint8_t)fate;
+        p.steps_out[id] = nst;
+        p.theta_out[id] = (double)hi[2] + (double)lo[2];
+        p.phi_out[id] = (double)hi[3] + (double)lo[3];
       } else {
         if (kMixed) {
           flush_lam();
