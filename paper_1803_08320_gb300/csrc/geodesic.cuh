@@ -434,33 +434,38 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
 // / (2 rho^2), dp_th/dl likewise; p_t and p_ph are constant (H does not
 // depend on t, ph) and are not integrated.  f = (dt, dr, dth, dph, dp_r,
 // dp_th)/dl.  One reciprocal, as in the geodesic form.
+// Products and sums in the full-rate FP64 operand forms (vmul, vadd, vsub).
 template <typename T, bool kFastRcp = true>
 __device__ __forceinline__ void ham_kerr(const BH<T>& bh, T r, T s, T c, T pt, T pr, T pth, T pph, T f[6]) {
+  auto mul = [&](T x, T y) { return vmul<T>(bh, x, y); };
+  auto sub = [&](T x, T y) { return vsub<T>(bh, x, y); };
   const T a = bh.a, a2 = bh.a2;
-  const T s2 = s * s, sc = s * c;
-  const T rho2 = fma(a2, c * c, r * r);
-  const T Delta = fma(r, r - bh.twoM, a2);
-  const T rD = rho2 * Delta;
-  const T inv = kFastRcp ? recip<T>(rD * s2) : T(1) / (rD * s2);
-  const T irho2 = Delta * s2 * inv;
-  const T iDelta = rho2 * s2 * inv;
-  const T is2 = rD * inv;
+  const T s2 = mul(s, s), sc = mul(s, c);
+  const T rho2 = fma(a2, mul(c, c), mul(r, r));
+  const T Delta = fma(r, sub(r, bh.twoM), a2);
+  const T rD = mul(rho2, Delta);
+  const T den = mul(rD, s2);
+  const T inv = kFastRcp ? recip<T>(den, bh.one) : T(1) / den;
+  const T irho2 = mul(mul(Delta, s2), inv);
+  const T iDelta = mul(mul(rho2, s2), inv);
+  const T is2 = mul(rD, inv);
   const T r2a2 = fma(r, r, a2);
-  const T P = fma(r2a2, pt, a * pph);
-  const T Tq = fma(a * s2, pt, pph);
-  const T PiD = P * iDelta;
-  const T TiS = Tq * is2;
-  f[0] = fma(-r2a2, PiD, a * Tq) * irho2;
-  f[1] = Delta * pr * irho2;
-  f[2] = pth * irho2;
-  f[3] = fma(-a, PiD, TiS) * irho2;
-  const T pr2 = pr * pr;
-  const T F = fma(Tq, TiS, fma(-P, PiD, fma(pth, pth, Delta * pr2)));
-  const T dFr = fma(T(2) * (r - bh.M), fma(PiD, PiD, pr2), T(-4) * r * pt * PiD);
-  const T dFth = T(2) * (sc * is2) * Tq * fma(T(2) * a, pt, -TiS);
-  const T mh = T(-0.5) * irho2;
-  f[4] = mh * fma(T(-2) * r * F, irho2, dFr);
-  f[5] = mh * fma(T(2) * a2 * sc * F, irho2, dFth);
+  const T P = fma(r2a2, pt, mul(a, pph));
+  const T Tq = fma(mul(a, s2), pt, pph);
+  const T PiD = mul(P, iDelta);
+  const T TiS = mul(Tq, is2);
+  f[0] = mul(fma(-r2a2, PiD, mul(a, Tq)), irho2);
+  f[1] = mul(mul(Delta, pr), irho2);
+  f[2] = mul(pth, irho2);
+  f[3] = mul(fma(-a, PiD, TiS), irho2);
+  const T pr2 = mul(pr, pr);
+  const T F = fma(Tq, TiS, fma(-P, PiD, fma(pth, pth, mul(Delta, pr2))));
+  const T m4r = -twice(twice(r));  // -4 r
+  const T dFr = fma(mul(bh.two, sub(r, bh.M)), fma(PiD, PiD, pr2), mul(mul(m4r, pt), PiD));
+  const T dFth = mul(mul(mul(bh.two, mul(sc, is2)), Tq), fma(mul(bh.two, a), pt, -TiS));
+  const T mh = mul(-bh.half, irho2);
+  f[4] = mul(mh, fma(mul(mul(-bh.two, r), F), irho2, dFr));
+  f[5] = mul(mh, fma(mul(mul(bh.two_a2, sc), F), irho2, dFth));
 }
 
 // ---------------------------------------------------------------------------
@@ -502,21 +507,25 @@ struct Adm {
 // apart (the product of all four would overflow near r = 10^4).
 template <typename T, bool kFastRcp = true>
 __device__ __forceinline__ void adm_kerr_sc(const BH<T>& bh, T r, T s, T c, Adm<T>& m) {
+  auto mul = [&](T x, T y) { return vmul<T>(bh, x, y); };
+  auto add = [&](T x, T y) { return vadd<T>(bh, x, y); };
+  auto sub = [&](T x, T y) { return vsub<T>(bh, x, y); };
   const T a2 = bh.a2;
-  const T s2 = s * s, sc = s * c;
-  const T rho2 = fma(a2, c * c, r * r);
-  const T Delta = fma(r, r - bh.twoM, a2);
+  const T s2 = mul(s, s), sc = mul(s, c);
+  const T rho2 = fma(a2, mul(c, c), mul(r, r));
+  const T Delta = fma(r, sub(r, bh.twoM), a2);
   const T r2a2 = fma(r, r, a2);
-  const T Sigma = fma(r2a2, r2a2, -(a2 * Delta) * s2);
-  const T rD = rho2 * Delta;
+  const T Sigma = fma(r2a2, r2a2, mul(-mul(a2, Delta), s2));
+  const T rD = mul(rho2, Delta);
   T irho2, iDelta, iSigma, is2;
   if constexpr (sizeof(T) == 8) {
-    const T SS = Sigma * s2;
-    const T inv = kFastRcp ? recip<T>(rD * SS) : T(1) / (rD * SS);
-    irho2 = Delta * SS * inv;
-    iDelta = rho2 * SS * inv;
-    iSigma = rD * s2 * inv;
-    is2 = rD * Sigma * inv;
+    const T SS = mul(Sigma, s2);
+    const T den = mul(rD, SS);
+    const T inv = kFastRcp ? recip<T>(den, bh.one) : T(1) / den;
+    irho2 = mul(mul(Delta, SS), inv);
+    iDelta = mul(mul(rho2, SS), inv);
+    iSigma = mul(mul(rD, s2), inv);
+    is2 = mul(mul(rD, Sigma), inv);
   } else {
     const T inv = T(1) / (rD * s2);
     irho2 = Delta * s2 * inv;
@@ -524,31 +533,32 @@ __device__ __forceinline__ void adm_kerr_sc(const BH<T>& bh, T r, T s, T c, Adm<
     is2 = rD * inv;
     iSigma = T(1) / Sigma;
   }
-  m.alpha2 = rD * iSigma;
-  m.ialpha2 = Sigma * irho2 * iDelta;
-  m.beta = -bh.twoM * bh.a * r * iSigma;
-  m.gam[0] = rho2 * iDelta;
+  m.alpha2 = mul(rD, iSigma);
+  m.ialpha2 = mul(mul(Sigma, irho2), iDelta);
+  const T m2Ma = mul(-bh.twoM, bh.a);  // -2 M a
+  m.beta = mul(mul(m2Ma, r), iSigma);
+  m.gam[0] = mul(rho2, iDelta);
   m.gam[1] = rho2;
-  m.gam[2] = Sigma * s2 * irho2;
-  m.igam[0] = Delta * irho2;
+  m.gam[2] = mul(mul(Sigma, s2), irho2);
+  m.igam[0] = mul(Delta, irho2);
   m.igam[1] = irho2;
-  m.igam[2] = rho2 * iSigma * is2;
-  const T a2sc2 = T(2) * a2 * sc;
-  const T lrho_r = twice(r) * irho2, lrho_t = -a2sc2 * irho2;
-  const T dDr = T(2) * (r - bh.M);
-  const T lD_r = dDr * iDelta;
-  const T lS_r = fma(T(4) * r, r2a2, -(a2 * s2) * dDr) * iSigma;
-  const T lS_t = -a2sc2 * Delta * iSigma;
-  m.dlna[0] = T(0.5) * (lrho_r + lD_r - lS_r);
-  m.dlna[1] = T(0.5) * (lrho_t - lS_t);
-  m.dbeta[0] = fma(-m.beta, lS_r, -bh.twoM * bh.a * iSigma);
-  m.dbeta[1] = -m.beta * lS_t;
-  m.dlng[0][0] = lrho_r - lD_r;
+  m.igam[2] = mul(mul(rho2, iSigma), is2);
+  const T a2sc2 = mul(bh.two_a2, sc);
+  const T lrho_r = mul(twice(r), irho2), lrho_t = mul(-a2sc2, irho2);
+  const T dDr = mul(bh.two, sub(r, bh.M));
+  const T lD_r = mul(dDr, iDelta);
+  const T lS_r = mul(fma(twice(twice(r)), r2a2, mul(-mul(a2, s2), dDr)), iSigma);
+  const T lS_t = mul(mul(-a2sc2, Delta), iSigma);
+  m.dlna[0] = mul(bh.half, sub(add(lrho_r, lD_r), lS_r));
+  m.dlna[1] = mul(bh.half, sub(lrho_t, lS_t));
+  m.dbeta[0] = fma(-m.beta, lS_r, mul(m2Ma, iSigma));
+  m.dbeta[1] = mul(-m.beta, lS_t);
+  m.dlng[0][0] = sub(lrho_r, lD_r);
   m.dlng[0][1] = lrho_t;
   m.dlng[1][0] = lrho_r;
   m.dlng[1][1] = lrho_t;
-  m.dlng[2][0] = lS_r - lrho_r;
-  m.dlng[2][1] = fma(T(2) * sc, is2, lS_t - lrho_t);
+  m.dlng[2][0] = sub(lS_r, lrho_r);
+  m.dlng[2][1] = fma(mul(bh.two, sc), is2, sub(lS_t, lrho_t));
 }
 
 template <typename T>
@@ -561,19 +571,20 @@ __device__ __forceinline__ void adm_kerr(const BH<T>& bh, T r, T th, Adm<T>& m) 
 // The 3+1 right-hand side f = (dt, dr, dth, dph, dp_r, dp_th)/dl at one
 // point of any provider (formulas above).
 template <typename T>
-__device__ __forceinline__ void adm_rhs(const Adm<T>& m, T pt, T pr, T pth, T pph, T f[6]) {
+__device__ __forceinline__ void adm_rhs(const BH<T>& bh, const Adm<T>& m, T pt, T pr, T pth, T pph, T f[6]) {
+  auto mul = [&](T x, T y) { return vmul<T>(bh, x, y); };
   const T A = fma(-m.beta, pph, pt);
-  const T u = A * m.ialpha2;
-  const T vr = pr * m.igam[0], vth = pth * m.igam[1], vph = pph * m.igam[2];
+  const T u = mul(A, m.ialpha2);
+  const T vr = mul(pr, m.igam[0]), vth = mul(pth, m.igam[1]), vph = mul(pph, m.igam[2]);
   f[0] = -u;
   f[1] = vr;
   f[2] = vth;
   f[3] = fma(m.beta, u, vph);
-  const T qr = T(0.5) * pr * vr, qth = T(0.5) * pth * vth, qph = T(0.5) * pph * vph;
+  const T qr = mul(mul(bh.half, pr), vr), qth = mul(mul(bh.half, pth), vth), qph = mul(mul(bh.half, pph), vph);
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const T kin = fma(qph, m.dlng[2][k], fma(qth, m.dlng[1][k], qr * m.dlng[0][k]));
-    f[4 + k] = fma(-u, fma(pph, m.dbeta[k], A * m.dlna[k]), kin);
+    const T kin = fma(qph, m.dlng[2][k], fma(qth, m.dlng[1][k], mul(qr, m.dlng[0][k])));
+    f[4 + k] = fma(-u, fma(pph, m.dbeta[k], mul(A, m.dlna[k])), kin);
   }
 }
 
@@ -584,7 +595,7 @@ __device__ __forceinline__ void ham_rhs_sc(const BH<T>& bh, T r, T s, T c, T pt,
   if constexpr (kForm == kHamAdm) {
     Adm<T> m;
     adm_kerr_sc<T, kFastRcp>(bh, r, s, c, m);
-    adm_rhs<T>(m, pt, pr, pth, pph, f);
+    adm_rhs<T>(bh, m, pt, pr, pth, pph, f);
   } else {
     ham_kerr<T, kFastRcp>(bh, r, s, c, pt, pr, pth, pph, f);
   }
@@ -610,7 +621,7 @@ __device__ __forceinline__ void adm_lower(const Adm<double>& m, const double u[4
 // u^mu = g^{mu nu} p_nu from the 3+1 quantities (the first half of adm_rhs).
 __device__ __forceinline__ void adm_raise(const Adm<double>& m, const double p[4], double u[4]) {
   double f[6];
-  adm_rhs<double>(m, p[0], p[1], p[2], p[3], f);
+  adm_rhs<double>(make_bh<double>(1.0, 0.0), m, p[0], p[1], p[2], p[3], f);
 #pragma unroll
   for (int j = 0; j < 4; ++j) u[j] = f[j];
 }
