@@ -568,6 +568,17 @@ int malbec_measure_step_loop(uint32_t form, double* steps_per_s);
  * Blocks the calling thread. */
 int malbec_check_fp64_helpers(double err[4]);
 
+/* Self-check of the operand forms the kernels compute in (not in the paper),
+ * bit for bit on 2^22 seeded samples of every class of value (zeros,
+ * subnormals, normals, infinities, NaN; a NaN matches a NaN): counts[0..2]:
+ * mismatches of the FP64 forms fma(x, y, -0), fma(x, 1, y), fma(x, 1, -y)
+ * (constants in per-thread registers) against x*y, x + y, x - y; counts[3]:
+ * of the exponent doubling against x + x (finite normal x); counts[4..6]: of
+ * the paired FP32 add, subtract, and multiply and fma against the scalar
+ * operations; counts[7]: of the paired compensated update against the scalar
+ * one.  MALBEC_EINVAL for a null pointer.  Blocks the calling thread. */
+int malbec_check_operand_forms(uint64_t counts[8]);
+
 /* Bounded device-side waits (not in the paper).  The one wait a trace
  * kernel makes on other warps is the zone warp's wait for the rest of its
  * block (launch configuration, zone_wait_limit_us); when it runs out the

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmalbec.so")
 SOURCES = ["api.cu", "trace.cu", "ic.cu", "peaks.cu", "noalloc.cu", "bundles.cu", "server.cu"]
-HEADERS = ["geodesic.cuh", "camera.cuh", "bound.cuh", "internal.h"]
+HEADERS = ["geodesic.cuh", "camera.cuh", "bound.cuh", "fp32pair.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no implicit multiply-add contraction, so every kernel that
 # evaluates the same source expression rounds it the same way (results of a

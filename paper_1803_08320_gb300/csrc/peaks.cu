@@ -6,6 +6,7 @@
 // reciprocal against CUDA's sincos and division.
 #include <string.h>
 
+#include "fp32pair.cuh"
 #include "geodesic.cuh"
 #include "internal.h"
 
@@ -161,6 +162,60 @@ __global__ void helpers_check_kernel(unsigned long long* err, uint64_t n) {
   }
 }
 
+
+// Operand forms against the plain operations, bit for bit: FP64 fma(x, y, -0)
+// against x*y, fma(x, 1, y) against x + y and fma(x, 1, -y) against x - y
+// (-0 and 1 in per-thread registers, as the trace kernels hold them), twice(x)
+// against x + x for finite normal x; the paired FP32 add, subtract, multiply
+// and fma and comp_add2 against their scalar forms.  Operands: seeded random
+// bit patterns (every class: zeros, subnormals, normals, infinities, NaN)
+// and, every fourth draw, random magnitudes near each other; a NaN result
+// matches a NaN result.  cnt[k]: mismatches of check k.
+__device__ __forceinline__ bool same64(double a, double b) {
+  return (a != a && b != b) || __double_as_longlong(a) == __double_as_longlong(b);
+}
+__device__ __forceinline__ bool same32(float a, float b) {
+  return (a != a && b != b) || __float_as_int(a) == __float_as_int(b);
+}
+__device__ __forceinline__ double draw64(unsigned long long h, unsigned long long g) {
+  if ((g & 3ull) == 0ull) return ldexp(1.0 + (double)(h >> 12) * 0x1.0p-52, (int)(h % 41ull) - 20) * ((h >> 7) & 1 ? -1.0 : 1.0);
+  return __longlong_as_double((long long)h);
+}
+__device__ __forceinline__ float draw32(unsigned long long h, unsigned long long g) {
+  if ((g & 3ull) == 0ull) return ldexpf(1.0f + (float)(h >> 41) * 0x1.0p-23f, (int)(h % 41ull) - 20) * ((h >> 7) & 1 ? -1.f : 1.f);
+  return __int_as_float((int)(h >> 16));
+}
+__global__ void operand_forms_kernel(unsigned long long* cnt, uint64_t n, unsigned long long lane_zero) {
+  const BH<double> b = make_bh<double>(1.0, 0.5, (unsigned long long)threadIdx.x & lane_zero);
+  unsigned long long c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long h1 = mix64(4 * i), h2 = mix64(4 * i + 1), h3 = mix64(4 * i + 2), h4 = mix64(4 * i + 3);
+    const double x = draw64(h1, h3), y = draw64(h2, h3 >> 2);
+    c[0] += !same64(vmul(b, x, y), x * y);
+    c[1] += !same64(vadd(b, x, y), x + y);
+    c[2] += !same64(vsub(b, x, y), x - y);
+    const double xn = ldexp(1.0 + (double)(h4 >> 12) * 0x1.0p-52, (int)(h4 % 2045ull) - 1022);  // finite normal
+    c[3] += !same64(twice(xn), xn + xn) || !same64(twice(-xn), -xn - xn);
+    const float2 p = make_float2(draw32(h1, h3), draw32(h2, h4)), q = make_float2(draw32(h3, h1), draw32(h4, h2));
+    const float2 r = make_float2(draw32(h1 ^ h4, h2), draw32(h2 ^ h3, h1));
+    const float2 sa = f2add(p, q), ss = f2sub(p, q), sm = f2mul(p, q), sf = f2fma(p, q, r);
+    c[4] += !same32(sa.x, p.x + q.x) || !same32(sa.y, p.y + q.y);
+    c[5] += !same32(ss.x, p.x - q.x) || !same32(ss.y, p.y - q.y);
+    c[6] += !same32(sm.x, p.x * q.x) || !same32(sm.y, p.y * q.y) || !same32(sf.x, fmaf(p.x, q.x, r.x)) ||
+            !same32(sf.y, fmaf(p.y, q.y, r.y));
+    // comp_add2 on a compensated pair against comp_add per component
+    float2 hi2 = make_float2(p.x, q.x), lo2 = make_float2(p.x * 0x1.0p-30f, q.x * 0x1.0p-30f);
+    const float2 d2 = make_float2(r.x, r.y), e2 = make_float2(r.x * 0x1.0p-30f, r.y * 0x1.0p-30f);
+    float h0 = hi2.x, l0 = lo2.x, hh = hi2.y, ll = lo2.y;
+    comp_add(h0, l0, d2.x, e2.x);
+    comp_add(hh, ll, d2.y, e2.y);
+    comp_add2(hi2, lo2, d2, e2);
+    c[7] += !same32(hi2.x, h0) || !same32(lo2.x, l0) || !same32(hi2.y, hh) || !same32(lo2.y, ll);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (c[k]) atomicAdd(&cnt[k], c[k]);
+}
 }  // namespace
 }  // namespace malbec
 
@@ -195,4 +250,22 @@ extern "C" int malbec_measure_fma_peak(malbec_precision prec, double* gflops) {
   if (prec == MALBEC_FP64) return malbec::measure<double>(4000, gflops);
   if (prec == MALBEC_FP32_MIXED) return malbec::measure<float>(200000, gflops);
   return MALBEC_EINVAL;
+}
+
+extern "C" int malbec_check_operand_forms(uint64_t counts[8]) {
+  if (!counts) return MALBEC_EINVAL;
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 8 * sizeof(unsigned long long));
+  if (e != cudaSuccess) return malbec::set_cuda_error(e);
+  e = cudaMemset(d, 0, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    malbec::operand_forms_kernel<<<1024, 256>>>(d, 1ull << 22, 0ull);
+    e = cudaGetLastError();
+  }
+  unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return malbec::set_cuda_error(e);
+  for (int k = 0; k < 8; ++k) counts[k] = h[k];
+  return MALBEC_OK;
 }

@@ -135,6 +135,7 @@ def _declare(L):
     sig("malbec_measure_fma_peak", ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D))
     sig("malbec_measure_step_loop", ctypes.c_int, _U32, ctypes.POINTER(_D))
     sig("malbec_check_fp64_helpers", ctypes.c_int, ctypes.POINTER(_D))
+    sig("malbec_check_operand_forms", ctypes.c_int, ctypes.POINTER(_U64))
     sig("malbec_bundle_out_bytes", _SZ, ctypes.POINTER(Bundle), ctypes.c_int)
     sig("malbec_trace_bundles", ctypes.c_int, ctypes.POINTER(Bundle), _U32, ctypes.c_int, _VP)
     sig("malbec_plan_create", ctypes.c_int, ctypes.POINTER(Bundle), _U32, ctypes.c_int, ctypes.POINTER(_VP))
@@ -680,3 +681,15 @@ def check_fp64_helpers() -> dict:
     e = (_D * 4)()
     _check(lib().malbec_check_fp64_helpers(e), "malbec_check_fp64_helpers")
     return {"sin_abs": e[0], "cos_abs": e[1], "recip_ulp": e[2], "recip_estimate_rel": e[3]}
+
+
+def check_operand_forms() -> dict:
+    """Mismatch counts of the kernels' operand forms against the plain
+    operations, bit for bit (blocks the caller): FP64 fma(x, y, -0),
+    fma(x, 1, y), fma(x, 1, -y), the exponent doubling, and the paired FP32
+    add, subtract, multiply/fma and compensated update."""
+    c = (_U64 * 8)()
+    _check(lib().malbec_check_operand_forms(c), "malbec_check_operand_forms")
+    keys = ("fp64_mul", "fp64_add", "fp64_sub", "fp64_twice", "fp32x2_add", "fp32x2_sub", "fp32x2_mul_fma",
+            "fp32x2_comp_add")
+    return dict(zip(keys, (int(v) for v in c)))
