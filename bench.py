@@ -33,7 +33,7 @@ METRIC = "RK4 geodesic steps/s at stated error vs FP64 oracle; p50/p99 request l
 UNIT = "steps/s"
 WORKLOAD = "kerr_camera_a0.9_1024x1024_incl80_fov25_h0.05r_cap2e4"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-KERNEL_SOURCES = ["geodesic.cuh", "camera.cuh", "trace.cu"]
+KERNEL_SOURCES = ["geodesic.cuh", "camera.cuh", "fp32pair.cuh", "trace_kernel.cuh", "trace.cu", "trace_dopri.cu"]
 
 
 def kernel_source_hash() -> str:
@@ -1256,6 +1256,36 @@ def main():
                   "note": "Dormand-Prince 5(4) (MALBEC_METHOD_DOPRI5), the same camera; accuracy compared by "
                           "the drift of E, L_z, Q and g(u,u) (exact invariants of the flow), since the final "
                           "angles of escaped rays depend on where each method's last step crosses r_esc"}
+        # the adaptive method in FP32_MIXED (rtol >= 1e-6) against FP64 at the
+        # same tolerance, same protocol
+        term_dm = dataclasses.replace(term_dp, rtol=1e-6, atol=1e-6)
+        cwm = CameraRun(cw.M, cw.a, term_dm)
+        dm_runs = {}
+        for prec in ("fp64", "fp32_mixed"):
+            for _ in range(args.warmup):
+                mb.trace_camera(cw.M, cw.a, cam, term_dm, prec, stream=stream, out=out)
+            barrier()
+            torch.cuda.synchronize()
+            tt_, rr_ = timed_renders(mb, cwm, cam, prec, args.steps, stream, flush, out=out)
+            torch.cuda.synchronize()
+            barrier()
+            rr_ = {k: v.clone() for k, v in rr_.items() if k in ("fate", "steps", "theta", "phi")}
+            att_ = int(rr_["steps"].to(torch.int64).sum().item())
+            t_ = max_over_ranks(sum(tt_) / 1e3)
+            dm_runs[prec] = (world * att_ * args.steps / t_, 1e3 * t_ / args.steps, rr_)
+        r64_, r32_ = dm_runs["fp64"][2], dm_runs["fp32_mixed"][2]
+        esc_m = (r64_["fate"] == mb.FATE_ESCAPED) & (r32_["fate"] == mb.FATE_ESCAPED)
+        dopri5["fp32_mixed_rtol1e-6"] = {
+            "value": dm_runs["fp32_mixed"][0], "unit": "attempts/s", "ms_per_step": dm_runs["fp32_mixed"][1],
+            "fp64_same_tolerance": {"value": dm_runs["fp64"][0], "ms_per_step": dm_runs["fp64"][1]},
+            "speedup_vs_fp64_same_tolerance": dm_runs["fp32_mixed"][0] / dm_runs["fp64"][0],
+            "fate_agreement_vs_fp64_same_tolerance": float(((r32_["fate"] & mb.FATE_MASK) == (r64_["fate"] & mb.FATE_MASK))
+                                                           .float().mean().item()),
+            "escaped_difference_vs_fp64_same_tolerance": err_stats(torch, (r32_["theta"][esc_m] - r64_["theta"][esc_m]).abs(),
+                                                                   (r32_["phi"][esc_m] - r64_["phi"][esc_m]).abs()),
+            "tolerance": {"rtol": 1e-6, "atol": 1e-6, "max_step": "0.5 r"},
+            "note": "FP32 attempts on the compensated state, FP64 attempts in the FP64 zones; the difference to "
+                    "FP64 at the same tolerance is of the size of the method's own error at that tolerance"}
 
         esc_b = (fate_bl == mb.FATE_ESCAPED) & (fate_adm == mb.FATE_ESCAPED)
         d_b = (theta_adm[esc_b] - theta_bl[esc_b]).abs()

@@ -152,14 +152,24 @@ typedef struct {
  *                         stage points, as for RK4), escape on accepted
  *                         steps.  Any form (in the canonical forms p_t and
  *                         p_ph stay exactly constant, as with RK4).  Requires
- *                         atol > 0, rtol >= 0 and MALBEC_FP64; every entry
+ *                         atol > 0 and rtol >= 0.  MALBEC_FP64: every entry
  *                         point (bundles and servers as for the forms).
+ *                         MALBEC_FP32_MIXED (malbec_trace and
+ *                         malbec_trace_camera): attempts in FP32 on the
+ *                         compensated state, in FP64 in the FP64 zones, the
+ *                         error norm and the step rule in the precision of
+ *                         the attempt; requires rtol >=
+ *                         MALBEC_DOPRI5_MIXED_RTOL_MIN (an FP32 error
+ *                         estimate carries rounding noise of ~1e-7 of the
+ *                         state); other entry points: MALBEC_EINVAL.
  * rtol, atol: the tolerances of MALBEC_METHOD_DOPRI5 (ignored by RK4). */
 #define MALBEC_FORM_GEODESIC 0
 #define MALBEC_FORM_HAMILTONIAN 1
 #define MALBEC_FORM_ADM 2
 #define MALBEC_METHOD_RK4 0
 #define MALBEC_METHOD_DOPRI5 1
+/* smallest rtol of MALBEC_METHOD_DOPRI5 in MALBEC_FP32_MIXED */
+#define MALBEC_DOPRI5_MIXED_RTOL_MIN 1e-6
 typedef struct {
   double eps_hor;
   double r_esc;

@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmalbec.so")
-SOURCES = ["api.cu", "trace.cu", "ic.cu", "peaks.cu", "noalloc.cu", "bundles.cu", "server.cu"]
-HEADERS = ["geodesic.cuh", "camera.cuh", "bound.cuh", "fp32pair.cuh", "internal.h"]
+SOURCES = ["api.cu", "trace.cu", "trace_dopri.cu", "ic.cu", "peaks.cu", "noalloc.cu", "bundles.cu", "server.cu"]
+HEADERS = ["geodesic.cuh", "camera.cuh", "bound.cuh", "fp32pair.cuh", "trace_kernel.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no implicit multiply-add contraction, so every kernel that
 # evaluates the same source expression rounds it the same way (results of a

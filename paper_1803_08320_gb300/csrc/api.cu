@@ -48,10 +48,12 @@ int check_term(const malbec_term& t, const malbec_metric& m) {
   return MALBEC_OK;
 }
 
-// The adaptive method runs in FP64 only.
-int check_method_precision(const malbec_term& t, malbec_precision prec) {
-  if (t.method == MALBEC_METHOD_DOPRI5 && prec != MALBEC_FP64) return MALBEC_EINVAL;
-  return MALBEC_OK;
+// The adaptive method runs in FP64 on every entry point, and in FP32_MIXED
+// on the direct traces (mixed_ok) when rtol >= MALBEC_DOPRI5_MIXED_RTOL_MIN.
+int check_method_precision(const malbec_term& t, malbec_precision prec, bool mixed_ok) {
+  if (t.method != MALBEC_METHOD_DOPRI5 || prec == MALBEC_FP64) return MALBEC_OK;
+  if (mixed_ok && prec == MALBEC_FP32_MIXED && t.rtol >= MALBEC_DOPRI5_MIXED_RTOL_MIN) return MALBEC_OK;
+  return MALBEC_EINVAL;
 }
 
 namespace {
@@ -90,12 +92,13 @@ malbec_launch_config launch_config() {
 
 // Launch shape: persistent warps, as many as fit (occupancy) but no more than
 // the rays need; small batches spread one warp per block across the SMs.
-int choose_shape(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, LaunchShape* shape, int* refill_min) {
-  return choose_shape_cfg(kerr, mixed, src, sink, n, launch_config(), shape, refill_min);
+int choose_shape(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, LaunchShape* shape, int* refill_min,
+                 int form, int method) {
+  return choose_shape_cfg(kerr, mixed, src, sink, n, launch_config(), shape, refill_min, form, method);
 }
 
 int choose_shape_cfg(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, const malbec_launch_config& cfg,
-                     LaunchShape* shape, int* refill_min) {
+                     LaunchShape* shape, int* refill_min, int form, int method) {
   int sms = 0;
   int rc = device_sms(&sms);
   if (rc) return rc;
@@ -105,8 +108,8 @@ int choose_shape_cfg(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, c
   if (cfg.threads_per_block) tpb = (int)cfg.threads_per_block;
   // the exchange as launch_trace will decide it: off for whole-image cameras
   // unless asked for
-  const bool banks = mixed && (cfg.exchange ? cfg.exchange == 1 : src != kSrcCamera);
-  int per_sm = trace_max_blocks_per_sm(kerr, mixed, src, sink, banks, tpb);
+  const bool banks = mixed && method == MALBEC_METHOD_RK4 && (cfg.exchange ? cfg.exchange == 1 : src != kSrcCamera);
+  int per_sm = trace_max_blocks_per_sm(kerr, mixed, src, sink, banks, tpb, form, method);
   if (per_sm <= 0) per_sm = 1;
   // Resident warps per SM.  FP64: one warp per SM sub-partition already
   // saturates the FP64 unit (it costs the same per warp instruction whatever
@@ -153,7 +156,7 @@ namespace {
 int run_trace(TraceParams& p, bool kerr, bool mixed, Source src, Sink sink, cudaStream_t stream) {
   LaunchShape shape;
   int refill_min = 1;
-  int rc = choose_shape(kerr, mixed, src, sink, p.n, &shape, &refill_min);
+  int rc = choose_shape(kerr, mixed, src, sink, p.n, &shape, &refill_min, (int)p.form, (int)p.method);
   if (rc) return rc;
   p.refill_min = refill_min;
   fill_zone(p);
@@ -334,7 +337,7 @@ int malbec_trace(malbec_metric m, const double* ics, uint64_t n, malbec_term t, 
   if (rc) return rc;
   rc = check_term(t, m);
   if (rc) return rc;
-  rc = check_method_precision(t, prec);
+  rc = check_method_precision(t, prec, true);
   if (rc) return rc;
   if (!ics || !out) return MALBEC_EINVAL;
   malbec_layout L;
@@ -420,7 +423,7 @@ int malbec_trace_camera(malbec_metric m, const malbec_camera* cam, malbec_term t
   if (rc) return rc;
   if (!out || ((uintptr_t)out & 255u) != 0) return MALBEC_EINVAL;
   if (prec != MALBEC_FP64 && prec != MALBEC_FP32_MIXED) return MALBEC_EINVAL;
-  rc = check_method_precision(t, prec);
+  rc = check_method_precision(t, prec, true);
   if (rc) return rc;
   malbec_camera_layout L;
   rc = malbec_camera_out_layout(cam, &L);

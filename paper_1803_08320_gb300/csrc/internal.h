@@ -119,9 +119,13 @@ struct LaunchShape {
 // trace.cu
 cudaError_t launch_trace(const TraceParams& p, bool kerr, bool mixed, Source src, Sink sink,
                          const LaunchShape& shape, cudaStream_t stream);
+// trace_dopri.cu: the Dormand-Prince kernel for (mixed, src, sink, form), or
+// nullptr if there is none
+const void* pick_dopri(bool mixed, Source src, Sink sink, int form);
 // resident blocks per SM of the geodesic RK4 kernel of (kerr, mixed, src,
 // sink), with (banks) or without the FP32_MIXED block ray exchange
-int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, bool banks, int threads_per_block);
+int trace_max_blocks_per_sm(bool kerr, bool mixed, Source src, Sink sink, bool banks, int threads_per_block,
+                            int form = MALBEC_FORM_GEODESIC, int method = MALBEC_METHOD_RK4);
 // total of the device-wide counter of zone-warp waits that ran out (current device)
 cudaError_t read_wait_timeouts(unsigned long long* total);
 
@@ -143,10 +147,12 @@ int set_cuda_error(cudaError_t e);
 void fill_zone(TraceParams& p);
 int check_metric(const malbec_metric& m);
 int check_term(const malbec_term& t, const malbec_metric& m);
-int check_method_precision(const malbec_term& t, malbec_precision prec);
-int choose_shape(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, LaunchShape* shape, int* refill_min);
+int check_method_precision(const malbec_term& t, malbec_precision prec, bool mixed_ok = false);
+int choose_shape(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, LaunchShape* shape, int* refill_min,
+                 int form = MALBEC_FORM_GEODESIC, int method = MALBEC_METHOD_RK4);
 int choose_shape_cfg(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, const malbec_launch_config& cfg,
-                     LaunchShape* shape, int* refill_min);
+                     LaunchShape* shape, int* refill_min, int form = MALBEC_FORM_GEODESIC,
+                     int method = MALBEC_METHOD_RK4);
 int check_camera_desc(const malbec_metric& m, const malbec_camera* cam, const malbec_term* t);
 
 // bundles.cu

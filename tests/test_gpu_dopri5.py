@@ -198,10 +198,14 @@ def test_unsupported_combinations_are_rejected(mb):
     ics[1] = 10.0
     ics[2] = 1.0
     ics[4] = 1.2
+    # FP32_MIXED takes the adaptive method at rtol >= MALBEC_DOPRI5_MIXED_RTOL_MIN only
     with pytest.raises(mb.MalbecError):
         gpu_trace(mb, 1.0, 0.5, ics, dp_term(mb), precision="fp32_mixed")
+    with pytest.raises(mb.MalbecError):
+        gpu_trace(mb, 1.0, 0.5, ics, dp_term(mb, tol=0.5e-6), precision="fp32_mixed")
+    assert gpu_trace(mb, 1.0, 0.5, ics, dp_term(mb, tol=1e-6, n_steps_cap=50), precision="fp32_mixed")["fate"].size == 4
     # job tables and servers run Dormand-Prince in FP64 only
-    b = mb.make_bundle(mb.BUNDLE_BOUND, 4, 1.0, 0.5, dp_term(mb), seed=1)
+    b = mb.make_bundle(mb.BUNDLE_BOUND, 4, 1.0, 0.5, dp_term(mb, tol=1e-6), seed=1)
     with pytest.raises(mb.MalbecError):
         mb.attach_outputs([b], "fp32_mixed")
         mb.trace_bundles([b], "fp32_mixed")
@@ -226,6 +230,9 @@ def test_noalloc_entry_point_gives_the_same_bits(mb, W):
         assert torch.equal(a[k], b[k]), k
     with pytest.raises(mb.MalbecError):
         mb.trace_noalloc(wl.M, 0.0, ics, t, out, precision="fp32_mixed", a_per_ray=spins)
+    with pytest.raises(mb.MalbecError):
+        mb.trace_noalloc(wl.M, 0.0, ics, dp_term(mb, tol=1e-6, n_steps_cap=500), out, precision="fp32_mixed",
+                         a_per_ray=spins)
 
 
 def test_every_form_conserves_the_invariants(mb, W):
@@ -247,3 +254,79 @@ def test_every_form_conserves_the_invariants(mb, W):
         assert (d[2:].amax(dim=0) <= 1500 * 1e-11).float().mean().item() >= 0.95, f
         if f != 0:
             assert d[:2].max().item() < 1e-12, f
+
+
+# --------------------------------------------------------------------------- FP32_MIXED
+def test_mixed_camera_against_the_oracle(mb, orc, W, form):
+    """The adaptive method in FP32_MIXED (FP32 attempts on the compensated
+    state, FP64 attempts in the FP64 zones) at rtol = atol = 1e-6 on a 48 x 48
+    Kerr a = 0.9 camera, against the oracle's method 1 at the same tolerance
+    and against the oracle at 1e-11.  Away from the critical curve and the
+    polar axis: terminations equal the oracle's on >= 99.9% of the pixels
+    (measured 100%); the escaped angles equal the oracle's to a median of
+    1e-6 (measured 6e-8: most rays take the oracle's sequence of attempts);
+    and against the 1e-11 render the FP32_MIXED error is the method's own at
+    this tolerance -- its p99 within 1.2x the oracle's own p99 at 1e-6 (both
+    measured 3.7e-3 to 6.0e-3)."""
+    import math
+
+    import torch
+
+    from test_gpu_parity import _camera_near, _pixel_ab, sin_theta_turn
+
+    cw = W.camera(nx=48, ny=48)
+    t = dp_term(mb, tol=1e-6, dl=0.0, dl_r_scale=0.5, n_steps_cap=20_000, form=form)
+    cam = mb.make_camera(cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny)
+    res = mb.trace_camera(cw.M, cw.a, cam, t, "fp32_mixed")
+    torch.cuda.synchronize()
+    got = {k: np_(v) for k, v in res.items() if k != "buffer"}
+    pix = np.arange(cw.n)
+    ics = orc.camera_ics(cw.M, cw.a, cw.r_obs, cw.incl, cw.fov_half, cw.nx, cw.ny, pix)
+    ref = orc.trace_many(cw.M, cw.a, ics, oracle_term(orc, t))
+    tight = orc.trace_many(cw.M, cw.a, ics, oracle_term(orc, dp_term(mb, tol=1e-11, dl=0.0, dl_r_scale=0.5,
+                                                                        n_steps_cap=20_000, form=form)))
+    al, be = _pixel_ab(cw, pix)
+    Lz = -al * math.sin(cw.incl)
+    Q = be * be + math.cos(cw.incl) ** 2 * (al * al - cw.a * cw.a)
+    sel = ~_camera_near(orc, cw, pix) & (sin_theta_turn(1.0, Lz, Q, cw.a, 0.0) >= 0.05)
+    m = mb.FATE_MASK
+    same = (got["fate"] & m) == (ref["fate"] & m)
+    esc = sel & (got["fate"] == mb.FATE_ESCAPED) & (ref["fate"] == mb.FATE_ESCAPED) & \
+        (tight["fate"] == mb.FATE_ESCAPED)
+    e_same = np.abs(got["theta"][esc] - ref["y"][2][esc])
+    e_mixed = np.abs(got["theta"][esc] - tight["y"][2][esc])
+    e_oracle = np.abs(ref["y"][2][esc] - tight["y"][2][esc])
+    print("form", form, "fates", same[sel].mean(), "escaped", esc.sum(), "theta vs same tol median",
+          np.median(e_same), "p99 vs 1e-11: mixed", np.quantile(e_mixed, 0.99), "oracle", np.quantile(e_oracle, 0.99))
+    assert sel.sum() > 1000 and esc.sum() > 600
+    assert same[sel].mean() >= 0.999
+    assert np.median(e_same) <= 1e-6
+    assert np.quantile(e_mixed, 0.99) <= 1.2 * np.quantile(e_oracle, 0.99)
+
+
+def test_mixed_bound_orbits_keep_the_invariants_as_fp64(mb, orc, W, form):
+    """512 generic bound orbits, 3000 attempts at rtol = atol = 1e-6: the
+    FP32_MIXED adaptive method drifts from E, L_z, Q and g(u,u) as the FP64
+    one does at the same tolerance (median and p99 of each within 1.5x of
+    FP64's, measured within 5%: the error is the method's, not FP32
+    rounding's), and in the canonical forms E and L_z stay exact to the
+    conversions at the two ends (<= 1e-13)."""
+    wl = W.bound()
+    idx = wl.subsample(512)
+    ys, spins, _ = orc.bound_samples(wl.M, wl.a_max, wl.seed, idx)
+    t = dp_term(mb, tol=1e-6, n_steps_cap=3000, form=form)
+    runs = {p: gpu_trace(mb, wl.M, 0.0, ys, t, a_per_ray=spins, precision=p) for p in ("fp64", "fp32_mixed")}
+    capped = np.ones(ys.shape[1], dtype=bool)
+    for r in runs.values():
+        capped &= (r["fate"] & mb.FATE_MASK) == mb.FATE_CAPPED
+    assert capped.mean() > 0.95
+
+    def drift(r):
+        return np.abs(r["inv1"][:, capped] - r["inv0"][:, capped]) / np.maximum(np.abs(r["inv0"][:, capped]), 1.0)
+
+    d64, d32 = drift(runs["fp64"]), drift(runs["fp32_mixed"])
+    for c in (2, 3) if form != 0 else (0, 1, 2, 3):
+        for qq in (0.5, 0.99):
+            assert np.quantile(d32[c], qq) <= 1.5 * np.quantile(d64[c], qq) + 1e-12, (c, qq)
+    if form != 0:
+        assert d32[:2].max() <= 1e-13
