@@ -772,6 +772,12 @@ __device__ __forceinline__ double dopri5_attempt(const BH<double>& bh, double h,
                                                  const double k1[8], double y5[8], double e[8], double k7[8]) {
   double s0, c0;
   sincos(y[2], &s0, &c0);
+  // the tableau's coefficients as per-thread registers (full-rate DFMAs):
+  // vreg with a zero that depends on this attempt's h, so that each is formed
+  // next to its use instead of all 35 being held through the attempt
+  const unsigned long long vzh =
+      (unsigned long long)__double_as_longlong(h) & ((unsigned long long)__double_as_longlong(bh.nz) & 0x7fffffffffffffffull);
+  auto K = [&](double c) { return vreg(c, vzh); };
   double k2[8], k3[8], k4[8], k5[8], k6[8];
   double d[8];
   double rmin = 0.0;
@@ -799,40 +805,42 @@ __device__ __forceinline__ double dopri5_attempt(const BH<double>& bh, double h,
     rmin = first ? r : fmin(rmin, r);
   };
 #pragma unroll
-  for (int q = 0; q < 8; ++q) d[q] = (1.0 / 5.0) * k1[q];
+  for (int q = 0; q < 8; ++q) d[q] = vmul(bh, K(1.0 / 5.0), k1[q]);
   stage(k2, true);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) d[q] = fma(3.0 / 40.0, k1[q], (9.0 / 40.0) * k2[q]);
+  for (int q = 0; q < 8; ++q) d[q] = fma(K(3.0 / 40.0), k1[q], vmul(bh, K(9.0 / 40.0), k2[q]));
   stage(k3, false);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) d[q] = fma(44.0 / 45.0, k1[q], fma(-56.0 / 15.0, k2[q], (32.0 / 9.0) * k3[q]));
+  for (int q = 0; q < 8; ++q) d[q] = fma(K(44.0 / 45.0), k1[q], fma(K(-56.0 / 15.0), k2[q], vmul(bh, K(32.0 / 9.0), k3[q])));
   stage(k4, false);
 #pragma unroll
   for (int q = 0; q < 8; ++q)
-    d[q] = fma(19372.0 / 6561.0, k1[q],
-               fma(-25360.0 / 2187.0, k2[q], fma(64448.0 / 6561.0, k3[q], (-212.0 / 729.0) * k4[q])));
+    d[q] = fma(K(19372.0 / 6561.0), k1[q],
+               fma(K(-25360.0 / 2187.0), k2[q], fma(K(64448.0 / 6561.0), k3[q], vmul(bh, K(-212.0 / 729.0), k4[q]))));
   stage(k5, false);
 #pragma unroll
   for (int q = 0; q < 8; ++q)
-    d[q] = fma(9017.0 / 3168.0, k1[q],
-               fma(-355.0 / 33.0, k2[q],
-                   fma(46732.0 / 5247.0, k3[q], fma(49.0 / 176.0, k4[q], (-5103.0 / 18656.0) * k5[q]))));
+    d[q] = fma(K(9017.0 / 3168.0), k1[q],
+               fma(K(-355.0 / 33.0), k2[q],
+                   fma(K(46732.0 / 5247.0), k3[q], fma(K(49.0 / 176.0), k4[q], vmul(bh, K(-5103.0 / 18656.0), k5[q])))));
   stage(k6, false);
   // the fifth-order weights (a_2 = 0)
 #pragma unroll
   for (int q = 0; q < 8; ++q)
-    d[q] = fma(35.0 / 384.0, k1[q],
-               fma(500.0 / 1113.0, k3[q], fma(125.0 / 192.0, k4[q], fma(-2187.0 / 6784.0, k5[q], (11.0 / 84.0) * k6[q]))));
+    d[q] = fma(K(35.0 / 384.0), k1[q],
+               fma(K(500.0 / 1113.0), k3[q],
+                   fma(K(125.0 / 192.0), k4[q], fma(K(-2187.0 / 6784.0), k5[q], vmul(bh, K(11.0 / 84.0), k6[q])))));
 #pragma unroll
   for (int q = 0; q < 8; ++q) y5[q] = fma(h, d[q], y[q]);
   stage(k7, false);
   // e = h sum_j (b_j - bhat_j) k_j
 #pragma unroll
   for (int q = 0; q < 8; ++q)
-    e[q] = h * fma(71.0 / 57600.0, k1[q],
-                   fma(-71.0 / 16695.0, k3[q],
-                       fma(71.0 / 1920.0, k4[q],
-                           fma(-17253.0 / 339200.0, k5[q], fma(22.0 / 525.0, k6[q], (-1.0 / 40.0) * k7[q])))));
+    e[q] = vmul(bh, h, fma(K(71.0 / 57600.0), k1[q],
+                   fma(K(-71.0 / 16695.0), k3[q],
+                       fma(K(71.0 / 1920.0), k4[q],
+                           fma(K(-17253.0 / 339200.0), k5[q],
+                               fma(K(22.0 / 525.0), k6[q], vmul(bh, K(-1.0 / 40.0), k7[q])))))));
   return rmin;
 }
 
@@ -845,13 +853,15 @@ __device__ __forceinline__ double dopri5_attempt(const BH<double>& bh, double h,
 // relative size ~1e-16 / tol; on the grid that noise moves the step only
 // when it carries the exponent across an integer, so the sequence of steps
 // does not depend on rounding (and matches any other correct implementation
-// of the same rule) except at those rare crossings.
-__device__ __forceinline__ double dopri5_norm(const double y[8], const double y5[8], const double e[8], double rtol,
-                                              double atol) {
+// of the same rule) except at those rare crossings.  Each component's
+// quotient is a product with the refined reciprocal of the scale (within an
+// ulp of the division, one rounding more), in the full-rate operand forms.
+__device__ __forceinline__ double dopri5_norm(const BH<double>& bh, const double y[8], const double y5[8],
+                                              const double e[8], double rtol, double atol) {
   double s = 0.0;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const double t = e[q] / fma(rtol, fmax(fabs(y[q]), fabs(y5[q])), atol);
+    const double t = vmul(bh, e[q], recip<double>(fma(rtol, fmax(fabs(y[q]), fabs(y5[q])), atol), bh.one));
     s = fma(t, t, s);
   }
   return sqrt(0.125 * s);

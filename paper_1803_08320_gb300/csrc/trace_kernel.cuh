@@ -1310,7 +1310,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
           escaped = false;
           accept = captured || !finite;
           if (!accept) {
-            const double err = dopri5_norm(yd, y5, e, rtol, atol);
+            const double err = dopri5_norm(bh64, yd, y5, e, rtol, atol);
             accept = err <= 1.0;
             hn_f = (float)(h * dopri5_factor(err, accept, after_reject));
             after_reject = !accept;
@@ -1368,7 +1368,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
         escaped = false;
         bool accept = captured || !finite;
         if (!accept) {
-          const double err = dopri5_norm(y, y5, e, rtol, atol);
+          const double err = dopri5_norm(bh64, y, y5, e, rtol, atol);
           accept = err <= 1.0;
           h_next = h * dopri5_factor(err, accept, after_reject);
           after_reject = !accept;
