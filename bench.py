@@ -1123,7 +1123,7 @@ def main():
         return {"steps_per_s": loop[form], "frac": fl * loop[form] / 1e9 / peak64,
                 "kernel_over_ceiling": kernel_rate / loop[form],
                 "note": "malbec_measure_step_loop: the same RK4 step with no queue, termination or output, "
-                        "one warp per SM sub-partition (more warps or rays per thread measured no faster)"}
+                        "two warps per SM sub-partition, as the FP64 trace kernels"}
     barrier, max_over_ranks = ranks.barrier, ranks.max
 
     with torch.cuda.stream(stream):

@@ -562,8 +562,8 @@ int malbec_measure_fma_peak(malbec_precision prec, double* gflops);
  * kernels take (same right-hand side, Sec. 2 eq. kerr with eq. geo, eq. Ham
  * or eq. ADM, and the classical RK4 tableau), with no work queue, termination
  * test or output: every thread follows an inclined bound orbit of Kerr
- * a = 0.9 M near r = 10 M with dtau = 0.5 for 4000 steps, one warp per SM
- * sub-partition, all SMs.  Blocks the calling thread; best of three launches.
+ * a = 0.9 M near r = 10 M with dtau = 0.5 for 4000 steps, two warps per SM
+ * sub-partition (the FP64 trace kernels' shape), all SMs.  Blocks the calling thread; best of three launches.
  * Writes RK4 steps/s: the ceiling of a trace kernel for that right-hand
  * side's instruction mix.  MALBEC_EINVAL for another form. */
 int malbec_measure_step_loop(uint32_t form, double* steps_per_s);

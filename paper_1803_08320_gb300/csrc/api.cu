@@ -111,13 +111,15 @@ int choose_shape_cfg(bool kerr, bool mixed, Source src, Sink sink, uint64_t n, c
   const bool banks = mixed && method == MALBEC_METHOD_RK4 && (cfg.exchange ? cfg.exchange == 1 : src != kSrcCamera);
   int per_sm = trace_max_blocks_per_sm(kerr, mixed, src, sink, banks, tpb, form, method);
   if (per_sm <= 0) per_sm = 1;
-  // Resident warps per SM.  FP64: one warp per SM sub-partition already
-  // saturates the FP64 unit (it costs the same per warp instruction whatever
-  // the number of active lanes), and more warps only slow the longest rays,
-  // which set the end of the launch.  FP32_MIXED: two per sub-partition,
-  // three for whole-image cameras (their kernels are held to 168 registers
-  // for it; latency-bound with two: 1024^2 render 9.4-9.7 ms against 11.0).
-  const int target_warps = mixed ? (src == kSrcCamera ? 12 : 8) : 4;
+  // Resident warps per SM.  FP64: two per SM sub-partition; the second warp
+  // issues while the first waits on an integer test of an FP64 result
+  // (1024^2 camera: 135.1 ms against 142.7 with one warp per sub-partition;
+  // Dormand-Prince at 1e-9: 311 against 333 ms).  The FP64 unit costs the
+  // same per warp instruction whatever the number of active lanes.
+  // FP32_MIXED: two per sub-partition, three for whole-image cameras (their
+  // kernels are held to 168 registers for it; latency-bound with two: 1024^2
+  // render 9.4-9.7 ms against 11.0).
+  const int target_warps = mixed ? (src == kSrcCamera ? 12 : 8) : 8;
   int want = target_warps / (tpb / 32);
   if (want < 1) want = 1;
   if (cfg.blocks_per_sm) want = (int)cfg.blocks_per_sm;

@@ -65,7 +65,7 @@ int measure(int iters, double* gflops) {
 // bound orbit of Kerr a = 0.9 M (r0 = 10 M + a lane offset, dtau = 0.5) for
 // nsteps steps; one warp per SM sub-partition, as in the trace kernels.
 template <int kForm>
-__global__ void __launch_bounds__(128, 1) step_loop_kernel(double* out, int nsteps, unsigned long long lane_zero) {
+__global__ void __launch_bounds__(128, 2) step_loop_kernel(double* out, int nsteps, unsigned long long lane_zero) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const double M = 1.0, a = 0.9, h = 0.5;
   const BH<double> bh = make_bh<double>(M, a, (unsigned long long)threadIdx.x & lane_zero);  // as the trace kernels
@@ -96,7 +96,7 @@ int step_loop(double* steps_per_s) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return set_cuda_error(e);
-  const int threads = 128, blocks = sms, nsteps = 4000;
+  const int threads = 128, blocks = 2 * sms, nsteps = 4000;  // two warps per SM sub-partition, as the trace kernels
   double* buf = nullptr;
   e = cudaMalloc(&buf, sizeof(double) * (size_t)threads * blocks);
   if (e != cudaSuccess) return set_cuda_error(e);
