@@ -554,12 +554,26 @@ def run_paper_case(mb, torch, stream, stride: int = 10) -> dict:
                 sec = e0.elapsed_time(e1) / 1e3
                 steps = int(r["steps"].to(torch.int64).sum().item())
                 row[mode] = {"seconds": sec, "steps_per_s": steps / sec, "d2h_bytes": nbytes}
+            # the same rays in FP32_MIXED, final state only: the latency of a
+            # small batch is that of one lane's sequence of steps
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream.synchronize()
+            e0.record(stream)
+            r = mb.trace(1.0, 0.5, ics, term, precision="fp32_mixed", stream=stream, out=out)
+            e1.record(stream)
+            stream.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            steps = int(r["steps"].to(torch.int64).sum().item())
+            row["final_fp32_mixed"] = {"seconds": sec, "steps_per_s": steps / sec,
+                                       "us_per_step_of_one_ray": 1e6 * sec / term.n_steps_cap}
+            row["final"]["us_per_step_of_one_ray"] = 1e6 * row["final"]["seconds"] / term.n_steps_cap
             p0, p1 = PAPER_GPU_S_NO_OUTPUT.get(n), PAPER_GPU_S_WITH_OUTPUT.get(n)
             row["paper_gpu_seconds"] = {"no_output": p0, "with_ascii_output": p1}
             row["speedup_vs_paper_gpu"] = {"no_output": p0 / row["final"]["seconds"] if p0 else None,
                                            "with_output": p1 / row["strided"]["seconds"] if p1 else None}
             rows.append(row)
-    return {"a": 0.5, "h": 0.1, "rk4_steps_per_ray": 10_000, "trajectory_stride": stride, "precision": "fp64",
+    return {"a": 0.5, "h": 0.1, "rk4_steps_per_ray": 10_000, "trajectory_stride": stride,
+            "precision": "fp64 (and fp32_mixed, final state only)",
             "rows": rows,
             "paper_hardware": "GTX 960M (Maxwell), CUDA 7.5; the paper's numbers are context, not a target"}
 

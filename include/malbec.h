@@ -233,9 +233,9 @@ int malbec_get_mixed_zone(malbec_mixed_zone* zone);
  *   threads_per_block  32..256, a multiple of 32 (automatic: 128, or 32 for
  *                      batches smaller than 4 warps per SM);
  *   blocks_per_sm      resident blocks per SM, capped by occupancy
- *                      (automatic: 4 warps per SM for FP64 -- one per SM
- *                      sub-partition saturates the FP64 unit --, 8 for
- *                      FP32_MIXED);
+ *                      (automatic: 8 warps per SM for FP64 -- two per SM
+ *                      sub-partition keep the FP64 unit busy --, 8 for
+ *                      FP32_MIXED, 12 for FP32_MIXED whole-image cameras);
  *   refill_min         a warp takes new rays once this many lanes are idle
  *                      (automatic: 2 for FP64; for FP32_MIXED whole-image
  *                      cameras 32, 8 or 1 for >= 16, >= 4 or fewer rays per
