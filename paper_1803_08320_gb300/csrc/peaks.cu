@@ -63,7 +63,7 @@ int measure(int iters, double* gflops) {
 
 // The RK4 step of one form, nothing else: each thread follows an inclined
 // bound orbit of Kerr a = 0.9 M (r0 = 10 M + a lane offset, dtau = 0.5) for
-// nsteps steps; one warp per SM sub-partition, as in the trace kernels.
+// nsteps steps; two warps per SM sub-partition, as in the FP64 trace kernels.
 template <int kForm>
 __global__ void __launch_bounds__(128, 2) step_loop_kernel(double* out, int nsteps, unsigned long long lane_zero) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;

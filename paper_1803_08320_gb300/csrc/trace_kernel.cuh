@@ -15,7 +15,8 @@
 // FP32, and the increments h/6 (k1 + 2k2 + 2k3 + k4) -- with h/6 as a float
 // pair -- are added with TwoSum.  lambda is accumulated in FP64 (the h of
 // FP32 steps through an error-free float-pair partial sum flushed every 32
-// steps) and the invariants are evaluated in FP64; a step whose start lies
+// steps) and the invariants are evaluated in FP64 (the end norm of an
+// FP32_MIXED camera pixel in FP32, for its validity flag); a step whose start lies
 // inside the FP64 zone (near the horizon, near the photon orbits for null
 // rays, or near the polar axis where the BL Christoffel symbols diverge) runs
 // entirely in FP64, and the warps of a block exchange rays so that zone steps
@@ -574,7 +575,7 @@ __device__ __forceinline__ void to_velocity(double M, double a, const double z[8
 // minimum-blocks argument it gives every instantiation fewer registers (the
 // FP32_MIXED camera kernel 146 instead of 190, and 1.9x slower: 20.5 against
 // 10.8 ms per 1024^2 render; some request-loop instantiations were capped at
-// 128 and spilled).  Two exceptions are held to 168 registers, so that three
+// 128 and spilled).  Two RK4 exceptions are held to 168 registers, so that three
 // 128-thread blocks fit an SM (3 x 128 x 168 <= 65536): the FP32_MIXED
 // job-table kernel with the block ray exchange, whose autotuned shape is
 // three blocks per SM (with 176 registers it ran on two, and the 4096 uneven
