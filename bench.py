@@ -287,6 +287,9 @@ def run_profile_case(args) -> None:
     if args.profile_case == "camera_dopri5":
         term = dataclasses.replace(mb.term_from(cw.term, method=mb.METHOD_DOPRI5, rtol=1e-9, atol=1e-9),
                                    dl=0.0, dl_r_scale=0.5)
+    if args.profile_case == "camera_mixed_dopri5_1024":
+        term = dataclasses.replace(mb.term_from(cw.term, method=mb.METHOD_DOPRI5, rtol=1e-6, atol=1e-6),
+                                   dl=0.0, dl_r_scale=0.5)
     for _ in range(max(1, args.steps)):
         res = mb.trace_camera(cw.M, cw.a, cam, term, prec)
     torch.cuda.synchronize()
@@ -1071,7 +1074,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", choices=["camera_fp64", "camera_mixed", "camera_canonical", "camera_adm",
                                                "camera_dopri5", "traj_mixed", "camera_fp64_1024",
-                                               "camera_mixed_1024"],
+                                               "camera_mixed_1024", "camera_mixed_dopri5_1024"],
                     default=None,
                     help="case for ncu: a 512x512 render of the same camera (1024x1024 for *_1024), --steps times")
     ap.add_argument("--workload", choices=["camera", "bundles", "serving", "bound", "paper", "integrators",

@@ -275,6 +275,27 @@ __device__ __forceinline__ float rk4_step_mixed_ham(const BH<float>& bh, float h
 // and k7 = f at the fifth-order point.  Canonical forms: p_t = hi[4] and
 // p_ph = hi[7] are fixed (their k components are 0).  Returns the smallest
 // stage radius among the stage points 2..7.
+
+// The FP32_MIXED Dormand-Prince kernels call one out-of-line copy of each
+// right-hand side (and of the FP64 zone attempt) instead of inlining seven:
+// the inlined kernel stalled on instruction fetch (ncu: no_instruction 3.6
+// per issue, 25% of issue slots used); 1024^2 camera at rtol 1e-6: 17.1 ->
+// 15.2 ms, the same arithmetic.
+template <bool kKerr>
+__device__ __noinline__ void accel_f32_call(const BH<float>& bh, float r, float th, float ut, float ur, float uth,
+                                            float uph, float* acc) {
+  accel<kKerr, float>(bh, r, th, ut, ur, uth, uph, acc);
+}
+template <int kForm>
+__device__ __noinline__ void ham_f32_call(const BH<float>& bh, float r, float th, float pt, float pr, float pth,
+                                          float pph, float* f) {
+  ham_rhs<kForm, float>(bh, r, th, pt, pr, pth, pph, f);
+}
+template <bool kKerr, int kForm>
+__device__ __noinline__ double dopri5_attempt_call(const BH<double>& bh, double h, const double* y, const double* k1,
+                                                   double* y5, double* e, double* k7) {
+  return dopri5_attempt<kKerr, kForm>(bh, h, y, k1, y5, e, k7);
+}
 template <bool kKerr, int kForm>
 __device__ __forceinline__ float dopri5_attempt_mixed(const BH<float>& bh, float hf, const float hi[8],
                                                       const float lo[8], const float k1[8], float dx[8],
@@ -289,10 +310,10 @@ __device__ __forceinline__ float dopri5_attempt_mixed(const BH<float>& bh, float
     if constexpr (kForm == MALBEC_FORM_GEODESIC) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) k[j] = z[4 + j];
-      accel<kKerr, float>(bh, z[1], z[2], z[4], z[5], z[6], z[7], k + 4);
+      accel_f32_call<kKerr>(bh, z[1], z[2], z[4], z[5], z[6], z[7], k + 4);
     } else {
       float f[6];
-      ham_rhs<kForm, float>(bh, z[1], z[2], hi[4], z[5], z[6], hi[7], f);
+      ham_f32_call<kForm>(bh, z[1], z[2], hi[4], z[5], z[6], hi[7], f);
 #pragma unroll
       for (int j = 0; j < 4; ++j) k[j] = f[j];
       k[4] = 0.f;
@@ -1305,7 +1326,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
             k1l[c] = (double)k1f[c];
           }
           const double h = (double)hf;
-          const double rmin = dopri5_attempt<kKerr, kForm>(bh64, h, yd, k1l, y5, e, k7);
+          const double rmin = dopri5_attempt_call<kKerr, kForm>(bh64, h, yd, k1l, y5, e, k7);
           captured = (y5[1] <= r_cap) | (rmin <= r_cap);
           finite = finite8(y5);
           escaped = false;
