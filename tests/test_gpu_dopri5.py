@@ -330,3 +330,53 @@ def test_mixed_bound_orbits_keep_the_invariants_as_fp64(mb, orc, W, form):
             assert np.quantile(d32[c], qq) <= 1.5 * np.quantile(d64[c], qq) + 1e-12, (c, qq)
     if form != 0:
         assert d32[:2].max() <= 1e-13
+
+
+
+
+def test_mixed_strided_samples(mb, orc):
+    """FP32_MIXED adaptive samples every 25 attempts of eccentric orbits
+    (circular ones with u^r = 0.01 and u^theta = 0.004, so Q > 0; one
+    starting inside the capture radius)
+    at rtol = atol = 1e-6: FP32 samples (the state's hi words), sample 0 the
+    initial state rounded to FP32, sample k finite exactly when k x 25 <= the
+    attempts taken (NaN after the end), and a capped orbit's last sample its
+    final state to one FP32 unit.  The step sequences part from the oracle's
+    (FP64, same tolerance) after a few hundred attempts, so the samples are
+    checked on the flow's invariants: the largest change of E, L_z, Q and
+    g(u,u) over a ray's samples stays within 1.5x the oracle's own over its
+    samples (median and p90 over the rays; measured within 10%) plus the
+    FP32 rounding of a sample (1e-6)."""
+    rng = np.random.default_rng(5)
+    ys = np.stack([orc.circular_state(1.0, 0.5, r, 1) for r in rng.uniform(7.0, 12.0, 24)], axis=1)
+    ys[5], ys[6] = 0.01, 0.004
+    ys[1, 0] = 1.87  # inside the capture radius (1.01 r+ = 1.885), outside r+: ends at its first attempt
+    t = dp_term(mb, tol=1e-6, r_esc=40.0, n_steps_cap=600, dl=0.5)
+    got = gpu_trace(mb, 1.0, 0.5, ys, t, mode=mb.OUT_STRIDED, stride=25, precision="fp32_mixed")
+    ref = orc.trace_many(1.0, 0.5, ys, oracle_term(orc, t), stride=25, want_traj=True)
+    traj = got["traj"]
+    n, ns = ys.shape[1], 600 // 25 + 1
+    assert traj.shape == (n, ns, 8) and traj.dtype == np.float32
+    assert np.array_equal(traj[:, 0, :], ys.T.astype(np.float32))
+    steps = got["steps"].astype(np.int64)
+    want_fin = np.arange(ns)[None, :] * 25 <= steps[:, None]
+    assert np.array_equal(np.isfinite(traj).all(axis=2), want_fin)
+    assert np.array_equal(np.isnan(traj).all(axis=2), ~want_fin)
+    capped = (got["fate"] & mb.FATE_MASK) == mb.FATE_CAPPED
+    assert capped.sum() >= 20 and got["fate"][0] == mb.FATE_CAPTURED
+    assert np.array_equal(got["fate"], ref["fate"])
+    y_end = got["y"][:, capped].T
+    assert (np.abs(traj[capped, -1, :] - y_end) <= np.spacing(np.abs(y_end).astype(np.float32))).all()
+
+    def inv_drift(tr):
+        out = np.zeros((4, int(capped.sum())))
+        for j, i in enumerate(np.flatnonzero(capped)):
+            inv = np.stack([orc.invariants(1.0, 0.5, tr[i, k].astype(np.float64)) for k in range(ns)], axis=1)
+            out[:, j] = (np.abs(inv - inv[:, :1]) / np.maximum(np.abs(inv[:, :1]), 1.0)).max(axis=1)
+        return out
+
+    d32, d64 = inv_drift(traj), inv_drift(ref["traj"])
+    for c in range(4):
+        for qq in (0.5, 0.9):
+            print("invariant", c, "q", qq, "mixed", np.quantile(d32[c], qq), "oracle", np.quantile(d64[c], qq))
+            assert np.quantile(d32[c], qq) <= 1.5 * np.quantile(d64[c], qq) + 1e-6, (c, qq)
