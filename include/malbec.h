@@ -152,16 +152,18 @@ typedef struct {
  *                         stage points, as for RK4), escape on accepted
  *                         steps.  Any form (in the canonical forms p_t and
  *                         p_ph stay exactly constant, as with RK4).  Requires
- *                         atol > 0 and rtol >= 0.  MALBEC_FP64: every entry
- *                         point (bundles and servers as for the forms).
- *                         MALBEC_FP32_MIXED (malbec_trace and
- *                         malbec_trace_camera): attempts in FP32 on the
- *                         compensated state, in FP64 in the FP64 zones, the
- *                         error norm and the step rule in the precision of
- *                         the attempt; requires rtol >=
+ *                         atol > 0 and rtol >= 0.  Every entry point
+ *                         (bundles and servers as for the forms), in both
+ *                         precisions, except malbec_trace_noalloc, which
+ *                         takes it in FP64 only.  MALBEC_FP32_MIXED: attempts in FP32
+ *                         on the compensated state, in FP64 in the FP64
+ *                         zones, the error norm and the step rule in the
+ *                         precision of the attempt; requires rtol >=
  *                         MALBEC_DOPRI5_MIXED_RTOL_MIN (an FP32 error
  *                         estimate carries rounding noise of ~1e-7 of the
- *                         state); other entry points: MALBEC_EINVAL.
+ *                         state; MALBEC_EINVAL below it).  The block ray
+ *                         exchange is off for this method (a ray keeps its
+ *                         lane and its step-size state).
  * rtol, atol: the tolerances of MALBEC_METHOD_DOPRI5 (ignored by RK4). */
 #define MALBEC_FORM_GEODESIC 0
 #define MALBEC_FORM_HAMILTONIAN 1
@@ -252,7 +254,7 @@ int malbec_get_mixed_zone(malbec_mixed_zone* zone);
  *                      back (zone steps run with fuller warps), 2 = every
  *                      ray stays in its warp (automatic: 2 for whole-image
  *                      cameras, whose rays spend few steps in the zone, 1
- *                      otherwise);
+ *                      otherwise; always 2 for MALBEC_METHOD_DOPRI5);
  *   zone_wait_limit_us with the exchange, the longest a block's zone warp,
  *                      once it has no ray left, waits for the other warps of
  *                      its block before it closes its bank and leaves (the
@@ -481,7 +483,7 @@ typedef struct {
   malbec_precision precision;
   double idle_timeout_s;  /* kernel exit after this long without work, > 0 */
   uint32_t form;          /* MALBEC_FORM_* of every job of this server (0: geodesic) */
-  uint32_t method;        /* MALBEC_METHOD_* of every job (DOPRI5: FP64 servers only) */
+  uint32_t method;        /* MALBEC_METHOD_* of every job (0: RK4) */
 } malbec_server_config;
 
 typedef struct {

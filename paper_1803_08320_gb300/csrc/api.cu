@@ -49,7 +49,9 @@ int check_term(const malbec_term& t, const malbec_metric& m) {
 }
 
 // The adaptive method runs in FP64 on every entry point, and in FP32_MIXED
-// on the direct traces (mixed_ok) when rtol >= MALBEC_DOPRI5_MIXED_RTOL_MIN.
+// (its FP32 error estimate carries rounding noise of ~1e-7 of the state)
+// when rtol >= MALBEC_DOPRI5_MIXED_RTOL_MIN on the entry points that take it
+// (mixed_ok: the direct traces, job tables and servers).
 int check_method_precision(const malbec_term& t, malbec_precision prec, bool mixed_ok) {
   if (t.method != MALBEC_METHOD_DOPRI5 || prec == MALBEC_FP64) return MALBEC_OK;
   if (mixed_ok && prec == MALBEC_FP32_MIXED && t.rtol >= MALBEC_DOPRI5_MIXED_RTOL_MIN) return MALBEC_OK;

@@ -42,7 +42,7 @@ int validate(const malbec_bundle& b, malbec_precision prec) {
   if (rc) return rc;
   rc = check_term(b.term, m);  // form and method included
   if (rc) return rc;
-  rc = check_method_precision(b.term, prec);
+  rc = check_method_precision(b.term, prec, true);
   if (rc) return rc;
   if (b.kind == MALBEC_BUNDLE_CAMERA) {
     rc = check_camera_desc(m, &b.camera, &b.term);

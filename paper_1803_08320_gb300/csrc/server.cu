@@ -200,10 +200,9 @@ int malbec_server_create(const malbec_server_config* cfg, malbec_server** server
       !(cfg->idle_timeout_s > 0.0) || !isfinite(cfg->idle_timeout_s) ||
       (cfg->precision != MALBEC_FP64 && cfg->precision != MALBEC_FP32_MIXED))
     return MALBEC_EINVAL;
-  // the class of jobs this server runs: any form; Dormand-Prince in FP64 only
-  if (cfg->form > MALBEC_FORM_ADM || cfg->method > MALBEC_METHOD_DOPRI5 ||
-      (cfg->method == MALBEC_METHOD_DOPRI5 && cfg->precision != MALBEC_FP64))
-    return MALBEC_EINVAL;
+  // the class of jobs this server runs: any form, either method (each job's
+  // tolerances are checked when it is submitted)
+  if (cfg->form > MALBEC_FORM_ADM || cfg->method > MALBEC_METHOD_DOPRI5) return MALBEC_EINVAL;
   malbec_server* S = new malbec_server();
   S->cfg = *cfg;
   memset(&S->stats, 0, sizeof(S->stats));

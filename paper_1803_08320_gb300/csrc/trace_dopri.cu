@@ -7,8 +7,8 @@ namespace malbec {
 
 const void* pick_dopri(bool mixed, Source src, Sink sink, int form) {
   // Dormand-Prince 5(4): every form (the Kerr right-hand sides, a = 0
-  // included); FP64 from every source, FP32_MIXED from state arrays and
-  // cameras (no block exchange)
+  // included), every source, FP64 and FP32_MIXED (no block exchange: a ray
+  // never changes warps, so its step-size state stays in its lane)
   if (mixed) {
 #define MALBEC_PICK_DPM(F)                                                                 \
   if (form == F) {                                                                         \
@@ -18,6 +18,10 @@ const void* pick_dopri(bool mixed, Source src, Sink sink, int form) {
       return kernel_ptr<true, true, kSrcStates, kSinkStrided, false, F, MALBEC_METHOD_DOPRI5>();  \
     if (src == kSrcCamera && sink == kSinkCamera)                                          \
       return kernel_ptr<true, true, kSrcCamera, kSinkCamera, false, F, MALBEC_METHOD_DOPRI5>();   \
+    if (src == kSrcJobs && sink == kSinkJobs)                                              \
+      return kernel_ptr<true, true, kSrcJobs, kSinkJobs, false, F, MALBEC_METHOD_DOPRI5>();       \
+    if (src == kSrcServe && sink == kSinkJobs)                                             \
+      return kernel_ptr<true, true, kSrcServe, kSinkJobs, false, F, MALBEC_METHOD_DOPRI5>();      \
   }
     MALBEC_PICK_DPM(MALBEC_FORM_GEODESIC)
     MALBEC_PICK_DPM(MALBEC_FORM_HAMILTONIAN)

@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
   // FP32_MIXED Dormand-Prince: the next step size and k1 in FP32, the
   // tolerances in FP32
   float hn_f = 0.f, k1f[8];
-  const float rtol_f = (float)p.rtol, atol_f = (float)p.atol;
+  float rtol_f = (float)p.rtol, atol_f = (float)p.atol;  // per job from job tables
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     k1d[c] = 0.0;
@@ -1164,6 +1164,10 @@ __global__ void __launch_bounds__(kMaxTPB, 1) __maxnreg__((trace_reg_cap<kMixed,
           cap = J.cap;
           rtol = J.rtol;
           atol = J.atol;
+          if constexpr (kMixed && kDopri) {
+            rtol_f = (float)rtol;
+            atol_f = (float)atol;
+          }
           step_consts(dl, dl_scale, r_esc, h_fix, h6_fix_h, h6_fix_l, scale_f, r_esc_f);
           if (J.kind == MALBEC_BUNDLE_CAMERA) {
             camera_state(J.cam, a, id, y);

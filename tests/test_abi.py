@@ -121,11 +121,10 @@ def test_trace_validation_rejects_before_any_cuda_call(mb):
         assert lib.malbec_trace(m, fake, 10, dp, mb.OUT_FINAL, 0, mb.FP32_MIXED, fake, None) == mb.EINVAL
         cam = mb.make_camera(1000.0, 1.3, 25.0, 8, 8)
         assert lib.malbec_trace_camera(m, ctypes.byref(cam), dp, mb.FP32_MIXED, fake, None) == mb.EINVAL
-    # the job tables take it in FP64 only
-    dp6 = _term(eps_hor=0.01, r_esc=1000.0, n_steps_cap=10, dl=0.01, method=1, rtol=1e-6, atol=1e-9)
-    b = mb.make_bundle(mb.BUNDLE_BOUND, 10, 1.0, 0.5, dp6, seed=3)
-    b.out = fake
-    assert lib.malbec_trace_bundles(mb._bundle_array([b]), 1, mb.FP32_MIXED, None) == mb.EINVAL
+        # and in the job tables (checked before anything is allocated or launched)
+        b = mb.make_bundle(mb.BUNDLE_BOUND, 10, 1.0, 0.5, dp, seed=3)
+        b.out = fake
+        assert lib.malbec_trace_bundles(mb._bundle_array([b]), 1, mb.FP32_MIXED, None) == mb.EINVAL
 
 
 

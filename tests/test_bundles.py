@@ -189,10 +189,10 @@ def test_bound_bundle_matches_oracle(mb, orc):
 CLASSES = [(0, 0), (1, 0), (2, 0), (0, 1), (1, 1), (2, 1)]  # (form, method): RK4 and Dormand-Prince, each form
 
 
-def _with_class(mb, t, form, method):
+def _with_class(mb, t, form, method, tol=1e-9):
     """The bundle's term in class (form, method); Dormand-Prince at tolerance
-    1e-9 (its first step is the RK4 step: dl, or dl_r_scale r0)."""
-    return mb.term_from(t, form=form, method=method, rtol=1e-9 if method else 0.0, atol=1e-9 if method else 0.0)
+    `tol` (its first step is the RK4 step: dl, or dl_r_scale r0)."""
+    return mb.term_from(t, form=form, method=method, rtol=tol if method else 0.0, atol=tol if method else 0.0)
 
 
 @pytest.mark.gpu
@@ -200,17 +200,22 @@ def _with_class(mb, t, form, method):
 def test_bundles_of_every_form_and_method_equal_single_launches(mb, precision):
     """A job table mixing the equations (geodesic form, canonical forms
     through eq. kerr and eq. ADM) and the integrators (RK4, Dormand-Prince
-    5(4), FP64 only): one persistent launch per class, and every bundle's
-    results equal those of tracing it alone with the same term -- bitwise in
-    FP64; in FP32_MIXED (RK4 only) fates and steps on >= 99.5% of rays and
-    states within 1e-6 on >= 99% of those."""
+    5(4) at 1e-9 in FP64, at 1e-6 in FP32_MIXED): one persistent launch per
+    class, and every bundle's results equal those of tracing it alone with
+    the same term -- bitwise in FP64 and for FP32_MIXED Dormand-Prince (no
+    block exchange: a ray takes the same attempts in its lane on either
+    entry point; a camera pixel's validity flag comes from the FP64 end norm
+    in a job table and from the FP32 one in a whole-image trace, so only the
+    fate without the flag is compared there); FP32_MIXED RK4 fates and steps
+    on >= 99.5% of rays and states within 1e-6 on >= 99% of those."""
     import torch
 
-    classes = CLASSES if precision == "fp64" else [c for c in CLASSES if c[1] == 0]
+    classes = CLASSES
+    tol = 1e-9 if precision == "fp64" else 1e-6
     bundles, singles = _mixed_bundles(mb, torch, seed=5, count=18)
     for i, b in enumerate(bundles):
         form, method = classes[i % len(classes)]
-        t = _with_class(mb, singles[i][2], form, method)
+        t = _with_class(mb, singles[i][2], form, method, tol)
         b.term = t.c()
         singles[i] = (singles[i][0], singles[i][1], t, singles[i][3], singles[i][4])
     views = mb.attach_outputs(bundles, precision)
@@ -222,9 +227,11 @@ def test_bundles_of_every_form_and_method_equal_single_launches(mb, precision):
         keys = ("fate", "steps", "theta", "phi") if spec[0] == "camera" else ("y", "inv0", "inv1", "steps", "fate",
                                                                              "lambda")
         cls = (spec[2].form, spec[2].method)
-        if precision == "fp64":
+        if precision == "fp64" or spec[2].method == mb.METHOD_DOPRI5:
             for k in keys:
                 x, y = v[k].cpu().numpy(), ref[k].cpu().numpy()
+                if k == "fate" and precision != "fp64" and spec[0] == "camera":
+                    x, y = x & mb.FATE_MASK, y & mb.FATE_MASK
                 assert np.array_equal(np.isnan(x), np.isnan(y)), (spec[0], cls, k)
                 assert np.array_equal(np.nan_to_num(x), np.nan_to_num(y)), (spec[0], cls, k)
         else:

@@ -28,7 +28,7 @@ def test_server_config_validation(mb):
                 mb.ServerConfig(10**9, 16, 16, 7, 0.01),
                 mb.ServerConfig(10**9, 16, 16, mb.FP64, 0.0),
                 mb.ServerConfig(10**9, 16, 16, mb.FP64, 0.01, 3, 0),          # no such form
-                mb.ServerConfig(10**9, 16, 16, mb.FP32_MIXED, 0.01, 0, 1)):   # Dormand-Prince: FP64 only
+                mb.ServerConfig(10**9, 16, 16, mb.FP32_MIXED, 0.01, 0, 2)):   # no such method
         assert lib.malbec_server_create(ctypes.byref(cfg), ctypes.byref(h)) == mb.EINVAL
     assert lib.malbec_server_destroy(None) == mb.EINVAL
     assert lib.malbec_submit(None, None, None) == mb.EINVAL
@@ -135,28 +135,32 @@ def test_admission_by_budget_and_pending_limit(mb):
     srv.close()
 
 
-def _in_class(mb, jobs, form, method):
+def _in_class(mb, jobs, form, method, tol=1e-9):
     """The same jobs in another class (form, method); Dormand-Prince at
-    tolerance 1e-9."""
+    tolerance `tol`."""
     for b in jobs:
         t = mb.Termination(b.term.eps_hor, b.term.r_esc, b.term.n_steps_cap, b.term.dl, b.term.dl_r_scale, form,
-                           method, 1e-9 if method else 0.0, 1e-9 if method else 0.0)
+                           method, tol if method else 0.0, tol if method else 0.0)
         b.term = t.c()
     return jobs
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision,form,method", [("fp32_mixed", 1, 0), ("fp32_mixed", 2, 0), ("fp64", 2, 0),
-                                                   ("fp64", 0, 1), ("fp64", 1, 1)])
+                                                   ("fp64", 0, 1), ("fp64", 1, 1), ("fp32_mixed", 0, 1),
+                                                   ("fp32_mixed", 2, 1)])
 def test_server_of_another_class_alone_and_in_the_mix(mb, precision, form, method):
     """A server runs one class of jobs (form, method): the canonical forms
-    (eq. Ham through eq. kerr and eq. ADM) and Dormand-Prince (FP64) are
-    served with the same guarantees -- each result bitwise the same alone and
-    in the mix, FP64 results equal to tracing the job alone with the bundle
-    launch -- and a job of another class is refused."""
+    (eq. Ham through eq. kerr and eq. ADM) and Dormand-Prince (FP64 at 1e-9,
+    FP32_MIXED at 1e-6) are served with the same guarantees -- each result
+    bitwise the same alone and in the mix, FP64 and FP32_MIXED
+    Dormand-Prince results equal to tracing the job alone with the bundle
+    launch (no block exchange in either) -- and a job of another class, or
+    (FP32_MIXED Dormand-Prince) below the tolerance floor, is refused."""
     import torch
 
-    jobs = _in_class(mb, _jobs(mb, seed=4, count=6), form, method)
+    tol = 1e-6 if (precision == "fp32_mixed" and method == 1) else 1e-9
+    jobs = _in_class(mb, _jobs(mb, seed=4, count=6), form, method, tol)
     mixed, stats = _serve(mb, jobs, precision, form=form, method=method)
     assert stats["completed"] == len(jobs)
     for j, b in enumerate(jobs):
@@ -164,9 +168,9 @@ def test_server_of_another_class_alone_and_in_the_mix(mb, precision, form, metho
         keys = ("fate", "steps", "theta", "phi") if b.kind == mb.BUNDLE_CAMERA else ("fate", "steps", "y", "inv1")
         for k in keys:
             assert _same(mixed[j][k], alone[0][k]), (j, k)
-        if precision == "fp64":
-            (ref,) = mb.attach_outputs([b], "fp64")
-            mb.trace_bundles([b], "fp64")
+        if precision == "fp64" or method == 1:
+            (ref,) = mb.attach_outputs([b], precision)
+            mb.trace_bundles([b], precision)
             torch.cuda.synchronize()
             for k in keys:
                 assert _same(mixed[j][k], ref[k]), (j, k)
@@ -175,6 +179,10 @@ def test_server_of_another_class_alone_and_in_the_mix(mb, precision, form, metho
     if (form, method) != (0, 0):
         with pytest.raises(mb.MalbecError):
             srv.submit(other)
+    if precision == "fp32_mixed" and method == 1:
+        (below_floor,) = _in_class(mb, _jobs(mb, seed=9, count=1), form, method, 0.5e-6)
+        with pytest.raises(mb.MalbecError):
+            srv.submit(below_floor)
     srv.close()
 
 
