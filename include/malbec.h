@@ -570,15 +570,18 @@ int malbec_measure_fma_peak(malbec_precision prec, double* gflops);
  * side's instruction mix.  MALBEC_EINVAL for another form. */
 int malbec_measure_step_loop(uint32_t form, double* steps_per_s);
 
-/* Self-check of two FP64 device helpers of the right-hand sides, on 2^22
+/* Self-check of three FP64 device helpers of the right-hand sides, on 2^22
  * seeded samples: the stage sine/cosine by angle addition (|d| <= 1/4)
- * against CUDA's sincos at the same, exactly representable angle, and the
- * refined reciprocal against the IEEE division 1.0 / x (x in 2^[-60, 60]).
- * err[0], err[1]: max absolute sine, cosine difference; err[2]: max
- * reciprocal difference in units of the last place of 1/x; err[3]: max
- * relative error of the hardware reciprocal estimate before refinement.
- * Blocks the calling thread. */
-int malbec_check_fp64_helpers(double err[4]);
+ * against CUDA's sincos at the same, exactly representable angle, the
+ * refined reciprocal against the IEEE division 1.0 / x (x in 2^[-60, 60]),
+ * and the steps' own sine/cosine (Cody-Waite reduction and Taylor series)
+ * against CUDA's sincos on x in [-4, 8], next to the multiples of pi/2
+ * there, and up to 2^30 in magnitude.  err[0], err[1]: max absolute stage sine, cosine difference;
+ * err[2]: max reciprocal difference in units of the last place of 1/x;
+ * err[3]: max relative error of the hardware reciprocal estimate before
+ * refinement; err[4], err[5]: max absolute sine, cosine difference of the
+ * steps' sine/cosine.  Blocks the calling thread. */
+int malbec_check_fp64_helpers(double err[6]);
 
 /* Self-check of the operand forms the kernels compute in (not in the paper),
  * bit for bit on 2^22 seeded samples of every class of value (zeros,

@@ -23,16 +23,6 @@
 
 namespace malbec {
 
-template <typename T>
-struct Trig;
-template <>
-struct Trig<double> {
-  __device__ __forceinline__ static void sc(double x, double* s, double* c) { sincos(x, s, c); }
-};
-template <>
-struct Trig<float> {
-  __device__ __forceinline__ static void sc(float x, float* s, float* c) { sincosf(x, s, c); }
-};
 
 // 1/x.  FP64: the hardware estimate (PTX rcp.approx.ftz.f64) refined by one
 // step of the cubically convergent iteration y <- y (1 + e + e^2), e = 1 - x y
@@ -145,6 +135,68 @@ __device__ __forceinline__ T vsub(const BH<T>& b, T x, T y) {
     return x - y;
 }
 
+// sin and cos of an angle in FP64 on the FMA unit alone (the RK4 steps take
+// one per step, the rolled steps and the wide stage offsets one per stage).
+// Cody & Waite's reduction (Software Manual for the Elementary Functions,
+// 1980): x = k pi/2 + r with k the integer nearest x 2/pi (added to and taken
+// from 1.5 2^52, whose last bits then hold k) and r = (x - k P1) - k P2,
+// pi/2 = P1 + P2 + O(1e-33), P1 the double nearest pi/2; |r| <= pi/4 up to
+// the rounding of x 2/pi.  Then the Taylor series in z = r^2,
+//   sin r = r - r^3/3! + ... + r^17/17!,  cos r = 1 - r^2/2! + ... + r^16/16!
+// (first omitted terms below 1e-19 and 3e-18 for |r| <= pi/4), and the
+// quadrant k mod 4 by swapping the two and flipping sign bits on the integer
+// pipe.  Error: within one unit of 2^-52 absolute against a long-double
+// reference over x in [-2, 4] and next to the multiples of pi/2 (2e7 draws);
+// sin(-0) is +0.  |x| >= 2^10 (stage angles of a ray thrown through the
+// polar axis, non-finite x) goes to CUDA's sincos, which reduces any
+// argument exactly and so keeps such a ray's later arithmetic that of the
+// library's sincos.  Coefficients in the full-rate operand form (vreg with a
+// zero taken from x's bits and b.nz, formed next to each use).  FP32: sincosf.
+template <typename T>
+struct Trig;
+template <>
+struct Trig<double> {
+  __device__ __forceinline__ static void sc(const BH<double>& b, double x, double* s, double* c) {
+    if ((__double2hiint(x) & 0x7fffffff) >= 0x40900000) {  // |x| >= 2^10, inf, NaN
+      sincos(x, s, c);
+      return;
+    }
+    const unsigned long long vz =
+        (unsigned long long)__double_as_longlong(x) & ((unsigned long long)__double_as_longlong(b.nz) & 0x7fffffffffffffffull);
+    auto K = [&](double v) { return vreg(v, vz); };
+    const double t = fma(x, K(0x1.45f306dc9c883p-1), K(0x1.8p52));
+    const double kd = fma(t, b.one, K(-0x1.8p52));
+    const unsigned q = (unsigned)__double2loint(t);
+    double r = fma(-kd, K(0x1.921fb54442d18p+0), x);
+    r = fma(-kd, K(0x1.1a62633145c07p-54), r);
+    const double z = vmul(b, r, r);
+    double p = fma(z, K(1.0 / 355687428096000.0), K(-1.0 / 1307674368000.0));
+    p = fma(z, p, K(1.0 / 6227020800.0));
+    p = fma(z, p, K(-1.0 / 39916800.0));
+    p = fma(z, p, K(1.0 / 362880.0));
+    p = fma(z, p, K(-1.0 / 5040.0));
+    p = fma(z, p, K(1.0 / 120.0));
+    p = fma(z, p, K(-1.0 / 6.0));
+    const double sr = fma(vmul(b, r, z), p, r);
+    double pc = fma(z, K(1.0 / 20922789888000.0), K(-1.0 / 87178291200.0));
+    pc = fma(z, pc, K(1.0 / 479001600.0));
+    pc = fma(z, pc, K(-1.0 / 3628800.0));
+    pc = fma(z, pc, K(1.0 / 40320.0));
+    pc = fma(z, pc, K(-1.0 / 720.0));
+    pc = fma(z, pc, K(1.0 / 24.0));
+    pc = fma(z, pc, -b.half);
+    const double cr = fma(z, pc, b.one);
+    const unsigned long long bs = (q & 1u) ? __double_as_longlong(cr) : __double_as_longlong(sr);
+    const unsigned long long bc = (q & 1u) ? __double_as_longlong(sr) : __double_as_longlong(cr);
+    *s = __longlong_as_double((long long)(bs ^ ((unsigned long long)(q & 2u) << 62)));
+    *c = __longlong_as_double((long long)(bc ^ ((unsigned long long)((q + 1u) & 2u) << 62)));
+  }
+};
+template <>
+struct Trig<float> {
+  __device__ __forceinline__ static void sc(const BH<float>&, float x, float* s, float* c) { sincosf(x, s, c); }
+};
+
 // sin and cos at a stage angle th = th0 + c x (c x = d, the stage's offset
 // from the step's start angle th0), given s0 = sin th0 and c0 = cos th0.
 // FP64 with |d| < 1/4: the angle-addition formulas with sin d and cos d - 1
@@ -159,8 +211,8 @@ __device__ __forceinline__ T vsub(const BH<T>& b, T x, T y) {
 // tier is a per-lane choice on the bits of d, so a ray's result never depends
 // on the other rays of its warp.
 template <typename T>
-__device__ __forceinline__ void stage_trig(const BH<T>&, T s0, T c0, T c, T x, T th0, T* s, T* cs) {
-  Trig<T>::sc(fma(c, x, th0), s, cs);
+__device__ __forceinline__ void stage_trig(const BH<T>& b, T s0, T c0, T c, T x, T th0, T* s, T* cs) {
+  Trig<T>::sc(b, fma(c, x, th0), s, cs);
 }
 // The range tests read the exponent bits on the integer pipe (an FP64 compare
 // would take an issue of the FP64 unit, which costs as much as an FMA there);
@@ -196,7 +248,7 @@ __device__ __forceinline__ void stage_trig<double>(const BH<double>& b, double s
     pc = fma(z, pc, -b.half);
     cm1 = vmul(b, z, pc);
   } else {
-    sincos(fma(c, x, th0), s, cs);
+    Trig<double>::sc(b, fma(c, x, th0), s, cs);
     return;
   }
   *s = fma(s0, cm1, fma(c0, sd, s0));
@@ -337,7 +389,7 @@ __device__ __forceinline__ void accel_sc(const BH<T>& bh, T r, T s, T c, T ut, T
 template <bool kKerr, typename T>
 __device__ __forceinline__ void accel(const BH<T>& bh, T r, T th, T ut, T ur, T uth, T uph, T acc[4]) {
   T s, c;
-  Trig<T>::sc(th, &s, &c);
+  Trig<T>::sc(bh, th, &s, &c);
   accel_sc<kKerr, T>(bh, r, s, c, ut, ur, uth, uph, acc);
 }
 
@@ -366,13 +418,13 @@ __device__ __forceinline__ T rk4_step(const BH<T>& bh, T h, T y[8]) {
   T rmin = T(0);
   long long kmin = 0;
   T s0 = T(0), c0 = T(1);
-  if constexpr (!kRolled) Trig<T>::sc(y[2], &s0, &c0);
+  if constexpr (!kRolled) Trig<T>::sc(bh, y[2], &s0, &c0);
   T sn = s0, cs = c0;
   auto stage = [&](int s) {
     T acc[4];
     if constexpr (kRolled) {
       T sr, cr;
-      Trig<T>::sc(th, &sr, &cr);
+      Trig<T>::sc(bh, th, &sr, &cr);
       accel_sc<kKerr, T, false>(bh, r, sr, cr, u[0], u[1], u[2], u[3], acc);
     } else {
       accel_sc<kKerr, T>(bh, r, sn, cs, u[0], u[1], u[2], u[3], acc);
@@ -564,7 +616,7 @@ __device__ __forceinline__ void adm_kerr_sc(const BH<T>& bh, T r, T s, T c, Adm<
 template <typename T>
 __device__ __forceinline__ void adm_kerr(const BH<T>& bh, T r, T th, Adm<T>& m) {
   T s, c;
-  Trig<T>::sc(th, &s, &c);
+  Trig<T>::sc(bh, th, &s, &c);
   adm_kerr_sc<T>(bh, r, s, c, m);
 }
 
@@ -604,7 +656,7 @@ __device__ __forceinline__ void ham_rhs_sc(const BH<T>& bh, T r, T s, T c, T pt,
 template <int kForm, typename T>
 __device__ __forceinline__ void ham_rhs(const BH<T>& bh, T r, T th, T pt, T pr, T pth, T pph, T f[6]) {
   T s, c;
-  Trig<T>::sc(th, &s, &c);
+  Trig<T>::sc(bh, th, &s, &c);
   ham_rhs_sc<kForm, T>(bh, r, s, c, pt, pr, pth, pph, f);
 }
 
@@ -639,13 +691,13 @@ __device__ __forceinline__ T rk4_step_ham(const BH<T>& bh, T h, T z[8]) {
   T rmin = T(0);
   long long kmin = 0;
   T s0 = T(0), c0 = T(1);
-  if constexpr (!kRolled) Trig<T>::sc(z[2], &s0, &c0);
+  if constexpr (!kRolled) Trig<T>::sc(bh, z[2], &s0, &c0);
   T sn = s0, cs = c0;
   auto stage = [&](int s) {
     T f[6];
     if constexpr (kRolled) {
       T sr, cr;
-      Trig<T>::sc(th, &sr, &cr);
+      Trig<T>::sc(bh, th, &sr, &cr);
       ham_rhs_sc<kForm, T, false>(bh, r, sr, cr, z[4], pr, pth, z[7], f);
     } else {
       ham_rhs_sc<kForm, T>(bh, r, sn, cs, z[4], pr, pth, z[7], f);
@@ -771,7 +823,7 @@ template <bool kKerr, int kForm = 0>
 __device__ __forceinline__ double dopri5_attempt(const BH<double>& bh, double h, const double y[8],
                                                  const double k1[8], double y5[8], double e[8], double k7[8]) {
   double s0, c0;
-  sincos(y[2], &s0, &c0);
+  Trig<double>::sc(bh, y[2], &s0, &c0);
   // the tableau's coefficients as per-thread registers (full-rate DFMAs):
   // vreg with a zero that depends on this attempt's h, so that each is formed
   // next to its use instead of all 35 being held through the attempt

@@ -136,7 +136,10 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
 // tier |d| < 2^-5), and recip against the IEEE division on
 // x = mantissa x 2^e, e in [-60, 60].  err: max |sin error|, max |cos error|,
 // max recip error in units of the last place of 1/x, max relative error of
-// the hardware estimate alone; non-negative doubles ordered as integers.
+// the hardware estimate alone, and the steps' sine and cosine (Trig<double>)
+// against sincos: x uniform in [-4, 8] or, every other draw, a multiple of
+// pi/2 there plus an offset down to 2^-60, or (one draw in 16) up to 2^30 in
+// magnitude; non-negative doubles ordered as integers.
 __global__ void helpers_check_kernel(unsigned long long* err, uint64_t n) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const unsigned long long h1 = mix64(2 * i), h2 = mix64(2 * i + 1);
@@ -159,6 +162,17 @@ __global__ void helpers_check_kernel(unsigned long long* err, uint64_t n) {
     atomicMax(&err[1], (unsigned long long)__double_as_longlong(ec));
     atomicMax(&err[2], (unsigned long long)__double_as_longlong(er));
     atomicMax(&err[3], (unsigned long long)__double_as_longlong(e0));
+    const unsigned long long h4 = mix64(i ^ 0x5bd1e995ull);
+    const double u = (double)(h4 >> 11) * 0x1.0p-53;
+    double xa = (h4 & 1ull) ? fma(12.0, u, -4.0)
+                            : fma(1.5707963267948966, (double)((long long)((h4 >> 1) % 8ull) - 2),
+                                  ldexp(u - 0.5, -(int)((h4 >> 4) % 61ull)));
+    if (((h4 >> 10) & 15ull) == 0ull) xa = ldexp(u - 0.5, (int)((h4 >> 14) % 31ull));
+    double sa, ca, sl, cl;
+    Trig<double>::sc(make_bh<double>(1.0, 0.0), xa, &sa, &ca);
+    sincos(xa, &sl, &cl);
+    atomicMax(&err[4], (unsigned long long)__double_as_longlong(fabs(sa - sl)));
+    atomicMax(&err[5], (unsigned long long)__double_as_longlong(fabs(ca - cl)));
   }
 }
 
@@ -227,21 +241,21 @@ extern "C" int malbec_measure_step_loop(uint32_t form, double* steps_per_s) {
   return MALBEC_EINVAL;
 }
 
-extern "C" int malbec_check_fp64_helpers(double err[4]) {
+extern "C" int malbec_check_fp64_helpers(double err[6]) {
   if (!err) return MALBEC_EINVAL;
   unsigned long long* d = nullptr;
-  cudaError_t e = cudaMalloc(&d, 4 * sizeof(unsigned long long));
+  cudaError_t e = cudaMalloc(&d, 6 * sizeof(unsigned long long));
   if (e != cudaSuccess) return malbec::set_cuda_error(e);
-  e = cudaMemset(d, 0, 4 * sizeof(unsigned long long));
+  e = cudaMemset(d, 0, 6 * sizeof(unsigned long long));
   if (e == cudaSuccess) {
     malbec::helpers_check_kernel<<<1024, 256>>>(d, 1ull << 22);
     e = cudaGetLastError();
   }
-  unsigned long long h[4] = {0, 0, 0, 0};
+  unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
   cudaFree(d);
   if (e != cudaSuccess) return malbec::set_cuda_error(e);
-  for (int k = 0; k < 4; ++k) memcpy(&err[k], &h[k], sizeof(double));
+  for (int k = 0; k < 6; ++k) memcpy(&err[k], &h[k], sizeof(double));
   return MALBEC_OK;
 }
 

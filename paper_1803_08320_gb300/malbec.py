@@ -676,11 +676,12 @@ def measure_step_loop(form=FORM_GEODESIC) -> float:
 
 
 def check_fp64_helpers() -> dict:
-    """Max errors of the FP64 stage sine/cosine and reciprocal against CUDA's
-    sincos and IEEE division (blocks the caller)."""
-    e = (_D * 4)()
+    """Max errors of the FP64 stage sine/cosine, reciprocal and step
+    sine/cosine against CUDA's sincos and IEEE division (blocks the caller)."""
+    e = (_D * 6)()
     _check(lib().malbec_check_fp64_helpers(e), "malbec_check_fp64_helpers")
-    return {"sin_abs": e[0], "cos_abs": e[1], "recip_ulp": e[2], "recip_estimate_rel": e[3]}
+    return {"sin_abs": e[0], "cos_abs": e[1], "recip_ulp": e[2], "recip_estimate_rel": e[3],
+            "step_sin_abs": e[4], "step_cos_abs": e[5]}
 
 
 def check_operand_forms() -> dict:
