@@ -248,7 +248,8 @@ int malbec_get_mixed_zone(malbec_mixed_zone* zone);
  *                      lanes (automatic: 8 with the exchange below, 32
  *                      without) ...
  *   zone_wait          ... or until a waiting lane sat out this many warp
- *                      steps (automatic: 64);
+ *                      steps (automatic: 1 for whole-image cameras, 64
+ *                      otherwise);
  *   exchange           FP32_MIXED: 1 = the warps of a block hand FP64-zone
  *                      rays to one zone warp per block and take FP32 rays
  *                      back (zone steps run with fuller warps), 2 = every
